@@ -1,0 +1,200 @@
+/*
+ * henry.h - C ABI of libhenry: batched GB300 (sm_103a) scenario solves of the
+ * Henry saltwater-intrusion problem and multilevel Monte Carlo accumulation,
+ * after arXiv 2302.07804 ("Uncertainty quantification in coastal aquifers
+ * using the multilevel Monte Carlo method").
+ *
+ * The problem (Sec. 2.1): fluid mass and salt mass balances, Eqs. (e_cont_eq)
+ * and (e_tran_eq), with Darcy's law (e_Darcy_vel), rho(c) = rho0 + (rho1 -
+ * rho0) c (e_lin_density), D = phi Dm I (e_mol_diff), on [0, Lx] x [0, Ly]
+ * with the seaside (x = Lx) at brine hydrostatic pressure and c = 1, fresh
+ * water flowing in at x = 0 with c = 0, no flux through top and bottom, and
+ * c = 0 at t = 0 with fresh-water hydrostatic pressure.  Discretisation
+ * (Sec. 2.3): cell-centred finite volumes with upwind advection on a uniform
+ * grid of square cells (nx0 2^l x ny0 2^l cells at MLMC level l), implicit
+ * Euler with r_l = steps0 2^l steps over [0, T], Newton's method per step,
+ * each Newton system solved by BiCGStab preconditioned by one geometric
+ * multigrid V-cycle (red-black 2x2-block Gauss-Seidel smoothing, coarse
+ * operators rediscretised on the 2x coarser grids (or Galerkin products), a
+ * dense solve on the 2 x 1 coarsest grid).  Random inputs (Sec. 4, three iid
+ * U[-1, 1] factors): phi = phi_mean (1 + phi_amp xi1), K = K_mean exp(logK_amp
+ * xi2), q_in = qin_mean (1 + qin_amp xi3).
+ *
+ * Conventions for every call below:
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; they
+ *    must stay valid until the work queued on `stream` has finished.  Pointers
+ *    named *_host are host pointers.  `stream` is a cudaStream_t (NULL = the
+ *    legacy default stream).
+ *  - Arrays are dense, C order, FP64 unless stated.  A "state" array is
+ *    [n][ny][nx][2] with (p [Pa], c [-]) per cell, cell (ix, iy) centred at
+ *    ((ix + 1/2) h, (iy + 1/2) h), y pointing up.
+ *  - Return value: HENRY_OK or an error code; on error henry_last_error()
+ *    gives a message (per calling thread).  No call throws or aborts.
+ *  - Calls are asynchronous with respect to the host except where stated
+ *    ("synchronises"): the batch solve synchronises `stream` between Newton
+ *    and Krylov iterations to test convergence.
+ *  - The handle owns all device workspace; it grows on demand and is freed by
+ *    henry_destroy.  A handle is not thread-safe: one host thread at a time.
+ */
+#ifndef HENRY_H
+#define HENRY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+enum {
+  HENRY_OK = 0,
+  HENRY_EINVAL = 1,  /* invalid argument (NULL pointer, n <= 0, level out of range, ...) */
+  HENRY_ECUDA = 2,   /* a CUDA runtime call failed */
+  HENRY_ENOMEM = 3,  /* device allocation failed */
+  HENRY_ENOCONV = 4, /* at least one sample did not converge; see status_dev */
+  HENRY_ELIMIT = 5   /* an iteration cap of the driver was reached */
+};
+
+/* Per-sample status codes written to status_dev. */
+enum {
+  HENRY_SAMPLE_OK = 0,
+  HENRY_SAMPLE_NEWTON = 1,   /* Newton did not converge within newton_maxit in some step */
+  HENRY_SAMPLE_LINEAR = 2,   /* BiCGStab hit lin_maxit or broke down in some Newton iteration */
+  HENRY_SAMPLE_NONFINITE = 3 /* a residual or coefficient was NaN or infinite */
+};
+
+/* Arithmetic of the linear solves (the Newton residual, update, QoIs and
+ * MLMC sums are FP64 in both). */
+enum { HENRY_FP64 = 0, HENRY_MIXED = 1 /* FP32 Jacobian, BiCGStab and V-cycle */ };
+
+/* Coarse-grid operators of the multigrid hierarchy. */
+enum { HENRY_COARSE_REDISCRETISE = 0, HENRY_COARSE_GALERKIN = 1 };
+
+/* Number of QoIs per sample: [0] total salt mass sum phi rho c h^2 [kg per m
+ * of depth] at T, [1] c at (1.5 m, 0.25 m) at T (mean of the 4 cells meeting
+ * at that vertex). */
+#define HENRY_N_QOI 2
+/* Number of random inputs per sample (xi1, xi2, xi3). */
+#define HENRY_N_XI 3
+
+typedef struct henry_handle henry_handle;
+
+/* Physics, discretisation and solver settings, SI units.  Paper values
+ * (Table tab:HenryParam): E[phi] 0.35, D 18.8571e-6, K 1.020408e-9, g 9.8,
+ * rho0 1000, rho1 1024.99, mu 1e-3; henry_default_config() fills the
+ * configuration solved here (g 9.81, rho1 1025, Dm 1.886e-5, T 7200 s,
+ * 32 x 16 cells and 20 steps at level 0). */
+typedef struct {
+  double Lx, Ly, T, rho0, rho1, mu, g, Dm;
+  double phi_mean, K_mean, qin_mean; /* qin_mean: inflow velocity [m/s] into the domain at x = 0 */
+  double phi_amp, logK_amp, qin_amp;
+  int32_t nx0, ny0, steps0, max_level; /* nx0 even, ny0 divisible by 4, nx0 / ny0 = Lx / Ly */
+  int32_t precision;                   /* HENRY_FP64 or HENRY_MIXED */
+  int32_t coarse_op;                   /* HENRY_COARSE_REDISCRETISE or HENRY_COARSE_GALERKIN */
+  double newton_atol;  /* stop when max |R| / (rho0 h^2 / tau) <= newton_atol ... */
+  double newton_dxtol; /* ... or right after an update with max(|dp| / (rho0 g Ly), |dc|) <= newton_dxtol */
+  double lin_rtol;     /* BiCGStab: ||r||_2 <= lin_rtol ||b||_2 per sample */
+  int32_t newton_maxit, lin_maxit, nu1, nu2; /* caps; pre/post smoothing sweeps of the V-cycle */
+  double workspace_bytes;                    /* device workspace budget per batch (chunking) */
+} henry_config;
+
+/* Iteration statistics of one henry_level_batch_solve call (host struct). */
+typedef struct {
+  int64_t newton_iters; /* Newton iterations summed over samples and steps (fine + coarse) */
+  int64_t linear_iters; /* BiCGStab iterations summed over samples and Newton iterations */
+  int64_t newton_solves; /* Newton solves (samples x steps) */
+  int64_t failed_samples;
+  double cell_steps; /* sum over solved scenarios of cells x steps (coarse partners included) */
+} henry_stats;
+
+/* Fill *cfg with the defaults described above.  Never fails. */
+void henry_default_config(henry_config* cfg);
+
+/* Create a handle for `cfg` (copied).  Allocates no device memory yet.
+ * Errors: EINVAL on a NULL pointer or inconsistent grid sizes. */
+int henry_create(const henry_config* cfg, henry_handle** out);
+
+/* Free the handle and its device workspace (synchronises the device).
+ * NULL is ignored. */
+void henry_destroy(henry_handle* h);
+
+/* Message of the last error on this thread ("" if none). */
+const char* henry_last_error(void);
+
+/* a1. Sample xi[n][3] for samples first_sample .. first_sample + n - 1 of
+ * MLMC level `level` with Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ * two 32-bit halves of `seed`; sample s uses counters (level, lo32(s),
+ * hi32(s), 0) -> xi1 from words (0,1), xi2 from words (2,3) and (level,
+ * lo32(s), hi32(s), 1) -> xi3 from words (0,1); two words (w0, w1) map
+ * exactly to (2 u + 1 - 2^52) 2^-52 with u = (w0 << 20) | (w1 >> 12), a value
+ * in (-1, 1).  The paper draws xi iid uniform on [-1, 1] (Sec. 4). */
+int henry_sample_xi(uint64_t seed, int level, uint64_t first_sample, int n, double* xi_dev, void* stream);
+
+/* a2-a11. Solve n scenarios at MLMC level `level` (0 <= level <= max_level)
+ * for inputs xi_dev[n][3] and write the QoIs at T to qoi_fine_dev[n][2].
+ * If with_coarse != 0 (level >= 1) also solve the same xi on level - 1 (the
+ * coarse partner of the telescoping difference, Eq. (A): same xi, grid and
+ * time step of the coarser level) into qoi_coarse_dev[n][2].
+ * status_dev[n] (int32) receives HENRY_SAMPLE_* (worst over fine and coarse).
+ * stats_host may be NULL.  Synchronises `stream`.  Returns HENRY_ENOCONV if
+ * any sample failed (its QoIs are then unspecified). */
+int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n,
+                            double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
+                            henry_stats* stats_host, void* stream);
+
+/* a12. Merge one batch of level-`level` samples into running MLMC sums.
+ * Y = qoi_fine - qoi_coarse (qoi_coarse_dev NULL: Y = qoi_fine, level 0), the
+ * level term of the telescoping sum Eq. (EgL) / Def. (Yell).  Samples with
+ * status_dev[i] != 0 are skipped (status_dev may be NULL: all used).
+ * sums_dev[2][n_qoi][3] holds (count, mean, M2) with M2 the centred sum of
+ * squares; [0] for Y and [1] for qoi_fine itself; it is read and updated in
+ * place (zero it before the first batch).  The batch's moments are formed in
+ * one block on the device and merged with Chan's pairwise update.  `level` is
+ * only checked (>= 0).  Asynchronous on `stream`. */
+int mlmc_accumulate(int level, int n, int n_qoi, const double* qoi_fine_dev, const double* qoi_coarse_dev,
+                    const int32_t* status_dev, double* sums_dev, void* stream);
+
+/* a13. Eq. (M_ell): m_l = ceil(var_budget^-1 sqrt(V_l / s_l) sum_i sqrt(V_i s_i))
+ * for l = 0 .. n_levels - 1 (host arrays; V_l >= 0, s_l > 0, var_budget > 0).
+ * Levels with V_l = 0 get m_l = 0.  Host only, synchronous. */
+int mlmc_allocate(int n_levels, const double* V_host, const double* s_host, double var_budget, int64_t* m_out_host);
+
+/* ---- Per-step entry points: one step of the solve on given states, for
+ * checking each step on its own.  Each evaluates the coefficients of
+ * xi_dev[n][3] at `level` and takes the current and previous-time-step states
+ * state_dev, state_old_dev ([n][ny][nx][2]).  Residuals and Jacobians are
+ * scaled by 1 / (rho0 h^2 / tau) of that level.  Asynchronous on `stream`. */
+
+/* a4. F_dev[n][ny][nx][2] = scaled residual (fluid mass, salt mass) and, if
+ * J_dev is not NULL, J_dev[n][ny][nx][5][2][2] = scaled Jacobian blocks
+ * coupling each cell to (self, west, east, south, north) neighbour; block
+ * [eq][var], eq 0 = fluid mass, 1 = salt; var 0 = p, 1 = c; zero across the
+ * domain boundary.  In HENRY_MIXED the blocks are the FP32 copy the solver
+ * uses, widened to FP64. */
+int henry_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                   const double* state_old_dev, double* F_dev, double* J_dev, void* stream);
+
+/* a8. y_dev = J x_dev with J the scaled Jacobian at the given states; x, y
+ * are [n][ny][nx][2]. */
+int henry_apply_jacobian(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                         const double* state_old_dev, const double* x_dev, double* y_dev, void* stream);
+
+/* a5 + a7. z_dev = one V(nu1, nu2) cycle applied to b_dev from a zero
+ * initial guess, on the hierarchy built at the given states; b, z are
+ * [n][ny][nx][2]. */
+int henry_precondition(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                       const double* state_old_dev, const double* b_dev, double* z_dev, void* stream);
+
+/* a6. x_dev = BiCGStab solution of J x = b_dev to lin_rtol (right-
+ * preconditioned by the V-cycle, from x = 0); iters_dev[n] (int32, may be
+ * NULL) receives the iteration counts (-1: not converged within lin_maxit).
+ * Synchronises `stream`. */
+int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                       const double* state_old_dev, const double* b_dev, double* x_dev, int32_t* iters_dev,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HENRY_H */

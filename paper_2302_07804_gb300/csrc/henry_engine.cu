@@ -1,0 +1,754 @@
+// Host engine and C ABI of libhenry (declared in include/henry.h).
+//
+// One "group" = the device workspace of a batch of B samples at one MLMC
+// level: the fine state, old state and residual (FP64), the Jacobian
+// hierarchy (6 block planes per multigrid level), the Krylov and multigrid
+// vectors (T = double or float), per-sample coefficients, scalars, flags and
+// partial sums.  It is carved out of a single cudaMalloc and kept in the
+// handle for reuse by later calls of the same level.
+//
+// The solve of one group runs the r_l implicit-Euler steps (Sec. 2.3 of
+// arXiv 2302.07804); each step runs Newton iterations, each Newton iteration
+// assembles the residual and the Jacobian on the fine grid and the coarse
+// operators, and solves the Newton system with BiCGStab right-preconditioned
+// by one V-cycle.  Per-sample convergence decisions are taken on the device;
+// the host only reads "how many samples are still iterating" once per Newton
+// and once per BiCGStab iteration to decide when to stop launching.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "henry.h"
+#include "henry_kernels.cuh"
+#include "henry_misc.cuh"
+
+using namespace hk;
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return set_err(HENRY_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+#define CKL()                                                                                        \
+  do {                                                                                               \
+    cudaError_t e_ = cudaGetLastError();                                                             \
+    if (e_ != cudaSuccess) return set_err(HENRY_ECUDA, "kernel launch failed (line %d): %s", __LINE__, \
+                                          cudaGetErrorString(e_));                                   \
+  } while (0)
+
+inline unsigned nblk(int64_t n, int tpb = TPB) { return (unsigned)((n + tpb - 1) / tpb); }
+
+struct Level {
+  int nx, ny, N;
+  double h;
+  double2 *x, *xo;  // state (fine: Newton iterate; coarse: restricted) and old state
+  void* J;          // 6 planes of B4
+  void *mgx, *mgb;  // multigrid vectors (coarse levels)
+  int64_t plane;
+};
+
+// Carves sub-arrays out of one allocation (256-byte aligned).
+struct Carver {
+  char* base;
+  size_t off;
+  template <typename P>
+  P* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+template <typename T>
+struct Group {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  int level = -1, Bcap = 0, K = 0, nct = 0;
+  char* mem = nullptr;
+  size_t bytes = 0;
+  std::vector<Level> lv;
+  double2* F = nullptr;
+  V2 *r, *rh, *p, *v, *s, *t, *ph, *sh, *dx;
+  Coef* coef;
+  double* part;
+  int *newton_active, *lin_active, *newton_it, *status, *iters, *counter;
+  unsigned long long* totals;  // [0] Newton iterations, [1] BiCGStab iterations
+  LinScal* sc;
+  T* Ainv;
+
+  // Lay out (or size, with base == nullptr) the workspace for B samples.
+  size_t carve(char* base, int B, int nx0, int ny0, double h0) {
+    Carver c{base, 0};
+    std::vector<Level> L;
+    int nx = nx0, ny = ny0;
+    double h = h0;
+    for (;;) {
+      Level l;
+      l.nx = nx; l.ny = ny; l.N = nx * ny; l.h = h;
+      l.plane = (int64_t)B * l.N;
+      l.x = c.take<double2>(sizeof(double2) * l.plane);
+      l.xo = c.take<double2>(sizeof(double2) * l.plane);
+      l.J = c.take<B4>(sizeof(B4) * 6 * l.plane);
+      if (L.empty()) {
+        l.mgx = l.mgb = nullptr;
+      } else {
+        l.mgx = c.take<V2>(sizeof(V2) * l.plane);
+        l.mgb = c.take<V2>(sizeof(V2) * l.plane);
+      }
+      L.push_back(l);
+      if (nx <= 2 || ny <= 1) break;
+      nx /= 2; ny /= 2; h *= 2.0;
+    }
+    const int64_t n0 = (int64_t)B * nx0 * ny0;
+    F = c.take<double2>(sizeof(double2) * n0);
+    V2** vecs[9] = {&r, &rh, &p, &v, &s, &t, &ph, &sh, &dx};
+    for (auto vp : vecs) *vp = c.take<V2>(sizeof(V2) * n0);
+    coef = c.take<Coef>(sizeof(Coef) * B);
+    nct = nx0 * ny0 / TPB;
+    part = c.take<double>(sizeof(double) * NPART * (size_t)B * nct);
+    newton_active = c.take<int>(sizeof(int) * B);
+    lin_active = c.take<int>(sizeof(int) * B);
+    newton_it = c.take<int>(sizeof(int) * B);
+    status = c.take<int>(sizeof(int) * B);
+    iters = c.take<int>(sizeof(int) * B);
+    counter = c.take<int>(sizeof(int) * 4);
+    totals = c.take<unsigned long long>(sizeof(unsigned long long) * 4);
+    sc = c.take<LinScal>(sizeof(LinScal) * B);
+    Ainv = c.take<T>(sizeof(T) * 16 * B);
+    if (base) {
+      lv = L;
+      K = (int)L.size() - 1;
+    }
+    return c.off + 256;
+  }
+};
+
+}  // namespace
+
+struct henry_handle {
+  henry_config cfg;
+  std::map<int, Group<double>> g64;
+  std::map<int, Group<float>> g32;
+  int* host_counter = nullptr;  // pinned
+  unsigned long long* host_totals = nullptr;
+};
+
+namespace {
+
+Phys phys_of(const henry_config& c) {
+  Phys p;
+  p.rho0 = c.rho0; p.rho1 = c.rho1; p.drho = c.rho1 - c.rho0; p.g = c.g; p.Ly = c.Ly;
+  return p;
+}
+
+struct LevelGeom {
+  int nx, ny, steps;
+  double h, tau;
+};
+LevelGeom geom(const henry_config& c, int level) {
+  LevelGeom g;
+  g.nx = c.nx0 << level;
+  g.ny = c.ny0 << level;
+  g.steps = c.steps0 << level;
+  g.h = c.Ly / g.ny;
+  g.tau = c.T / g.steps;
+  return g;
+}
+
+template <typename T>
+size_t bytes_per_sample(const henry_config& c, int level) {
+  Group<T> g;
+  LevelGeom lg = geom(c, level);
+  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h);
+}
+
+template <typename T>
+std::map<int, Group<T>>& groups(henry_handle* h);
+template <>
+std::map<int, Group<double>>& groups<double>(henry_handle* h) { return h->g64; }
+template <>
+std::map<int, Group<float>>& groups<float>(henry_handle* h) { return h->g32; }
+
+int ensure_pinned(henry_handle* H);
+
+// Workspace for B samples at `level` (reused when large enough).
+template <typename T>
+int get_group(henry_handle* H, int level, int B, Group<T>** out) {
+  int rc0 = ensure_pinned(H);
+  if (rc0) return rc0;
+  auto& m = groups<T>(H);
+  Group<T>& g = m[level];
+  if (g.mem && g.Bcap >= B) {
+    *out = &g;
+    return HENRY_OK;
+  }
+  if (g.mem) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(g.mem));
+    g.mem = nullptr;
+  }
+  LevelGeom lg = geom(H->cfg, level);
+  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(HENRY_ENOMEM, "cudaMalloc of %zu bytes for %d samples at level %d failed", bytes, B, level);
+  }
+  g.mem = mem;
+  g.bytes = bytes;
+  g.carve(mem, B, lg.nx, lg.ny, lg.h);
+  g.level = level;
+  g.Bcap = B;
+  *out = &g;
+  return HENRY_OK;
+}
+
+template <typename T>
+int max_batch(const henry_config& c, int level) {
+  const double per = (double)bytes_per_sample<T>(c, level);
+  const double b = std::floor(c.workspace_bytes / per);
+  return (int)std::max(1.0, std::min(b, 1.0e6));
+}
+
+// Coefficients from xi for B samples (writes coef and status).
+template <typename T>
+int set_coefficients(henry_handle* H, Group<T>& G, const double* xi, int B, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
+  k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status);
+  CKL();
+  return HENRY_OK;
+}
+
+// Coarse-grid operators for every multigrid level below the fine one, plus
+// the coarsest inverse.  Expects lv[k].x for k >= 1 up to date when
+// rediscretising (call restrict_states first).
+template <typename T>
+int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  const Phys ph = phys_of(H->cfg);
+  for (int k = 1; k <= G.K; ++k) {
+    Level& L = G.lv[k];
+    if (H->cfg.coarse_op == HENRY_COARSE_GALERKIN) {
+      Level& Lf = G.lv[k - 1];
+      k_galerkin<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)Lf.J, Lf.plane, (B4*)L.J,
+                                                             L.plane, G.lin_active);
+    } else {
+      k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, inv_tau, inv_s,
+                                                                    L.x, L.xo, G.lin_active, nullptr, (B4*)L.J,
+                                                                    L.plane, nullptr);
+    }
+    CKL();
+  }
+  Level& Lc = G.lv[G.K];
+  k_coarse_inverse<T><<<nblk(B, 64), 64, 0, st>>>(B, (const B4*)Lc.J, Lc.plane, G.Ainv, G.lin_active);
+  CKL();
+  return HENRY_OK;
+}
+
+// x_k -> x_{k+1} (mean of children) for all levels; `old` selects xo.
+template <typename T>
+int restrict_states(Group<T>& G, int B, bool old, const int* active, cudaStream_t st) {
+  for (int k = 0; k < G.K; ++k) {
+    Level& Lf = G.lv[k];
+    Level& Lc = G.lv[k + 1];
+    k_restrict_state<<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, old ? Lf.xo : Lf.x,
+                                                              old ? Lc.xo : Lc.x, active);
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// One V(nu1, nu2) cycle: x0 = M^{-1} b0 on the fine level (active = lin_active).
+template <typename T>
+int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, typename VT<T>::v2* x0,
+           cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  const int nu1 = H->cfg.nu1, nu2 = H->cfg.nu2;
+  const int* act = G.lin_active;
+  for (int k = 0; k < G.K; ++k) {
+    Level& L = G.lv[k];
+    const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
+    V2* x = k == 0 ? x0 : (V2*)L.mgx;
+    const B4* J = (const B4*)L.J;
+    const unsigned gh = nblk((int64_t)B * L.N / 2);
+    Level& Lc = G.lv[k + 1];
+    if (nu1 > 0) {
+      k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
+      k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      for (int i = 1; i < nu1; ++i) {
+        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
+        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      }
+      k_residual_restrict<T, 0><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
+                                                                        (V2*)Lc.mgb, act);
+    } else {
+      k_zero<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>((int64_t)B * L.N, x);
+      k_residual_restrict<T, 1><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
+                                                                        (V2*)Lc.mgb, act);
+    }
+    CKL();
+  }
+  {
+    Level& Lc = G.lv[G.K];
+    k_coarse_solve<T><<<nblk(B, 64), 64, 0, st>>>(B, G.Ainv, (const V2*)Lc.mgb, (V2*)Lc.mgx, act);
+    CKL();
+  }
+  for (int k = G.K - 1; k >= 0; --k) {
+    Level& L = G.lv[k];
+    Level& Lc = G.lv[k + 1];
+    const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
+    V2* x = k == 0 ? x0 : (V2*)L.mgx;
+    const B4* J = (const B4*)L.J;
+    const unsigned gh = nblk((int64_t)B * L.N / 2);
+    if (nu2 > 0) {
+      k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act);
+      k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      for (int i = 1; i < nu2; ++i) {
+        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
+        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      }
+    } else {
+      k_prolong_add<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, x, (const V2*)Lc.mgx, act);
+    }
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// Pinned host words for the convergence counters (allocated on first use, so
+// that creating a handle touches no GPU).
+int ensure_pinned(henry_handle* H) {
+  if (!H->host_counter) CK(cudaMallocHost(&H->host_counter, 64));
+  if (!H->host_totals) CK(cudaMallocHost(&H->host_totals, 64));
+  return HENRY_OK;
+}
+
+int read_counter(henry_handle* H, const int* dev, cudaStream_t st, int* out) {
+  CK(cudaMemcpyAsync(H->host_counter, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out = *H->host_counter;
+  return HENRY_OK;
+}
+
+// BiCGStab on the fine level for the samples with lin_active set; right-hand
+// side -F; solution in G.dx.
+template <typename T>
+int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
+  Level& L = G.lv[0];
+  const int N = L.N;
+  const unsigned g = nblk((int64_t)B * N);
+  k_bicg_init<T><<<g, TPB, 0, st>>>(B, N, G.F, G.r, G.rh, G.p, G.v, G.dx, G.part, G.lin_active);
+  CKL();
+  const double rtol2 = H->cfg.lin_rtol * H->cfg.lin_rtol;
+  for (int it = 0; it <= H->cfg.lin_maxit; ++it) {
+    CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
+    k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, H->cfg.lin_maxit, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
+                                    G.iters, G.status, G.counter + 1, G.totals + 1);
+    CKL();
+    int n_act = 0;
+    int rc = read_counter(H, G.counter + 1, st, &n_act);
+    if (rc) return rc;
+    if (n_act == 0) break;
+    rc = vcycle<T>(H, G, B, G.p, G.ph, st);
+    if (rc) return rc;
+    k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const typename VT<T>::b4*)L.J, L.plane, G.ph, G.v, G.rh,
+                                     G.part, P_RV, 0, G.lin_active);
+    k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active);
+    CKL();
+    rc = vcycle<T>(H, G, B, G.s, G.sh, st);
+    if (rc) return rc;
+    k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const typename VT<T>::b4*)L.J, L.plane, G.sh, G.t, G.s,
+                                     G.part, P_TS, P_TT, G.lin_active);
+    k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active);
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// Full scenario solves of B samples whose coefficients and status are set.
+template <typename T>
+int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  const Phys ph = phys_of(c);
+  Level& L = G.lv[0];
+  const int N = L.N;
+  const int64_t n0 = (int64_t)B * N;
+  const double inv_tau = 1.0 / lg.tau;
+  const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
+  const double inv_pref = 1.0 / (c.rho0 * c.g * c.Ly);
+  CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
+  k_init_state<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0 * c.g, c.Ly, L.x);
+  CKL();
+  for (int step = 0; step < lg.steps; ++step) {
+    k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
+    CKL();
+    int rc = restrict_states<T>(G, B, true, G.newton_active, st);
+    if (rc) return rc;
+    for (int it = 0; it <= c.newton_maxit; ++it) {
+      CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
+      k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, inv_tau, inv_s, L.x, L.xo,
+                                                     G.newton_active, G.F, (B4*)L.J, L.plane, G.part + P_MAX * (int64_t)B * G.nct);
+      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit,
+                                                       G.part + P_MAX * (int64_t)B * G.nct, G.newton_active,
+                                                       G.lin_active, G.newton_it, G.status, G.counter, G.totals);
+      CKL();
+      int n_act = 0;
+      rc = read_counter(H, G.counter, st, &n_act);
+      if (rc) return rc;
+      if (n_act == 0) break;
+      if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
+        rc = restrict_states<T>(G, B, false, G.lin_active, st);
+        if (rc) return rc;
+      }
+      rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
+      if (rc) return rc;
+      rc = linear_solve<T>(H, G, B, st);
+      if (rc) return rc;
+      k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, L.x, G.dx, G.part + P_MAX * (int64_t)B * G.nct,
+                                                    G.newton_active);
+      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, G.part + P_MAX * (int64_t)B * G.nct,
+                                                      G.newton_active, G.status);
+      CKL();
+    }
+  }
+  k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi);
+  CKL();
+  return HENRY_OK;
+}
+
+__global__ void k_merge_status(int n, const int* __restrict__ a, int32_t* __restrict__ out, int first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = a[i];
+  if (first) out[i] = v;
+  else if (out[i] == 0) out[i] = v;
+}
+
+template <typename T>
+int batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status, bool first,
+                      henry_stats* stats, cudaStream_t st) {
+  const int Bmax = max_batch<T>(H->cfg, level);
+  const LevelGeom lg = geom(H->cfg, level);
+  for (int off = 0; off < n; off += Bmax) {
+    const int B = std::min(Bmax, n - off);
+    Group<T>* G = nullptr;
+    int rc = get_group<T>(H, level, std::min(Bmax, n), &G);
+    if (rc) return rc;
+    rc = set_coefficients<T>(H, *G, xi + 3 * (int64_t)off, B, st);
+    if (rc) return rc;
+    rc = solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
+    if (rc) return rc;
+    k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, first ? 1 : 0);
+    CKL();
+    if (stats) {
+      CK(cudaMemcpyAsync(H->host_totals, G->totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      stats->newton_iters += H->host_totals[0];
+      stats->linear_iters += H->host_totals[1];
+      stats->newton_solves += (int64_t)B * lg.steps;
+      stats->cell_steps += (double)B * lg.nx * lg.ny * lg.steps;
+    }
+  }
+  return HENRY_OK;
+}
+
+// Per-step entry points: set up one group from given states.
+template <typename T>
+int setup_from_states(henry_handle* H, int level, const double* xi, int n, const double* state,
+                      const double* state_old, Group<T>** out, cudaStream_t st) {
+  Group<T>* G = nullptr;
+  int rc = get_group<T>(H, level, n, &G);
+  if (rc) return rc;
+  rc = set_coefficients<T>(H, *G, xi, n, st);
+  if (rc) return rc;
+  Level& L = G->lv[0];
+  const int64_t n0 = (int64_t)n * L.N;
+  k_to_storage<double2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const double2*)state, L.x);
+  k_to_storage<double2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const double2*)state_old, L.xo);
+  k_step_flags<<<nblk(n, 128), 128, 0, st>>>(n, G->status, G->newton_active, G->newton_it);
+  CK(cudaMemcpyAsync(G->lin_active, G->newton_active, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  CKL();
+  *out = G;
+  return HENRY_OK;
+}
+
+template <typename T>
+int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  const double inv_tau = 1.0 / lg.tau;
+  const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
+  Level& L = G.lv[0];
+  k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, inv_tau,
+                                                               inv_s, L.x, L.xo, G.newton_active, G.F, (B4*)L.J,
+                                                               L.plane, G.part + P_MAX * (int64_t)n * G.nct);
+  CKL();
+  if (!coarse) return HENRY_OK;
+  int rc = restrict_states<T>(G, n, true, G.lin_active, st);
+  if (rc) return rc;
+  rc = restrict_states<T>(G, n, false, G.lin_active, st);
+  if (rc) return rc;
+  return build_coarse_ops<T>(H, G, n, inv_tau, inv_s, st);
+}
+
+bool valid_level(henry_handle* h, int level) { return h && level >= 0 && level <= h->cfg.max_level; }
+
+template <typename T>
+int step_entry(henry_handle* H, int which, int level, const double* xi, int n, const double* state,
+               const double* state_old, const double* in, double* out, double* out2, int32_t* iters,
+               cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  Group<T>* G = nullptr;
+  int rc = setup_from_states<T>(H, level, xi, n, state, state_old, &G, st);
+  if (rc) return rc;
+  Level& L = G->lv[0];
+  const int64_t n0 = (int64_t)n * L.N;
+  rc = assemble_all<T>(H, *G, n, which >= 2, st);
+  if (rc) return rc;
+  switch (which) {
+    case 0:  // assemble
+      k_from_storage<double2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, G->F, (double2*)out);
+      if (out2) k_blocks_out<B4><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const B4*)L.J, L.plane, out2);
+      break;
+    case 1:  // apply
+      k_to_storage<V2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const double2*)in, G->p);
+      k_spmv<T, 0><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const B4*)L.J, L.plane, G->p, G->v, nullptr, nullptr,
+                                             0, 0, G->lin_active);
+      k_from_storage<V2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, G->v, (double2*)out);
+      break;
+    case 2:  // precondition
+      k_to_storage<V2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const double2*)in, G->p);
+      CKL();
+      rc = vcycle<T>(H, *G, n, G->p, G->ph, st);
+      if (rc) return rc;
+      k_from_storage<V2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, G->ph, (double2*)out);
+      break;
+    case 3:  // linear solve: F := -b, BiCGStab, dx out
+      k_to_storage<double2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, (const double2*)in, G->F);
+      k_scale_d2<<<nblk(n0), TPB, 0, st>>>(n0, -1.0, G->F);
+      CKL();
+      CK(cudaMemsetAsync(G->totals, 0, 4 * sizeof(unsigned long long), st));
+      rc = linear_solve<T>(H, *G, n, st);
+      if (rc) return rc;
+      k_from_storage<V2><<<nblk(n0), TPB, 0, st>>>(n, L.nx, L.ny, G->dx, (double2*)out);
+      if (iters) CK(cudaMemcpyAsync(iters, G->iters, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+      break;
+  }
+  CKL();
+  return HENRY_OK;
+}
+
+int check_step_args(henry_handle* h, int level, const double* xi, int n, const double* state,
+                    const double* state_old) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!xi || !state || !state_old) return set_err(HENRY_EINVAL, "NULL input pointer");
+  return HENRY_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void henry_default_config(henry_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof *c);
+  c->Lx = 2.0; c->Ly = 1.0; c->T = 7200.0;
+  c->rho0 = 1000.0; c->rho1 = 1025.0; c->mu = 1e-3; c->g = 9.81; c->Dm = 1.886e-5;
+  c->phi_mean = 0.35; c->K_mean = 1.02e-9; c->qin_mean = 6.6e-5;
+  c->phi_amp = 0.2; c->logK_amp = 0.5; c->qin_amp = 0.2;
+  c->nx0 = 32; c->ny0 = 16; c->steps0 = 20; c->max_level = 5;
+  c->precision = HENRY_FP64;
+  c->coarse_op = HENRY_COARSE_REDISCRETISE;
+  c->newton_atol = 1e-11;
+  c->newton_dxtol = 1e-12;
+  c->lin_rtol = 1e-8;
+  c->newton_maxit = 30;
+  c->lin_maxit = 100;
+  c->nu1 = 2; c->nu2 = 2;
+  c->workspace_bytes = 16.0e9;
+}
+
+int henry_create(const henry_config* cfg, henry_handle** out) {
+  if (!cfg || !out) return set_err(HENRY_EINVAL, "NULL argument");
+  *out = nullptr;
+  const henry_config& c = *cfg;
+  if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || c.nx0 != 2 * c.ny0)
+    return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
+  if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)
+    return set_err(HENRY_EINVAL, "domain must be Lx = 2 Ly (square cells)");
+  if (c.max_level < 0 || c.max_level > 8) return set_err(HENRY_EINVAL, "max_level %d outside [0, 8]", c.max_level);
+  if (((int64_t)(c.nx0 << c.max_level) * (c.ny0 << c.max_level)) % TPB != 0 || c.nx0 * c.ny0 < TPB)
+    return set_err(HENRY_EINVAL, "cells per sample must be a multiple of %d", TPB);
+  if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
+  if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
+    return set_err(HENRY_EINVAL, "bad coarse_op");
+  if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
+      c.lin_rtol <= 0 || c.workspace_bytes <= 0)
+    return set_err(HENRY_EINVAL, "bad solver settings");
+  henry_handle* h = new henry_handle();
+  h->cfg = c;
+  *out = h;
+  return HENRY_OK;
+}
+
+void henry_destroy(henry_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& kv : h->g64)
+    if (kv.second.mem) cudaFree(kv.second.mem);
+  for (auto& kv : h->g32)
+    if (kv.second.mem) cudaFree(kv.second.mem);
+  if (h->host_counter) cudaFreeHost(h->host_counter);
+  if (h->host_totals) cudaFreeHost(h->host_totals);
+  delete h;
+}
+
+const char* henry_last_error(void) { return g_err.c_str(); }
+
+int henry_sample_xi(uint64_t seed, int level, uint64_t first_sample, int n, double* xi_dev, void* stream) {
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!xi_dev) return set_err(HENRY_EINVAL, "xi_dev is NULL");
+  if (level < 0) return set_err(HENRY_EINVAL, "level %d < 0", level);
+  k_sample_xi<<<nblk(n, 128), 128, 0, (cudaStream_t)stream>>>(seed, level, first_sample, n, xi_dev);
+  CKL();
+  return HENRY_OK;
+}
+
+int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n,
+                            double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
+                            henry_stats* stats_host, void* stream) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!xi_dev || !qoi_fine_dev || !status_dev) return set_err(HENRY_EINVAL, "NULL device pointer");
+  if (with_coarse && level == 0) return set_err(HENRY_EINVAL, "level 0 has no coarse partner");
+  if (with_coarse && !qoi_coarse_dev) return set_err(HENRY_EINVAL, "qoi_coarse_dev is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  henry_stats local;
+  std::memset(&local, 0, sizeof local);
+  henry_stats* stp = stats_host ? &local : nullptr;
+  int rc;
+  if (h->cfg.precision == HENRY_MIXED) {
+    rc = batch_solve_level<float>(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
+    if (!rc && with_coarse)
+      rc = batch_solve_level<float>(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
+  } else {
+    rc = batch_solve_level<double>(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
+    if (!rc && with_coarse)
+      rc = batch_solve_level<double>(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
+  }
+  if (rc) return rc;
+  // count failed samples (synchronises)
+  std::vector<int32_t> hs(n);
+  CK(cudaMemcpyAsync(hs.data(), status_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int64_t failed = 0;
+  for (int i = 0; i < n; ++i) failed += hs[i] != 0;
+  if (stats_host) {
+    local.failed_samples = failed;
+    *stats_host = local;
+  }
+  if (failed) return set_err(HENRY_ENOCONV, "%lld of %d samples did not converge", (long long)failed, n);
+  return HENRY_OK;
+}
+
+int mlmc_accumulate(int level, int n, int n_qoi, const double* qoi_fine_dev, const double* qoi_coarse_dev,
+                    const int32_t* status_dev, double* sums_dev, void* stream) {
+  if (level < 0) return set_err(HENRY_EINVAL, "level %d < 0", level);
+  if (n <= 0 || n_qoi <= 0) return set_err(HENRY_EINVAL, "n = %d and n_qoi = %d must be positive", n, n_qoi);
+  if (!qoi_fine_dev || !sums_dev) return set_err(HENRY_EINVAL, "NULL device pointer");
+  k_mlmc_accumulate<<<1, 1024, 0, (cudaStream_t)stream>>>(n, n_qoi, qoi_fine_dev, qoi_coarse_dev, status_dev,
+                                                          sums_dev);
+  CKL();
+  return HENRY_OK;
+}
+
+int mlmc_allocate(int n_levels, const double* V, const double* s, double var_budget, int64_t* m_out) {
+  if (n_levels <= 0 || !V || !s || !m_out) return set_err(HENRY_EINVAL, "bad arguments");
+  if (!(var_budget > 0.0)) return set_err(HENRY_EINVAL, "var_budget must be positive");
+  double tot = 0.0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (!(V[l] >= 0.0) || !(s[l] > 0.0)) return set_err(HENRY_EINVAL, "V[%d] must be >= 0 and s[%d] > 0", l, l);
+    tot += std::sqrt(V[l] * s[l]);
+  }
+  for (int l = 0; l < n_levels; ++l) {
+    const double m = std::sqrt(V[l] / s[l]) * tot / var_budget;
+    if (!(m < 9.0e18)) return set_err(HENRY_EINVAL, "m[%d] overflows", l);
+    m_out[l] = (int64_t)std::ceil(m);
+  }
+  return HENRY_OK;
+}
+
+#define STEP_DISPATCH(which, in, out, out2, iters)                                                              \
+  (h->cfg.precision == HENRY_MIXED                                                                             \
+       ? step_entry<float>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,        \
+                           (cudaStream_t)stream)                                                               \
+       : step_entry<double>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,       \
+                            (cudaStream_t)stream))
+
+int henry_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                   const double* state_old_dev, double* F_dev, double* J_dev, void* stream) {
+  int rc = check_step_args(h, level, xi_dev, n, state_dev, state_old_dev);
+  if (rc) return rc;
+  if (!F_dev) return set_err(HENRY_EINVAL, "F_dev is NULL");
+  return STEP_DISPATCH(0, nullptr, F_dev, J_dev, nullptr);
+}
+
+int henry_apply_jacobian(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                         const double* state_old_dev, const double* x_dev, double* y_dev, void* stream) {
+  int rc = check_step_args(h, level, xi_dev, n, state_dev, state_old_dev);
+  if (rc) return rc;
+  if (!x_dev || !y_dev) return set_err(HENRY_EINVAL, "NULL vector pointer");
+  return STEP_DISPATCH(1, x_dev, y_dev, nullptr, nullptr);
+}
+
+int henry_precondition(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                       const double* state_old_dev, const double* b_dev, double* z_dev, void* stream) {
+  int rc = check_step_args(h, level, xi_dev, n, state_dev, state_old_dev);
+  if (rc) return rc;
+  if (!b_dev || !z_dev) return set_err(HENRY_EINVAL, "NULL vector pointer");
+  return STEP_DISPATCH(2, b_dev, z_dev, nullptr, nullptr);
+}
+
+int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                       const double* state_old_dev, const double* b_dev, double* x_dev, int32_t* iters_dev,
+                       void* stream) {
+  int rc = check_step_args(h, level, xi_dev, n, state_dev, state_old_dev);
+  if (rc) return rc;
+  if (!b_dev || !x_dev) return set_err(HENRY_EINVAL, "NULL vector pointer");
+  return STEP_DISPATCH(3, b_dev, x_dev, nullptr, iters_dev);
+}
+
+}  // extern "C"

@@ -1,0 +1,778 @@
+// Device kernels of the batched Henry-problem solver (sm_103a).
+//
+// Data layout (per multigrid level k of a batch of B samples, grid nx x ny):
+//  * every per-cell array is [B][N] with N = nx ny, sample-major;
+//  * inside a sample, cells are stored row by row, and inside each row the
+//    cells of colour 0 ((ix + iy) even) come first, then those of colour 1:
+//        st(ix, iy) = iy nx + colour (nx / 2) + ix / 2.
+//    A red or black Gauss-Seidel half-sweep therefore streams contiguous
+//    memory, and the two colours never share a 32-byte sector.
+//  * the Jacobian of a level is 6 planes of 2x2 blocks [6][B N]: centre,
+//    west, east, south, north, and the inverse of the centre block (so the
+//    smoother needs no division); block = {a00, a01, a10, a11}, row = equation
+//    (fluid mass, salt), column = unknown (p, c).
+//  * states (p, c) and residuals are FP64 double2; the Jacobian, Krylov and
+//    multigrid vectors are T (double, or float in the mixed-precision mode).
+//
+// The discrete equations are the cell-centred finite-volume form of Eqs.
+// (e_cont_eq), (e_tran_eq) with Darcy's law (e_Darcy_vel), rho(c) linear
+// (e_lin_density), D = phi Dm (e_mol_diff) and the boundary conditions of
+// Sec. 2.1 of arXiv 2302.07804; every flux is taken outward from the cell:
+//   interior face P|Nb:  rho_f = (rho_P + rho_Nb)/2,
+//       q = -(K/mu) ((p_Nb - p_P)/h + sigma rho_f g),  sigma = +1 north, -1 south, 0 east/west
+//       F = rho_f q h,  G = F c_up - rho_f phi Dm (c_Nb - c_P),  c_up = c_P if F >= 0 else c_Nb
+//   x = 0:  F = -rho0 q_in h,  G = F c_up(c_b = 0) + 2 rho_b phi Dm c_P,  rho_b = (rho_P + rho0)/2
+//   x = Lx: q = -(K/mu)(p_b - p_P)/(h/2), p_b = rho1 g (Ly - y_P), rho_b = (rho_P + rho1)/2,
+//           F = rho_b q h, c_up = c_P if F >= 0 else 1, G = F c_up - 2 rho_b phi Dm (1 - c_P)
+//   R^m = phi (rho - rho_old) h^2/tau + sum F,   R^s = phi (rho c - rho_old c_old) h^2/tau + sum G
+// and every residual and Jacobian entry is multiplied by inv_s = 1 / (rho0 h_fine^2 / tau).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hk {
+
+constexpr int TPB = 256;  // threads per CTA of every cell kernel
+
+struct __align__(32) d4_t { double a00, a01, a10, a11; };
+struct __align__(16) f4_t { float a00, a01, a10, a11; };
+
+template <typename T> struct VT;
+template <> struct VT<double> { typedef double2 v2; typedef d4_t b4; };
+template <> struct VT<float> { typedef float2 v2; typedef f4_t b4; };
+
+template <typename V2, typename T>
+__device__ __forceinline__ V2 mk2(T a, T b) { V2 v; v.x = a; v.y = b; return v; }
+
+// Physics constants passed by value.
+struct Phys {
+  double rho0, rho1, drho, g, Ly;
+};
+
+// Per-sample coefficients: porosity, K / mu, phi * Dm, inflow velocity.
+struct Coef {
+  double phi, kmu, PD, qin;
+};
+
+// Per-sample scalars of BiCGStab.
+struct LinScal {
+  double rho, alpha, omega, bnorm2;
+};
+
+// Partial-sum slots of the fine-level reductions: [q][B][nct].
+enum { P_RR = 0, P_RN = 1, P_RV = 2, P_TS = 3, P_TT = 4, P_MAX = 5, NPART = 6 };
+
+__host__ __device__ __forceinline__ int st_of(int ix, int iy, int nx) {
+  return iy * nx + (((ix + iy) & 1) ? (nx >> 1) : 0) + (ix >> 1);
+}
+__device__ __forceinline__ void xy_of(int st, int nx, int& ix, int& iy) {
+  iy = st / nx;
+  const int r = st - iy * nx, half = nx >> 1;
+  const int col = r >= half ? 1 : 0;
+  const int j = r - col * half;
+  ix = 2 * j + ((col ^ iy) & 1);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// Deterministic CTA-wide sum / max; the result is returned to every thread.
+template <bool MAX>
+__device__ __forceinline__ double block_reduce(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = MAX ? warp_max(v) : warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double u = lane < nw ? sh[lane] : (MAX ? -INFINITY : 0.0);
+    u = MAX ? warp_max(u) : warp_sum(u);
+    if (lane == 0) sh[32] = u;
+  }
+  __syncthreads();
+  return sh[32];
+}
+// Sum of a sample's nct partials, computed identically by every CTA of the
+// sample (fixed order), returned to every thread.
+__device__ __forceinline__ double sample_sum(const double* __restrict__ p, int nct, double* sh) {
+  double v = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < nct; i += 32) v += p[i];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) sh[33] = v;
+  }
+  __syncthreads();
+  v = sh[33];
+  __syncthreads();
+  return v;
+}
+__device__ __forceinline__ double sample_max(const double* __restrict__ p, int nct) {
+  double v = 0.0;
+  for (int i = 0; i < nct; ++i) v = fmax(v, p[i]);
+  return v;
+}
+
+// 2x2 block helpers.
+template <typename B4, typename T>
+__device__ __forceinline__ void bmv_sub(const B4& A, T x0, T x1, T& r0, T& r1) {
+  r0 -= A.a00 * x0 + A.a01 * x1;
+  r1 -= A.a10 * x0 + A.a11 * x1;
+}
+template <typename B4, typename T>
+__device__ __forceinline__ void bmv_add(const B4& A, T x0, T x1, T& r0, T& r1) {
+  r0 += A.a00 * x0 + A.a01 * x1;
+  r1 += A.a10 * x0 + A.a11 * x1;
+}
+template <typename B4>
+__device__ __forceinline__ B4 mkblk(double a00, double a01, double a10, double a11) {
+  B4 b;
+  b.a00 = a00; b.a01 = a01; b.a10 = a10; b.a11 = a11;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// a4 (and coarse operators by rediscretisation): residual and Jacobian.
+// One thread per cell; FINE: CTAs never straddle samples (N % TPB == 0) and
+// write the per-CTA max |F| (inf for non-finite) to rmax_part[s][ct].
+template <typename T, bool FINE>
+__global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
+                                                  double h, double inv_tau, double inv_s,
+                                                  const double2* __restrict__ x, const double2* __restrict__ xo,
+                                                  const int* __restrict__ active, double2* __restrict__ F,
+                                                  typename VT<T>::b4* __restrict__ J, int64_t plane,
+                                                  double* __restrict__ rmax_part) {
+  typedef typename VT<T>::b4 B4;
+  __shared__ double sh[40];
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t total = (int64_t)B * N;
+  const int s = (int)(e / N);
+  if (FINE) {
+    if (!active[s]) return;  // uniform over the CTA
+  } else {
+    if (e >= total || !active[s]) return;
+  }
+  const int st = (int)(e - (int64_t)s * N);
+  int ix, iy;
+  xy_of(st, nx, ix, iy);
+  const int64_t base = e - st;
+  const Coef cf = coef[s];
+  const double inv_h = 1.0 / h;
+  const double2 xP = x[e], xO = xo[e];
+  const double pP = xP.x, cP = xP.y;
+  const double rhoP = ph.rho0 + ph.drho * cP;
+  const double rhoO = ph.rho0 + ph.drho * xO.y;
+  const double Vt = h * h * inv_tau;
+  double Rm = cf.phi * (rhoP - rhoO) * Vt;
+  double Rs = cf.phi * (rhoP * cP - rhoO * xO.y) * Vt;
+  double C00 = 0.0, C01 = cf.phi * ph.drho * Vt, C10 = 0.0, C11 = cf.phi * (ph.drho * cP + rhoP) * Vt;
+  double Nb[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = 0.0;
+
+  // interior faces W, E, S, N
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const double sg = (k == 2 ? -ph.g : (k == 3 ? ph.g : 0.0));
+    const double2 xN = x[base + st_of(jx, jy, nx)];
+    const double pN = xN.x, cN = xN.y;
+    const double rhoN = ph.rho0 + ph.drho * cN;
+    const double rhof = 0.5 * (rhoP + rhoN);
+    const double q = -cf.kmu * ((pN - pP) * inv_h + sg * rhof);
+    const double Ff = rhof * q * h;
+    const bool up = Ff >= 0.0;
+    const double cup = up ? cP : cN;
+    const double dFdp = rhof * cf.kmu;
+    const double dFdc = 0.5 * ph.drho * q * h - rhof * cf.kmu * 0.5 * ph.drho * sg * h;
+    const double dif = cf.PD * (cN - cP);
+    Rm += Ff;
+    Rs += Ff * cup - rhof * dif;
+    C00 += dFdp;
+    C01 += dFdc;
+    C10 += dFdp * cup;
+    C11 += dFdc * cup + (up ? Ff : 0.0) - (0.5 * ph.drho * dif - rhof * cf.PD);
+    Nb[k][0] = -dFdp;
+    Nb[k][1] = dFdc;
+    Nb[k][2] = -dFdp * cup;
+    Nb[k][3] = dFdc * cup + (up ? 0.0 : Ff) - (0.5 * ph.drho * dif + rhof * cf.PD);
+  }
+  if (ix == 0) {  // land side: prescribed inflow of fresh water, c_b = 0
+    const double Fl = -ph.rho0 * cf.qin * h;
+    const double rb = 0.5 * (rhoP + ph.rho0);
+    const bool up = Fl >= 0.0;
+    Rm += Fl;
+    Rs += Fl * (up ? cP : 0.0) + 2.0 * rb * cf.PD * cP;
+    C11 += (up ? Fl : 0.0) + cf.PD * (ph.drho * cP + 2.0 * rb);
+  }
+  if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
+    const double yP = (iy + 0.5) * h;
+    const double pb = ph.rho1 * ph.g * (ph.Ly - yP);
+    const double rb = 0.5 * (rhoP + ph.rho1);
+    const double q = -cf.kmu * (pb - pP) * (2.0 * inv_h);
+    const double Fr = rb * q * h;
+    const bool up = Fr >= 0.0;
+    const double cup = up ? cP : 1.0;
+    const double dif = cf.PD * (1.0 - cP);
+    const double dFdp = 2.0 * rb * cf.kmu;
+    const double dFdc = 0.5 * ph.drho * q * h;
+    Rm += Fr;
+    Rs += Fr * cup - 2.0 * rb * dif;
+    C00 += dFdp;
+    C01 += dFdc;
+    C10 += dFdp * cup;
+    C11 += dFdc * cup + (up ? Fr : 0.0) - (ph.drho * dif - 2.0 * rb * cf.PD);
+  }
+  if (FINE) {
+    const double fm = Rm * inv_s, fs = Rs * inv_s;
+    if (F) F[e] = make_double2(fm, fs);
+    double loc = fmax(fabs(fm), fabs(fs));
+    if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
+    const double bm = block_reduce<true>(loc, sh);
+    if (threadIdx.x == 0) {
+      const int nct = N / TPB;
+      rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
+    }
+  }
+  if (J) {
+    const double a = C00 * inv_s, b = C01 * inv_s, c = C10 * inv_s, d = C11 * inv_s;
+    J[e] = mkblk<B4>(a, b, c, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      J[(k + 1) * plane + e] = mkblk<B4>(Nb[k][0] * inv_s, Nb[k][1] * inv_s, Nb[k][2] * inv_s, Nb[k][3] * inv_s);
+    const double idet = 1.0 / (a * d - b * c);
+    J[5 * plane + e] = mkblk<B4>(d * idet, -b * idet, -c * idet, a * idet);
+  }
+}
+
+// Coarse states: mean of the 2x2 children (both the iterate and the old state).
+__global__ void __launch_bounds__(TPB) k_restrict_state(int B, int ncx, int ncy, const double2* __restrict__ xf,
+                                                        double2* __restrict__ xc, const int* __restrict__ active) {
+  const int Nc = ncx * ncy;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * Nc) return;
+  const int s = (int)(e / Nc);
+  if (!active[s]) return;
+  const int stc = (int)(e - (int64_t)s * Nc);
+  int IX, IY;
+  xy_of(stc, ncx, IX, IY);
+  const int nxf = 2 * ncx;
+  const int64_t bf = (int64_t)s * Nc * 4;
+  const double2 a = xf[bf + st_of(2 * IX, 2 * IY, nxf)];
+  const double2 b = xf[bf + st_of(2 * IX + 1, 2 * IY, nxf)];
+  const double2 c = xf[bf + st_of(2 * IX, 2 * IY + 1, nxf)];
+  const double2 d = xf[bf + st_of(2 * IX + 1, 2 * IY + 1, nxf)];
+  xc[e] = make_double2(0.25 * (((a.x + b.x) + c.x) + d.x), 0.25 * (((a.y + b.y) + c.y) + d.y));
+}
+
+// a5 (Galerkin option): A_c = R A P with piecewise-constant P, R = P^T.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_galerkin(int B, int ncx, int ncy, const typename VT<T>::b4* __restrict__ Jf,
+                                                  int64_t plane_f, typename VT<T>::b4* __restrict__ Jc,
+                                                  int64_t plane_c, const int* __restrict__ active) {
+  typedef typename VT<T>::b4 B4;
+  const int Nc = ncx * ncy;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * Nc) return;
+  const int s = (int)(e / Nc);
+  if (!active[s]) return;
+  const int stc = (int)(e - (int64_t)s * Nc);
+  int IX, IY;
+  xy_of(stc, ncx, IX, IY);
+  const int nxf = 2 * ncx;
+  const int64_t bf = (int64_t)s * Nc * 4;
+  const int64_t ia = bf + st_of(2 * IX, 2 * IY, nxf), ib = bf + st_of(2 * IX + 1, 2 * IY, nxf);
+  const int64_t ic = bf + st_of(2 * IX, 2 * IY + 1, nxf), id = bf + st_of(2 * IX + 1, 2 * IY + 1, nxf);
+  auto ld = [&](int k, int64_t i) { return Jf[k * plane_f + i]; };
+  auto add = [](B4& acc, const B4& v) { acc.a00 += v.a00; acc.a01 += v.a01; acc.a10 += v.a10; acc.a11 += v.a11; };
+  B4 C = ld(0, ia);
+  add(C, ld(0, ib)); add(C, ld(0, ic)); add(C, ld(0, id));
+  add(C, ld(2, ia)); add(C, ld(1, ib)); add(C, ld(2, ic)); add(C, ld(1, id));
+  add(C, ld(4, ia)); add(C, ld(3, ic)); add(C, ld(4, ib)); add(C, ld(3, id));
+  B4 W = ld(1, ia); add(W, ld(1, ic));
+  B4 E = ld(2, ib); add(E, ld(2, id));
+  B4 S = ld(3, ia); add(S, ld(3, ib));
+  B4 Nn = ld(4, ic); add(Nn, ld(4, id));
+  Jc[e] = C;
+  Jc[plane_c + e] = W;
+  Jc[2 * plane_c + e] = E;
+  Jc[3 * plane_c + e] = S;
+  Jc[4 * plane_c + e] = Nn;
+  const double a = C.a00, b = C.a01, c = C.a10, d = C.a11;
+  const double idet = 1.0 / (a * d - b * c);
+  Jc[5 * plane_c + e] = mkblk<B4>(d * idet, -b * idet, -c * idet, a * idet);
+}
+
+// Coarsest grid (2 x 1 cells, 4 unknowns): explicit inverse per sample by
+// Gauss-Jordan elimination with partial pivoting in FP64.
+template <typename T>
+__global__ void k_coarse_inverse(int B, const typename VT<T>::b4* __restrict__ J, int64_t plane,
+                                 T* __restrict__ Ainv, const int* __restrict__ active) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B || !active[s]) return;
+  // cells: st 0 = (0,0) colour 0, st 1 = (1,0) colour 1
+  const int64_t a = (int64_t)s * 2, b = a + 1;
+  const auto Ca = J[a], Ea = J[2 * plane + a], Wb = J[plane + b], Cb = J[b];
+  double M[4][8];
+  const double blk[4][4] = {{Ca.a00, Ca.a01, Ea.a00, Ea.a01},
+                            {Ca.a10, Ca.a11, Ea.a10, Ea.a11},
+                            {Wb.a00, Wb.a01, Cb.a00, Cb.a01},
+                            {Wb.a10, Wb.a11, Cb.a10, Cb.a11}};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      M[i][j] = blk[i][j];
+      M[i][4 + j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+    if (piv != col)
+      for (int j = 0; j < 8; ++j) {
+        const double t = M[col][j];
+        M[col][j] = M[piv][j];
+        M[piv][j] = t;
+      }
+    const double inv = 1.0 / M[col][col];
+    for (int j = 0; j < 8; ++j) M[col][j] *= inv;
+    for (int r = 0; r < 4; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col];
+      for (int j = 0; j < 8; ++j) M[r][j] -= f * M[col][j];
+    }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) Ainv[(int64_t)s * 16 + i * 4 + j] = (T)M[i][4 + j];
+}
+
+template <typename T>
+__global__ void k_coarse_solve(int B, const T* __restrict__ Ainv, const typename VT<T>::v2* __restrict__ b,
+                               typename VT<T>::v2* __restrict__ x, const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B || !active[s]) return;
+  const V2 b0 = b[2 * (int64_t)s], b1 = b[2 * (int64_t)s + 1];
+  const T v[4] = {b0.x, b0.y, b1.x, b1.y};
+  const T* M = Ainv + (int64_t)s * 16;
+  T o[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o[i] = M[4 * i] * v[0] + M[4 * i + 1] * v[1] + M[4 * i + 2] * v[2] + M[4 * i + 3] * v[3];
+  x[2 * (int64_t)s] = mk2<V2>(o[0], o[1]);
+  x[2 * (int64_t)s + 1] = mk2<V2>(o[2], o[3]);
+}
+
+// a7: one half-sweep of red-black point-block Gauss-Seidel over colour `col`:
+//   x_P = C_P^{-1} (b_P - sum_nb A_nb x_nb).
+// MODE 0: x = 0 before the sweep (first pre-smoothing sweep: x_P = C_P^{-1} b_P).
+// MODE 1: plain sweep.
+// MODE 2: first post-smoothing sweep right after the coarse-grid correction:
+//         the neighbours' values are read as x_nb + x_c(parent(nb)), which is
+//         x += P x_c followed by the sweep (the swept cells' own old values do
+//         not enter point Gauss-Seidel, and the other colour is overwritten by
+//         the next half-sweep).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, const typename VT<T>::b4* __restrict__ J,
+                                               int64_t plane, const typename VT<T>::v2* __restrict__ b,
+                                               typename VT<T>::v2* __restrict__ x,
+                                               const typename VT<T>::v2* __restrict__ xc,
+                                               const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  const int N = nx * ny, halfN = N >> 1, half = nx >> 1;
+  const int64_t t = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (t >= (int64_t)B * halfN) return;
+  const int s = (int)(t / halfN);
+  if (!active[s]) return;
+  const int u = (int)(t - (int64_t)s * halfN);
+  const int iy = u / half, j = u - iy * half;
+  const int ix = 2 * j + ((col ^ iy) & 1);
+  const int64_t base = (int64_t)s * N;
+  const int64_t e = base + iy * nx + col * half + j;
+  const V2 bb = b[e];
+  T r0 = bb.x, r1 = bb.y;
+  if (MODE != 0) {
+    const int ncx = nx >> 1;
+    const int64_t basec = (int64_t)s * (N >> 2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+      const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+      if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+      V2 xn = x[base + st_of(jx, jy, nx)];
+      if (MODE == 2) {
+        const V2 cc = xc[basec + st_of(jx >> 1, jy >> 1, ncx)];
+        xn.x += cc.x;
+        xn.y += cc.y;
+      }
+      bmv_sub(J[(k + 1) * plane + e], xn.x, xn.y, r0, r1);
+    }
+  }
+  const B4 Ci = J[5 * plane + e];
+  x[e] = mk2<V2>(Ci.a00 * r0 + Ci.a01 * r1, Ci.a10 * r0 + Ci.a11 * r1);
+}
+
+// Residual b - A x restricted by summation over the 2x2 children.  After a
+// red-black sweep the black cells' residuals vanish (point Gauss-Seidel makes
+// each swept equation hold), so RED_ONLY sums the two colour-0 children only;
+// ZERO_X (no pre-smoothing, x = 0) restricts b itself.
+template <typename T, int MODE>  // MODE 0: RED_ONLY, 1: ZERO_X
+__global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int ncy,
+                                                           const typename VT<T>::b4* __restrict__ J, int64_t plane,
+                                                           const typename VT<T>::v2* __restrict__ b,
+                                                           const typename VT<T>::v2* __restrict__ x,
+                                                           typename VT<T>::v2* __restrict__ bc,
+                                                           const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  const int Nc = ncx * ncy;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * Nc) return;
+  const int s = (int)(e / Nc);
+  if (!active[s]) return;
+  const int stc = (int)(e - (int64_t)s * Nc);
+  int IX, IY;
+  xy_of(stc, ncx, IX, IY);
+  const int nx = 2 * ncx, ny = 2 * ncy;
+  const int64_t base = (int64_t)s * Nc * 4;
+  T s0 = 0, s1 = 0;
+  if (MODE == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const V2 bb = b[base + st_of(2 * IX + (c & 1), 2 * IY + (c >> 1), nx)];
+      s0 += bb.x;
+      s1 += bb.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int ix = 2 * IX + c, iy = 2 * IY + c;  // (0,0) and (1,1): colour 0
+      const int64_t i = base + st_of(ix, iy, nx);
+      const V2 bb = b[i], xx = x[i];
+      T r0 = bb.x, r1 = bb.y;
+      bmv_sub(J[i], xx.x, xx.y, r0, r1);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+        const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+        if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+        const V2 xn = x[base + st_of(jx, jy, nx)];
+        bmv_sub(J[(k + 1) * plane + i], xn.x, xn.y, r0, r1);
+      }
+      s0 += r0;
+      s1 += r1;
+    }
+  }
+  bc[e] = mk2<V2>(s0, s1);
+}
+
+// x += P x_c (used only when there is no post-smoothing to fuse it into).
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_prolong_add(int B, int nx, int ny, typename VT<T>::v2* __restrict__ x,
+                                                     const typename VT<T>::v2* __restrict__ xc,
+                                                     const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int s = (int)(e / N);
+  if (!active[s]) return;
+  int ix, iy;
+  xy_of((int)(e - (int64_t)s * N), nx, ix, iy);
+  const V2 c = xc[(int64_t)s * (N >> 2) + st_of(ix >> 1, iy >> 1, nx >> 1)];
+  V2 v = x[e];
+  v.x += c.x;
+  v.y += c.y;
+  x[e] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_zero(int64_t n, typename VT<T>::v2* __restrict__ x) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e < n) x[e] = mk2<typename VT<T>::v2>((T)0, (T)0);
+}
+
+// ---------------------------------------------------------------------------
+// a8: y = A x (fine level, all cells) with per-CTA partial dot products:
+//   NDOT 1: <w1, y>;  NDOT 2: <w1, y>, <y, y>.
+template <typename T, int NDOT>
+__global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typename VT<T>::b4* __restrict__ J,
+                                              int64_t plane, const typename VT<T>::v2* __restrict__ x,
+                                              typename VT<T>::v2* __restrict__ y,
+                                              const typename VT<T>::v2* __restrict__ w1, double* __restrict__ part,
+                                              int slot1, int slot2, const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  __shared__ double sh[40];
+  const int N = nx * ny, nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!active[s]) return;  // uniform over the CTA
+  const int st = (int)(e - (int64_t)s * N);
+  int ix, iy;
+  xy_of(st, nx, ix, iy);
+  const int64_t base = e - st;
+  const V2 xx = x[e];
+  T r0 = 0, r1 = 0;
+  bmv_add(J[e], xx.x, xx.y, r0, r1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const V2 xn = x[base + st_of(jx, jy, nx)];
+    bmv_add(J[(k + 1) * plane + e], xn.x, xn.y, r0, r1);
+  }
+  y[e] = mk2<V2>(r0, r1);
+  if (NDOT >= 1 && part) {
+    const V2 ww = w1[e];
+    double d1 = (double)ww.x * (double)r0 + (double)ww.y * (double)r1;
+    d1 = block_reduce<false>(d1, sh);
+    double d2 = 0.0;
+    if (NDOT == 2) d2 = block_reduce<false>((double)r0 * (double)r0 + (double)r1 * (double)r1, sh);
+    if (threadIdx.x == 0) {
+      const int64_t pi = (int64_t)s * nct + st / TPB, stride = (int64_t)B * nct;
+      part[slot1 * stride + pi] = d1;
+      if (NDOT == 2) part[slot2 * stride + pi] = d2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: right-preconditioned BiCGStab (Templates book), per sample, on the fine
+// level; per-sample scalars live in LinScal, per-CTA partial sums in part.
+
+// r = r_hat = b (= -F), p = v = dx = 0; partials <r_hat, r>, <r, r>.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_bicg_init(int B, int N, const double2* __restrict__ F,
+                                                   typename VT<T>::v2* __restrict__ r,
+                                                   typename VT<T>::v2* __restrict__ rh,
+                                                   typename VT<T>::v2* __restrict__ p, typename VT<T>::v2* __restrict__ v,
+                                                   typename VT<T>::v2* __restrict__ dx, double* __restrict__ part,
+                                                   const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  __shared__ double sh[40];
+  const int nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!active[s]) return;
+  const double2 f = F[e];
+  const V2 rr = mk2<V2>((T)(-f.x), (T)(-f.y));
+  const V2 z = mk2<V2>((T)0, (T)0);
+  r[e] = rr;
+  rh[e] = rr;
+  p[e] = z;
+  v[e] = z;
+  dx[e] = z;
+  const double d = (double)rr.x * (double)rr.x + (double)rr.y * (double)rr.y;
+  const double bs = block_reduce<false>(d, sh);
+  if (threadIdx.x == 0) {
+    const int64_t pi = (int64_t)s * nct + (e - (int64_t)s * N) / TPB, stride = (int64_t)B * nct;
+    part[P_RR * stride + pi] = bs;
+    part[P_RN * stride + pi] = bs;
+  }
+}
+
+// Start of iteration `it`: rho_it = <r_hat, r>, convergence test on ||r||,
+// beta = (rho_it / rho_{it-1}) (alpha / omega), p = r + beta (p - omega v).
+// A converged sample's CTA 0 clears lin_active; the last iteration counts
+// still-active samples in *n_active and per-sample iterations in iters.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_bicg_p(int B, int N, int it, int maxit, double rtol2,
+                                                const typename VT<T>::v2* __restrict__ r,
+                                                typename VT<T>::v2* __restrict__ p,
+                                                const typename VT<T>::v2* __restrict__ v,
+                                                const double* __restrict__ part, LinScal* __restrict__ sc,
+                                                int* __restrict__ lin_active, int* __restrict__ iters,
+                                                int* __restrict__ status, int* __restrict__ n_active,
+                                                unsigned long long* __restrict__ lin_total) {
+  typedef typename VT<T>::v2 V2;
+  __shared__ double sh[40];
+  const int nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!lin_active[s]) return;
+  const int ct = (int)((e - (int64_t)s * N) / TPB);
+  const int64_t stride = (int64_t)B * nct;
+  const double rho = sample_sum(part + P_RR * stride + (int64_t)s * nct, nct, sh);
+  const double rn2 = sample_sum(part + P_RN * stride + (int64_t)s * nct, nct, sh);
+  const double bn2 = (it == 0) ? rn2 : sc[s].bnorm2;
+  const bool finite = (rn2 <= 1.0e300) && (rho == rho);
+  if (!finite || rn2 <= rtol2 * bn2 || it >= maxit) {
+    // A sample that reaches maxit keeps its last iterate (inexact Newton
+    // step; Newton's own test decides); a non-finite one fails.
+    if (threadIdx.x == 0 && ct == 0) {
+      lin_active[s] = 0;
+      iters[s] = (finite && rn2 <= rtol2 * bn2) ? it : -1;
+      if (!finite) status[s] = 3;
+      atomicAdd(lin_total, (unsigned long long)it);
+    }
+    return;
+  }
+  if (threadIdx.x == 0 && ct == 0) {
+    atomicAdd(n_active, 1);
+    if (it == 0) sc[s].bnorm2 = bn2;
+  }
+  const V2 rr = r[e];
+  if (it == 0) {
+    p[e] = rr;
+    return;
+  }
+  const LinScal q = sc[s];
+  const double beta = (rho / q.rho) * (q.alpha / q.omega);
+  const V2 pp = p[e], vv = v[e];
+  const T bt = (T)beta, om = (T)q.omega;
+  p[e] = mk2<V2>(rr.x + bt * (pp.x - om * vv.x), rr.y + bt * (pp.y - om * vv.y));
+}
+
+// alpha = rho / <r_hat, v>; s = r - alpha v.  CTA 0 stores rho and alpha.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_bicg_s(int B, int N, const typename VT<T>::v2* __restrict__ r,
+                                                const typename VT<T>::v2* __restrict__ v,
+                                                typename VT<T>::v2* __restrict__ sv, const double* __restrict__ part,
+                                                LinScal* __restrict__ sc, const int* __restrict__ lin_active) {
+  typedef typename VT<T>::v2 V2;
+  __shared__ double sh[40];
+  const int nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!lin_active[s]) return;
+  const int ct = (int)((e - (int64_t)s * N) / TPB);
+  const int64_t stride = (int64_t)B * nct;
+  const double rho = sample_sum(part + P_RR * stride + (int64_t)s * nct, nct, sh);
+  const double rv = sample_sum(part + P_RV * stride + (int64_t)s * nct, nct, sh);
+  const double alpha = rho / rv;
+  if (threadIdx.x == 0 && ct == 0) {
+    sc[s].rho = rho;
+    sc[s].alpha = alpha;
+  }
+  const V2 rr = r[e], vv = v[e];
+  const T a = (T)alpha;
+  sv[e] = mk2<V2>(rr.x - a * vv.x, rr.y - a * vv.y);
+}
+
+// omega = <t, s> / <t, t>; dx += alpha p_hat + omega s_hat; r = s - omega t;
+// partials <r_hat, r>, <r, r>.  CTA 0 stores omega.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T>::v2* __restrict__ dx,
+                                                     const typename VT<T>::v2* __restrict__ ph,
+                                                     const typename VT<T>::v2* __restrict__ shv,
+                                                     const typename VT<T>::v2* __restrict__ sv,
+                                                     const typename VT<T>::v2* __restrict__ t,
+                                                     const typename VT<T>::v2* __restrict__ rh,
+                                                     typename VT<T>::v2* __restrict__ r, double* __restrict__ part,
+                                                     LinScal* __restrict__ sc, const int* __restrict__ lin_active) {
+  typedef typename VT<T>::v2 V2;
+  __shared__ double sh[40];
+  const int nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!lin_active[s]) return;
+  const int ct = (int)((e - (int64_t)s * N) / TPB);
+  const int64_t stride = (int64_t)B * nct;
+  const double ts = sample_sum(part + P_TS * stride + (int64_t)s * nct, nct, sh);
+  const double tt = sample_sum(part + P_TT * stride + (int64_t)s * nct, nct, sh);
+  const double omega = (tt > 0.0) ? ts / tt : 0.0;
+  const double alpha = sc[s].alpha;
+  if (threadIdx.x == 0 && ct == 0) sc[s].omega = omega;
+  const T a = (T)alpha, w = (T)omega;
+  const V2 x0 = dx[e], p0 = ph[e], s0 = shv[e], sv0 = sv[e], t0 = t[e], rh0 = rh[e];
+  dx[e] = mk2<V2>(x0.x + a * p0.x + w * s0.x, x0.y + a * p0.y + w * s0.y);
+  const V2 rn = mk2<V2>(sv0.x - w * t0.x, sv0.y - w * t0.y);
+  r[e] = rn;
+  const double d1 = block_reduce<false>((double)rh0.x * (double)rn.x + (double)rh0.y * (double)rn.y, sh);
+  const double d2 = block_reduce<false>((double)rn.x * (double)rn.x + (double)rn.y * (double)rn.y, sh);
+  if (threadIdx.x == 0) {
+    const int64_t pi = (int64_t)s * nct + ct;
+    part[P_RR * stride + pi] = d1;
+    part[P_RN * stride + pi] = d2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a9 / a10: Newton control.
+
+// Per sample, after the fine assembly: converged if max |F| <= atol; a
+// non-finite residual fails the sample; counts samples still iterating.
+__global__ void k_newton_res_check(int B, int nct, double atol, int maxit, const double* __restrict__ rmax_part,
+                                   int* __restrict__ newton_active, int* __restrict__ lin_active,
+                                   int* __restrict__ newton_it, int* __restrict__ status,
+                                   int* __restrict__ n_active, unsigned long long* __restrict__ it_total) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  int act = newton_active[s];
+  if (act) {
+    const double rm = sample_max(rmax_part + (int64_t)s * nct, nct);
+    if (!(rm <= 1.0e300)) {
+      status[s] = 3;
+      act = 0;
+    } else if (rm <= atol) {
+      act = 0;
+    } else if (newton_it[s] >= maxit) {
+      status[s] = status[s] ? status[s] : 1;
+      act = 0;
+    } else {
+      newton_it[s] += 1;
+      atomicAdd(n_active, 1);
+      atomicAdd(it_total, 1ULL);
+    }
+  }
+  newton_active[s] = act;
+  lin_active[s] = act;
+}
+
+// x += dx (FP64 state), per-CTA max of the scaled update.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_newton_update(int B, int N, double inv_pref, double2* __restrict__ x,
+                                                       const typename VT<T>::v2* __restrict__ dx,
+                                                       double* __restrict__ dmax_part,
+                                                       const int* __restrict__ newton_active) {
+  __shared__ double sh[40];
+  const int nct = N / TPB;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!newton_active[s]) return;
+  const auto d = dx[e];
+  double2 xx = x[e];
+  xx.x += (double)d.x;
+  xx.y += (double)d.y;
+  x[e] = xx;
+  double loc = fmax(fabs((double)d.x) * inv_pref, fabs((double)d.y));
+  if (!(loc <= 1.0e300)) loc = INFINITY;
+  const double m = block_reduce<true>(loc, sh);
+  if (threadIdx.x == 0) dmax_part[(int64_t)s * nct + (e - (int64_t)s * N) / TPB] = m;
+}
+
+__global__ void k_newton_dx_check(int B, int nct, double dxtol, const double* __restrict__ dmax_part,
+                                  int* __restrict__ newton_active, int* __restrict__ status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B || !newton_active[s]) return;
+  const double dm = sample_max(dmax_part + (int64_t)s * nct, nct);
+  if (!(dm <= 1.0e300)) {
+    status[s] = 3;
+    newton_active[s] = 0;
+  } else if (dm <= dxtol) {
+    newton_active[s] = 0;
+  }
+}
+
+// Start of a time step: old state = state; samples that have not failed iterate.
+__global__ void __launch_bounds__(TPB) k_step_begin(int64_t n, const double2* __restrict__ x, double2* __restrict__ xo) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e < n) xo[e] = x[e];
+}
+__global__ void k_step_flags(int B, const int* __restrict__ status, int* __restrict__ newton_active,
+                             int* __restrict__ newton_it) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  newton_active[s] = status[s] == 0 ? 1 : 0;
+  newton_it[s] = 0;
+}
+
+}  // namespace hk

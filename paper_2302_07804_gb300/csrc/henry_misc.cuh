@@ -1,0 +1,206 @@
+// Sampling, coefficients, initial state, QoIs, layout conversion and the
+// MLMC accumulation kernels (sm_103a).
+#pragma once
+#include "henry_kernels.cuh"
+
+namespace hk {
+
+// ---------------------------------------------------------------------------
+// a1: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64-bit multiplications whose high halves are XORed with the other
+// two counter words and the round key; the key advances by the Weyl
+// increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k.x += W0;
+      k.y += W1;
+    }
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+// Two words -> (2u + 1 - 2^52) 2^-52 with u = (w0 << 20) | (w1 >> 12): an odd
+// multiple of 2^-52 in (-1, 1), formed exactly in integers.
+__device__ __forceinline__ double words_to_unit(uint32_t w0, uint32_t w1) {
+  const int64_t u = ((int64_t)w0 << 20) | (int64_t)(w1 >> 12);
+  const int64_t k = 2 * u + 1 - ((int64_t)1 << 52);
+  return (double)k * 0x1p-52;
+}
+__global__ void k_sample_xi(uint64_t seed, int level, uint64_t first, int n, double* __restrict__ xi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t sidx = first + (uint64_t)i;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint4 a = philox4x32_10(make_uint4((uint32_t)level, (uint32_t)sidx, (uint32_t)(sidx >> 32), 0u), key);
+  const uint4 b = philox4x32_10(make_uint4((uint32_t)level, (uint32_t)sidx, (uint32_t)(sidx >> 32), 1u), key);
+  xi[3 * (int64_t)i + 0] = words_to_unit(a.x, a.y);
+  xi[3 * (int64_t)i + 1] = words_to_unit(a.z, a.w);
+  xi[3 * (int64_t)i + 2] = words_to_unit(b.x, b.y);
+}
+
+// a2: phi = phi_mean (1 + phi_amp xi1), K = K_mean exp(logK_amp xi2),
+// q_in = qin_mean (1 + qin_amp xi3); stored as (phi, K / mu, phi Dm, q_in).
+struct CoefModel {
+  double phi_mean, K_mean, qin_mean, phi_amp, logK_amp, qin_amp, mu, Dm;
+};
+__global__ void k_coefficients(CoefModel m, int n, const double* __restrict__ xi, Coef* __restrict__ coef,
+                               int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x1 = xi[3 * (int64_t)i], x2 = xi[3 * (int64_t)i + 1], x3 = xi[3 * (int64_t)i + 2];
+  Coef c;
+  c.phi = m.phi_mean * (1.0 + m.phi_amp * x1);
+  const double K = m.K_mean * exp(m.logK_amp * x2);
+  c.kmu = K / m.mu;
+  c.PD = c.phi * m.Dm;
+  c.qin = m.qin_mean * (1.0 + m.qin_amp * x3);
+  coef[i] = c;
+  const bool ok = (c.phi > 0.0) && (c.phi < 1.0) && (K > 0.0) && (K <= 1.0e300) && (c.qin == c.qin) &&
+                  (fabs(c.qin) <= 1.0e300);
+  status[i] = ok ? 0 : 3;
+}
+
+// a3: c = 0 and fresh-water hydrostatic pressure rho0 g (Ly - y).
+__global__ void __launch_bounds__(TPB) k_init_state(int B, int nx, int ny, double h, double rho0g, double Ly,
+                                                    double2* __restrict__ x) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int st = (int)(e % N);
+  const int iy = st / nx;
+  x[e] = make_double2(rho0g * (Ly - (iy + 0.5) * h), 0.0);
+}
+
+// a11: QoIs, one CTA per sample: salt mass sum phi rho c h^2 and c at
+// (1.5, 0.25) = mean of the cells (ix0, iy0), (ix0+1, iy0), (ix0, iy0+1),
+// (ix0+1, iy0+1) with ix0 = 1.5 / h - 1, iy0 = 0.25 / h - 1.
+__global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, double rho0, double drho,
+                                             const Coef* __restrict__ coef, const double2* __restrict__ x,
+                                             double* __restrict__ qoi) {
+  __shared__ double sh[40];
+  const int s = blockIdx.x;
+  const int N = nx * ny;
+  const double2* xs = x + (int64_t)s * N;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double c = xs[i].y;
+    acc += (rho0 + drho * c) * c;
+  }
+  acc = block_reduce<false>(acc, sh);
+  if (threadIdx.x == 0) {
+    const int ix0 = (3 * ny) / 2 - 1, iy0 = ny / 4 - 1;
+    const double c00 = xs[st_of(ix0, iy0, nx)].y, c10 = xs[st_of(ix0 + 1, iy0, nx)].y;
+    const double c01 = xs[st_of(ix0, iy0 + 1, nx)].y, c11 = xs[st_of(ix0 + 1, iy0 + 1, nx)].y;
+    qoi[2 * (int64_t)s] = coef[s].phi * acc * h * h;
+    qoi[2 * (int64_t)s + 1] = 0.25 * (((c00 + c10) + c01) + c11);
+  }
+}
+
+// Natural layout [B][ny][nx] <-> storage layout (colour-split rows).
+template <typename V2>
+__global__ void __launch_bounds__(TPB) k_to_storage(int B, int nx, int ny, const double2* __restrict__ in,
+                                                    V2* __restrict__ out) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int64_t s = e / N;
+  const int nat = (int)(e - s * N);
+  const int iy = nat / nx, ix = nat - iy * nx;
+  const double2 v = in[e];
+  V2 o;
+  o.x = v.x;
+  o.y = v.y;
+  out[s * N + st_of(ix, iy, nx)] = o;
+}
+template <typename V2>
+__global__ void __launch_bounds__(TPB) k_from_storage(int B, int nx, int ny, const V2* __restrict__ in,
+                                                      double2* __restrict__ out) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int64_t s = e / N;
+  const int nat = (int)(e - s * N);
+  const int iy = nat / nx, ix = nat - iy * nx;
+  const V2 v = in[s * N + st_of(ix, iy, nx)];
+  out[e] = make_double2((double)v.x, (double)v.y);
+}
+// Jacobian planes -> natural [B][ny][nx][5][2][2] FP64.
+template <typename B4>
+__global__ void __launch_bounds__(TPB) k_blocks_out(int B, int nx, int ny, const B4* __restrict__ J, int64_t plane,
+                                                    double* __restrict__ out) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int64_t s = e / N;
+  const int nat = (int)(e - s * N);
+  const int iy = nat / nx, ix = nat - iy * nx;
+  const int64_t src = s * N + st_of(ix, iy, nx);
+  for (int k = 0; k < 5; ++k) {
+    const B4 b = J[k * plane + src];
+    double* o = out + e * 20 + 4 * k;
+    o[0] = (double)b.a00;
+    o[1] = (double)b.a01;
+    o[2] = (double)b.a10;
+    o[3] = (double)b.a11;
+  }
+}
+
+__global__ void __launch_bounds__(TPB) k_scale_d2(int64_t n, double a, double2* __restrict__ x) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e < n) {
+    double2 v = x[e];
+    x[e] = make_double2(a * v.x, a * v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a12: MLMC accumulation, one CTA.  For each (quantity, QoI): the batch's
+// count, mean and centred sum of squares M2 (two passes over the batch), then
+// Chan's pairwise merge into the running (count, mean, M2).
+__global__ void __launch_bounds__(1024) k_mlmc_accumulate(int n, int n_qoi, const double* __restrict__ qf,
+                                                          const double* __restrict__ qc,
+                                                          const int32_t* __restrict__ status,
+                                                          double* __restrict__ sums) {
+  __shared__ double sh[40];
+  for (int which = 0; which < 2; ++which) {
+    for (int q = 0; q < n_qoi; ++q) {
+      double cnt = 0.0, sum = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (status && status[i] != 0) continue;
+        double y = qf[(int64_t)i * n_qoi + q];
+        if (which == 0 && qc) y -= qc[(int64_t)i * n_qoi + q];
+        cnt += 1.0;
+        sum += y;
+      }
+      cnt = block_reduce<false>(cnt, sh);
+      sum = block_reduce<false>(sum, sh);
+      if (cnt == 0.0) continue;
+      const double mb = sum / cnt;
+      double m2 = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (status && status[i] != 0) continue;
+        double y = qf[(int64_t)i * n_qoi + q];
+        if (which == 0 && qc) y -= qc[(int64_t)i * n_qoi + q];
+        m2 += (y - mb) * (y - mb);
+      }
+      m2 = block_reduce<false>(m2, sh);
+      if (threadIdx.x == 0) {
+        double* S = sums + ((int64_t)which * n_qoi + q) * 3;
+        const double na = S[0], ma = S[1], m2a = S[2];
+        const double nn = na + cnt;
+        const double d = mb - ma;
+        S[0] = nn;
+        S[1] = ma + d * (cnt / nn);
+        S[2] = m2a + m2 + d * d * (na * cnt / nn);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace hk

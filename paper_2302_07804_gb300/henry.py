@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libhenry (include/henry.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+turns torch tensors into device pointers and the current CUDA stream into a
+``cudaStream_t``.  There is no CPU fallback: ``lib()`` raises if the library
+is missing or cannot be loaded.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhenry.so")
+
+HENRY_OK, HENRY_EINVAL, HENRY_ECUDA, HENRY_ENOMEM, HENRY_ENOCONV, HENRY_ELIMIT = range(6)
+HENRY_SAMPLE_OK, HENRY_SAMPLE_NEWTON, HENRY_SAMPLE_LINEAR, HENRY_SAMPLE_NONFINITE = range(4)
+HENRY_FP64, HENRY_MIXED = 0, 1
+HENRY_COARSE_REDISCRETISE, HENRY_COARSE_GALERKIN = 0, 1
+N_QOI = 2
+N_XI = 3
+
+EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
+           "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
+           "henry_apply_jacobian", "henry_precondition", "henry_linear_solve")
+
+
+class HenryConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("Lx", "Ly", "T", "rho0", "rho1", "mu", "g", "Dm")] + \
+               [(n, ctypes.c_double) for n in ("phi_mean", "K_mean", "qin_mean")] + \
+               [(n, ctypes.c_double) for n in ("phi_amp", "logK_amp", "qin_amp")] + \
+               [(n, ctypes.c_int32) for n in ("nx0", "ny0", "steps0", "max_level", "precision", "coarse_op")] + \
+               [(n, ctypes.c_double) for n in ("newton_atol", "newton_dxtol", "lin_rtol")] + \
+               [(n, ctypes.c_int32) for n in ("newton_maxit", "lin_maxit", "nu1", "nu2")] + \
+               [("workspace_bytes", ctypes.c_double)]
+
+
+class HenryStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int64), ("linear_iters", ctypes.c_int64),
+                ("newton_solves", ctypes.c_int64), ("failed_samples", ctypes.c_int64),
+                ("cell_steps", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HenryError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libhenry error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libhenry.so (built by ``paper_2302_07804_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhenry.so is not built (%s); run paper_2302_07804_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        U64 = ctypes.c_uint64
+        L.henry_default_config.argtypes = [ctypes.POINTER(HenryConfig)]
+        L.henry_default_config.restype = None
+        L.henry_create.argtypes = [ctypes.POINTER(HenryConfig), ctypes.POINTER(P)]
+        L.henry_destroy.argtypes = [P]
+        L.henry_destroy.restype = None
+        L.henry_last_error.restype = ctypes.c_char_p
+        L.henry_sample_xi.argtypes = [U64, I, U64, I, P, P]
+        L.henry_level_batch_solve.argtypes = [P, I, I, P, I, P, P, P, ctypes.POINTER(HenryStats), P]
+        L.mlmc_accumulate.argtypes = [I, I, I, P, P, P, P, P]
+        L.mlmc_allocate.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(D), D, ctypes.POINTER(I64)]
+        L.henry_assemble.argtypes = [P, I, P, I, P, P, P, P, P]
+        L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
+        L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
+        L.henry_linear_solve.argtypes = [P, I, P, I, P, P, P, P, P, P]
+        for name in EXPORTS:
+            f = getattr(L, name)
+            if name not in ("henry_default_config", "henry_destroy", "henry_last_error"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc, allow=()):
+    if rc != HENRY_OK and rc not in allow:
+        raise HenryError(rc, lib().henry_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, shape=None):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return t
+
+
+def default_config(**overrides):
+    cfg = HenryConfig()
+    lib().henry_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def sample_xi(seed, level, first_sample, n, device="cuda", stream=None):
+    """xi[n][3] on the device from Philox4x32-10 (henry_sample_xi)."""
+    xi = torch.empty((n, N_XI), dtype=torch.float64, device=device)
+    _check(lib().henry_sample_xi(seed, level, first_sample, n, _ptr(xi), _stream(stream)))
+    return xi
+
+
+def mlmc_accumulate(level, qoi_fine, qoi_coarse, status, sums, stream=None):
+    """Merge a batch into sums[2][n_qoi][3] (count, mean, M2) in place."""
+    n, nq = qoi_fine.shape
+    _dev_f64(qoi_fine)
+    _dev_f64(sums, (2, nq, 3))
+    if qoi_coarse is not None:
+        _dev_f64(qoi_coarse, (n, nq))
+    if status is not None and not (status.is_cuda and status.dtype == torch.int32):
+        raise ValueError("status must be an int32 CUDA tensor")
+    _check(lib().mlmc_accumulate(level, n, nq, _ptr(qoi_fine), _ptr(qoi_coarse), _ptr(status), _ptr(sums),
+                                 _stream(stream)))
+    return sums
+
+
+def mlmc_allocate(V, s, var_budget):
+    """Eq. (M_ell) sample numbers (host)."""
+    L = len(V)
+    Va = (ctypes.c_double * L)(*[float(v) for v in V])
+    sa = (ctypes.c_double * L)(*[float(v) for v in s])
+    out = (ctypes.c_int64 * L)()
+    _check(lib().mlmc_allocate(L, Va, sa, float(var_budget), out))
+    return [int(v) for v in out]
+
+
+class Solver:
+    """Owns a henry_handle; see include/henry.h for the semantics of each call."""
+
+    def __init__(self, **overrides):
+        self.cfg = default_config(**overrides)
+        h = ctypes.c_void_p()
+        _check(lib().henry_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().henry_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def grid(self, level):
+        return (self.cfg.ny0 << level, self.cfg.nx0 << level)
+
+    def level_batch_solve(self, level, xi, with_coarse=False, stream=None, allow_failures=False, out=None):
+        """Returns (qoi_fine[n][2], qoi_coarse[n][2] or None, status[n] int32, stats dict)."""
+        n = xi.shape[0]
+        _dev_f64(xi, (n, N_XI))
+        if out is None:
+            qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
+            qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
+            st = torch.empty((n,), dtype=torch.int32, device=xi.device)
+        else:
+            qf, qc, st = out
+        stats = HenryStats()
+        rc = lib().henry_level_batch_solve(self._h, level, 1 if with_coarse else 0, _ptr(xi), n, _ptr(qf), _ptr(qc),
+                                           _ptr(st), ctypes.byref(stats), _stream(stream))
+        _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
+        return qf, qc, st, stats.as_dict()
+
+    def _states(self, level, state, state_old):
+        ny, nx = self.grid(level)
+        n = state.shape[0]
+        _dev_f64(state, (n, ny, nx, 2))
+        _dev_f64(state_old, (n, ny, nx, 2))
+        return n, ny, nx
+
+    def assemble(self, level, xi, state, state_old, with_jacobian=True, stream=None):
+        n, ny, nx = self._states(level, state, state_old)
+        F = torch.empty((n, ny, nx, 2), dtype=torch.float64, device=state.device)
+        J = torch.empty((n, ny, nx, 5, 2, 2), dtype=torch.float64, device=state.device) if with_jacobian else None
+        _check(lib().henry_assemble(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(F), _ptr(J),
+                                    _stream(stream)))
+        return F, J
+
+    def apply_jacobian(self, level, xi, state, state_old, x, stream=None):
+        n, ny, nx = self._states(level, state, state_old)
+        _dev_f64(x, (n, ny, nx, 2))
+        y = torch.empty_like(x)
+        _check(lib().henry_apply_jacobian(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(x),
+                                          _ptr(y), _stream(stream)))
+        return y
+
+    def precondition(self, level, xi, state, state_old, b, stream=None):
+        n, ny, nx = self._states(level, state, state_old)
+        _dev_f64(b, (n, ny, nx, 2))
+        z = torch.empty_like(b)
+        _check(lib().henry_precondition(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),
+                                        _ptr(z), _stream(stream)))
+        return z
+
+    def linear_solve(self, level, xi, state, state_old, b, stream=None):
+        n, ny, nx = self._states(level, state, state_old)
+        _dev_f64(b, (n, ny, nx, 2))
+        x = torch.empty_like(b)
+        its = torch.empty((n,), dtype=torch.int32, device=b.device)
+        _check(lib().henry_linear_solve(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),
+                                        _ptr(x), _ptr(its), _stream(stream)))
+        return x, its

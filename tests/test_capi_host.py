@@ -1,0 +1,82 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function include/henry.h declares; host-only calls (mlmc_allocate, argument
+validation) behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, golden_rows
+
+HEADER = os.path.join(ROOT, "include", "henry.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2302_07804_gb300 import build, henry
+    build.build()
+    return henry.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("henry_create", "henry_destroy", "henry_sample_xi", "henry_level_batch_solve",
+                     "mlmc_accumulate", "mlmc_allocate", "henry_last_error", "henry_assemble",
+                     "henry_apply_jacobian", "henry_precondition", "henry_linear_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_mlmc_allocate_reproduces_paper_table(L):
+    from paper_2302_07804_gb300 import henry
+    rows = golden_rows("paper_table_M_ell.txt")
+    s = [float(v) for v in rows[0][1:]]
+    V = [float(v) for v in rows[1][1:]]
+    for r in rows[2:]:
+        assert henry.mlmc_allocate(V, s, float(r[1])) == [int(v) for v in r[2:]]
+
+
+def test_mlmc_allocate_rejects_bad_input(L):
+    from paper_2302_07804_gb300 import henry
+    with pytest.raises(henry.HenryError) as e:
+        henry.mlmc_allocate([1e-5, 1e-6], [1.0, 0.0], 1e-6)
+    assert e.value.code == henry.HENRY_EINVAL
+    with pytest.raises(henry.HenryError):
+        henry.mlmc_allocate([1e-5], [1.0], 0.0)
+    assert henry.mlmc_allocate([0.0, 1e-6], [1.0, 2.0], 1e-6)[0] == 0
+
+
+def test_create_validates_config(L):
+    from paper_2302_07804_gb300 import henry
+    for bad in (dict(nx0=30), dict(ny0=12, nx0=24), dict(precision=7), dict(nu1=-1), dict(max_level=12),
+                dict(Lx=3.0)):
+        with pytest.raises(henry.HenryError) as e:
+            henry.Solver(**bad)
+        assert e.value.code == henry.HENRY_EINVAL
+
+
+def test_null_and_range_arguments_return_einval(L):
+    from paper_2302_07804_gb300 import henry
+    P = ctypes.c_void_p
+    assert L.henry_level_batch_solve(None, 0, 0, None, 1, None, None, None, None, None) == henry.HENRY_EINVAL
+    assert b"NULL" in L.henry_last_error()
+    s = henry.Solver()
+    assert L.henry_level_batch_solve(s._h, 9, 0, P(16), 1, P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert L.henry_level_batch_solve(s._h, 0, 0, P(16), 0, P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert L.henry_level_batch_solve(s._h, 0, 1, P(16), 4, P(16), P(16), P(16), None, None) == henry.HENRY_EINVAL
+    assert L.henry_sample_xi(1, 0, 0, 0, P(16), None) == henry.HENRY_EINVAL
+    assert L.mlmc_accumulate(0, 0, 2, P(16), None, None, P(16), None) == henry.HENRY_EINVAL
+    assert L.henry_assemble(s._h, -1, P(16), 1, P(16), P(16), P(16), None, None) == henry.HENRY_EINVAL
+    s.close()

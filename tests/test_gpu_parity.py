@@ -1,0 +1,298 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against
+the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64 path): per-step results agree to rounding (rtol 1e-11 on
+residual/Jacobian entries relative to the entry scale of the block row;
+1e-9 on a V-cycle, which multiplies rounding differences by the operator's
+amplification); QoIs of full scenario solves agree to 1e-10 relative (salt
+mass) and 1e-10 absolute (c at the point, a mass fraction in [0, 1]): both
+sides converge every Newton solve to the stopping rule's 1e-11 / 1e-12, far
+below that.  Philox xi and all index work are bit-exact.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import henry as ohenry
+from oracle import mg as omg
+from oracle import mlmc as omlmc
+from oracle import philox as ophilox
+from paper_2302_07804_gb300 import inputs
+
+PRM = ohenry.Params()
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def hl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_07804_gb300 import build, henry
+    build.build()
+    return henry
+
+
+@pytest.fixture(scope="module")
+def solver(hl):
+    s = hl.Solver()
+    yield s
+    s.close()
+
+
+def _to_dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _states_np(p, c):
+    return np.stack([p, c], axis=-1)
+
+
+@pytest.mark.parametrize("level,first", [(0, 0), (3, 12345), (5, (1 << 32) - 3)])
+def test_sample_xi_bit_exact(hl, level, first):
+    n = 257
+    xi = hl.sample_xi(inputs.SEED, level, first, n).cpu().numpy()
+    ref = ophilox.sample_xi(inputs.SEED, level, first, n)
+    assert np.array_equal(xi.view(np.uint64), ref.view(np.uint64))
+
+
+def _random_case(tag, level, n):
+    grid = ohenry.Grid.level(PRM, level)
+    xi = inputs.uniform_xi(tag, n)
+    p, c = inputs.random_states(tag, 2 * n, grid.ny, grid.nx, 5e3, 1e4, 300.0)
+    return grid, xi, p[:n], c[:n], p[n:], c[n:]
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_assemble_residual_and_jacobian(solver, level):
+    n = 3
+    grid, xi, p, c, po, co = _random_case(100 + level, level, n)
+    F, J = solver.assemble(level, _to_dev(xi), _to_dev(_states_np(p, c)), _to_dev(_states_np(po, co)))
+    F, J = F.cpu().numpy(), J.cpu().numpy()
+    s = ohenry.residual_scale(PRM, grid)
+    for i in range(n):
+        coef = ohenry.coefficients(PRM, grid, xi[i])
+        Rm, Rs = ohenry.residual(PRM, grid, coef, p[i], c[i], po[i], co[i])
+        Jo = omg.blocks_from_csr(ohenry.jacobian(PRM, grid, coef, p[i], c[i], po[i], co[i]), grid.nx, grid.ny) / s
+        Fo = np.stack([Rm, Rs], axis=-1) / s
+        # residual: cancellation of O(1e2) face fluxes -> compare to the flux scale
+        fscale = np.abs(Jo[..., 0, :, 0]).max() * 300.0 + 1.0
+        np.testing.assert_allclose(F[i], Fo, rtol=0, atol=1e-12 * fscale)
+        for eq in range(2):
+            for var in range(2):
+                row_scale = np.abs(Jo[..., eq, var]).max()
+                np.testing.assert_allclose(J[i][..., eq, var], Jo[..., eq, var], rtol=0, atol=1e-11 * row_scale)
+
+
+def test_assemble_mixed_precision_blocks(hl):
+    s32 = hl.Solver(precision=hl.HENRY_MIXED)
+    grid, xi, p, c, po, co = _random_case(120, 0, 2)
+    F, J = s32.assemble(0, _to_dev(xi), _to_dev(_states_np(p, c)), _to_dev(_states_np(po, co)))
+    s = ohenry.residual_scale(PRM, grid)
+    coef = ohenry.coefficients(PRM, grid, xi[0])
+    Jo = omg.blocks_from_csr(ohenry.jacobian(PRM, grid, coef, p[0], c[0], po[0], co[0]), grid.nx, grid.ny) / s
+    J = J.cpu().numpy()[0]
+    for eq in range(2):
+        for var in range(2):
+            np.testing.assert_allclose(J[..., eq, var], Jo[..., eq, var], rtol=0,
+                                       atol=1e-6 * np.abs(Jo[..., eq, var]).max())
+    Fo = np.stack(ohenry.residual(PRM, grid, coef, p[0], c[0], po[0], co[0]), axis=-1) / s
+    np.testing.assert_allclose(F.cpu().numpy()[0], Fo, rtol=0, atol=1e-9 * np.abs(Fo).max())  # F stays FP64
+    s32.close()
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_apply_jacobian(solver, level):
+    n = 2
+    grid, xi, p, c, po, co = _random_case(130 + level, level, n)
+    x = inputs.random_vectors(131, n, grid.ny, grid.nx)
+    y = solver.apply_jacobian(level, _to_dev(xi), _to_dev(_states_np(p, c)), _to_dev(_states_np(po, co)),
+                              _to_dev(x)).cpu().numpy()
+    s = ohenry.residual_scale(PRM, grid)
+    for i in range(n):
+        coef = ohenry.coefficients(PRM, grid, xi[i])
+        J = ohenry.jacobian(PRM, grid, coef, p[i], c[i], po[i], co[i]) / s
+        yo = (J @ x[i].ravel()).reshape(grid.ny, grid.nx, 2)
+        scale = np.abs(J).max() * np.abs(x[i]).max()
+        np.testing.assert_allclose(y[i], yo, rtol=0, atol=1e-12 * scale)
+
+
+def _trajectory(level, xi, steps):
+    grid = ohenry.Grid.level(PRM, level)
+    coef = ohenry.coefficients(PRM, grid, xi)
+    p, c = ohenry.initial_state(PRM, grid)
+    for _ in range(steps):
+        p, c, ok = ohenry.newton_step(PRM, grid, coef, p, c)
+        assert ok
+    return grid, coef, p, c
+
+
+@pytest.mark.parametrize("level,coarse_op", [(0, 0), (1, 0), (0, 1)])
+def test_vcycle_matches_oracle(hl, level, coarse_op):
+    s = hl.Solver(coarse_op=coarse_op)
+    xi = inputs.uniform_xi(140 + level, 2)
+    states, olds, ops = [], [], []
+    for i in range(2):
+        grid, coef, p, c = _trajectory(level, xi[i], 2 + i)
+        # Jacobian at a perturbed iterate of the next step
+        p1 = p + 5.0 * np.sin(np.arange(p.size).reshape(p.shape))
+        c1 = np.clip(c + 0.01, 0, 1)
+        states.append(_states_np(p1, c1))
+        olds.append(_states_np(p, c))
+        if coarse_op == 0:
+            ops.append(omg.rediscretised_hierarchy(PRM, grid, coef, p1, c1, p, c))
+        else:
+            A0 = omg.blocks_from_csr(ohenry.jacobian(PRM, grid, coef, p1, c1, p, c), grid.nx, grid.ny)
+            ops.append(omg.galerkin_hierarchy(A0 / ohenry.residual_scale(PRM, grid)))
+    b = inputs.random_vectors(141, 2, grid.ny, grid.nx)
+    z = s.precondition(level, _to_dev(xi), _to_dev(np.stack(states)), _to_dev(np.stack(olds)), _to_dev(b))
+    z = z.cpu().numpy()
+    for i in range(2):
+        zo = omg.vcycle(ops[i], b[i], s.cfg.nu1, s.cfg.nu2)
+        np.testing.assert_allclose(z[i], zo, rtol=0, atol=1e-9 * np.abs(zo).max())
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_linear_solve_reaches_tolerance(hl, precision):
+    s = hl.Solver(precision=precision, lin_rtol=1e-8 if precision == 0 else 1e-5)
+    level = 1
+    xi = inputs.uniform_xi(150, 2)
+    states, olds, Js = [], [], []
+    for i in range(2):
+        grid, coef, p, c = _trajectory(level, xi[i], 3)
+        states.append(_states_np(p, c))
+        olds.append(_states_np(p, c))
+        Js.append(ohenry.jacobian(PRM, grid, coef, p, c, p, c) / ohenry.residual_scale(PRM, grid))
+    b = inputs.random_vectors(151, 2, grid.ny, grid.nx)
+    x, its = s.linear_solve(level, _to_dev(xi), _to_dev(np.stack(states)), _to_dev(np.stack(olds)), _to_dev(b))
+    x, its = x.cpu().numpy(), its.cpu().numpy()
+    assert np.all(its > 0) and np.all(its <= 20), its
+    for i in range(2):
+        r = b[i].ravel() - Js[i] @ x[i].ravel()
+        rel = np.linalg.norm(r) / np.linalg.norm(b[i])
+        assert rel <= (1.5e-8 if precision == 0 else 5e-5), rel
+        xd = spla.spsolve(Js[i].tocsc(), b[i].ravel())
+        assert np.abs(x[i].ravel() - xd).max() <= (1e-5 if precision == 0 else 1e-2) * np.abs(xd).max()
+    s.close()
+
+
+def _qoi_check(q_gpu, q_ref):
+    np.testing.assert_allclose(q_gpu[:, 0], q_ref[:, 0], rtol=1e-10, atol=0)
+    np.testing.assert_allclose(q_gpu[:, 1], q_ref[:, 1], rtol=0, atol=1e-10)
+
+
+def test_level0_batch_solve_matches_oracle(hl, solver):
+    n = 16
+    xi_d = hl.sample_xi(inputs.SEED, 0, 0, n)
+    qf, qc, st, stats = solver.level_batch_solve(0, xi_d)
+    assert int(st.abs().sum()) == 0
+    xi = xi_d.cpu().numpy()
+    ref, ok = ohenry.solve_scenarios(PRM, 0, xi)
+    assert ok.all()
+    _qoi_check(qf.cpu().numpy(), ref)
+    assert stats["cell_steps"] == n * 512 * 20
+    assert stats["newton_iters"] >= n * 20 and stats["linear_iters"] > 0
+
+
+def test_level1_with_coarse_partner(hl, solver):
+    n = 3
+    xi_d = hl.sample_xi(inputs.SEED, 1, 40, n)
+    qf, qc, st, stats = solver.level_batch_solve(1, xi_d, with_coarse=True)
+    assert int(st.abs().sum()) == 0
+    xi = xi_d.cpu().numpy()
+    ref1, _ = ohenry.solve_scenarios(PRM, 1, xi)
+    ref0, _ = ohenry.solve_scenarios(PRM, 0, xi)
+    _qoi_check(qf.cpu().numpy(), ref1)
+    _qoi_check(qc.cpu().numpy(), ref0)
+    # the coarse partner equals an independent level-0 solve of the same xi, bit for bit
+    q0, _, _, _ = solver.level_batch_solve(0, xi_d)
+    assert torch.equal(q0, qc)
+    assert stats["cell_steps"] == n * (2048 * 40 + 512 * 20)
+
+
+def test_mixed_precision_solve_matches_oracle(hl):
+    s = hl.Solver(precision=hl.HENRY_MIXED, lin_rtol=1e-4)
+    n = 8
+    xi_d = hl.sample_xi(inputs.SEED, 0, 100, n)
+    qf, _, st, _ = s.level_batch_solve(0, xi_d)
+    assert int(st.abs().sum()) == 0
+    ref, _ = ohenry.solve_scenarios(PRM, 0, xi_d.cpu().numpy())
+    _qoi_check(qf.cpu().numpy(), ref)   # Newton on the FP64 residual reaches the same solution
+    s.close()
+
+
+def test_galerkin_option_solve_matches_oracle(hl):
+    s = hl.Solver(coarse_op=hl.HENRY_COARSE_GALERKIN)
+    xi_d = hl.sample_xi(inputs.SEED, 0, 200, 4)
+    qf, _, st, _ = s.level_batch_solve(0, xi_d)
+    assert int(st.abs().sum()) == 0
+    ref, _ = ohenry.solve_scenarios(PRM, 0, xi_d.cpu().numpy())
+    _qoi_check(qf.cpu().numpy(), ref)
+    s.close()
+
+
+def test_mlmc_accumulate_matches_two_pass(hl):
+    gen = inputs.rng(160)
+    qf = gen.normal(0.5, 0.1, size=(1000, 2))
+    qc = qf + gen.normal(0.0, 0.01, size=(1000, 2))
+    status = np.zeros(1000, dtype=np.int32)
+    status[::97] = 1
+    sums = torch.zeros((2, 2, 3), dtype=torch.float64, device=DEV)
+    st = torch.as_tensor(status, device=DEV)
+    # two batches merged must equal one two-pass computation over the union
+    hl.mlmc_accumulate(1, _to_dev(qf[:600]), _to_dev(qc[:600]), st[:600], sums)
+    hl.mlmc_accumulate(1, _to_dev(qf[600:]), _to_dev(qc[600:]), st[600:], sums)
+    keep = status == 0
+    y = omlmc.level_differences(qf[keep], qc[keep])
+    n, mean, m2 = omlmc.two_pass_moments(y)
+    S = sums.cpu().numpy()
+    assert S[0, 0, 0] == n
+    np.testing.assert_allclose(S[0, :, 1], mean, rtol=1e-13)
+    np.testing.assert_allclose(S[0, :, 2], m2, rtol=1e-10)
+    n1, mean1, m21 = omlmc.two_pass_moments(qf[keep])
+    np.testing.assert_allclose(S[1, :, 1], mean1, rtol=1e-13)
+    np.testing.assert_allclose(S[1, :, 2], m21, rtol=1e-10)
+
+
+def test_nan_input_reports_nonfinite_status(hl, solver):
+    xi = hl.sample_xi(inputs.SEED, 0, 0, 4)
+    xi[2, 1] = float("nan")
+    qf, _, st, stats = solver.level_batch_solve(0, xi, allow_failures=True)
+    st = st.cpu().numpy()
+    assert st[2] == hl.HENRY_SAMPLE_NONFINITE
+    assert (st[[0, 1, 3]] == 0).all()
+    assert stats["failed_samples"] == 1
+
+
+def test_newton_cap_reports_newton_status(hl):
+    s = hl.Solver(newton_maxit=1)
+    xi = hl.sample_xi(inputs.SEED, 0, 0, 2)
+    _, _, st, stats = s.level_batch_solve(0, xi, allow_failures=True)
+    assert (st.cpu().numpy() == hl.HENRY_SAMPLE_NEWTON).all()
+    with pytest.raises(hl.HenryError) as e:
+        s.level_batch_solve(0, xi)
+    assert e.value.code == hl.HENRY_ENOCONV
+    s.close()
+
+
+@pytest.mark.parametrize("level", [2, 3])
+def test_full_size_batch_sampled_against_oracle(hl, solver, level):
+    """Level-l batch of the MLMC workload's size in the same launch
+    configuration; one sampled scenario is recomputed by the oracle."""
+    n = {2: 64, 3: 32}[level]
+    xi_d = hl.sample_xi(inputs.SEED, level, 0, n)
+    qf, qc, st, _ = solver.level_batch_solve(level, xi_d, with_coarse=True)
+    assert int(st.abs().sum()) == 0
+    q = qf.cpu().numpy()
+    qcn = qc.cpu().numpy()
+    # properties that hold at any size
+    assert np.all((q[:, 1] >= -1e-12) & (q[:, 1] <= 1 + 1e-12))
+    assert np.all(q[:, 0] > 0)
+    assert np.abs(q[:, 1] - qcn[:, 1]).max() < 0.1   # level differences are small
+    i = n // 2
+    ref, ok = ohenry.solve_scenarios(PRM, level, xi_d[i:i + 1].cpu().numpy())
+    assert ok.all()
+    _qoi_check(q[i:i + 1], ref)
