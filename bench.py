@@ -1,0 +1,369 @@
+"""Benchmark: plain-FP64 MLMC of the Henry problem on levels 0..3 (RMSE 1e-3 allocation).
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+for every level l = 0..3, m_l scenarios with fresh Philox xi are solved
+together with their coarse partners (same xi, level l - 1), and the level
+differences are merged into the MLMC sums; the host then re-evaluates the
+allocation of Eq. (M_ell).  m_l comes from a pilot run (1000, 200, 50, 20
+samples) with variance budget eps^2 / 2, eps = 1e-3 on c(1.5, 0.25), and the
+level cost model s_l = cell-steps of a sample and its partner.
+
+Metric: cell-steps/s (sum over solved scenarios, coarse partners included, of
+cells x time steps, divided by the device time of the step).  The JSON line
+also carries the e2e figure (host xi in pinned memory copied in, QoIs and
+sums copied out every step), the roofline of the dominant kernel class (from
+the library's CUDA-event kernel timer over one extra step), the clocks seen
+during the timed region, the oracle's CPU throughput on a bounded sample,
+and the MLMC time to RMSE 1e-3 for FP64 and mixed precision.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EPS = 1e-3
+PILOT = (1000, 200, 50, 20)
+MAX_LEVEL = 3
+METRIC = "cell-steps/s"
+WORKLOAD = "henry-mlmc-fp64-levels0-3-rmse1e-3"
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle (reference arm / baseline)
+def oracle_sample(seconds_target=20.0):
+    """The oracle as it stands on the host cores: a bounded sample of the
+    workload (level-0..2 scenarios in the workload's level mix, one process
+    per core, spawn pool).  Returns (cell_steps_per_s, cores, description)."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import henry as oh
+    from oracle import philox as oph
+    from paper_2302_07804_gb300 import inputs
+    cores = os.cpu_count() or 1
+    prm = oh.Params()
+    # per core: 3 level-0, 1 level-1 scenarios; plus level-2 scenarios on a quarter of the cores
+    jobs = []
+    for lev, per_core in ((0, 3), (1, 1)):
+        xi = oph.sample_xi(inputs.SEED, lev, 10 ** 6, per_core * cores)
+        jobs += [(lev, x) for x in xi]
+    xi2 = oph.sample_xi(inputs.SEED, 2, 10 ** 6, max(1, cores // 4))
+    jobs += [(2, x) for x in xi2]
+    t0 = time.perf_counter()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_job, jobs)
+    wall = time.perf_counter() - t0
+    cs = sum(r for r in res)
+    desc = ("%d level-0, %d level-1, %d level-2 scenarios (32x16x20, 64x32x40, 128x64x80 cell-steps each) "
+            "of the MLMC workload, oracle Newton + sparse direct solve, spawn pool of %d processes, wall %.1f s"
+            % (3 * cores, cores, len(xi2), cores, wall))
+    return cs / wall, cores, desc, wall
+
+
+def _oracle_job(args):
+    from oracle import henry as oh
+    lev, xi = args
+    prm = oh.Params()
+    oh.solve_scenario(prm, lev, xi)
+    g = oh.Grid.level(prm, lev)
+    return g.ncell * g.steps
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    vals = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    total_wall = 0.0
+    cores = 1
+    desc = ""
+    for _ in range(max(1, args.steps)):
+        v, cores, desc, wall = oracle_sample()
+        vals.append(v)
+        total_wall += wall
+    value = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "-bounded-sample", "levels": "0-2 sample of the level mix"},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="henry", choices=["henry", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip mlmc-time, profile and cpu legs")
+    args = ap.parse_args()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_07804_gb300 import henry, inputs, mlmc
+
+    dev = torch.device("cuda", local)
+    solver = henry.Solver(precision=henry.HENRY_FP64)
+    # Replicas: each rank draws from its own Philox counter range.
+    seed = inputs.SEED + 1000003 * rank
+    # ---- pilot (untimed): V_l of c(1.5, 0.25) -> m_l
+    levels = [mlmc.LevelState(l, dev) for l in range(MAX_LEVEL + 1)]
+    for l in range(MAX_LEVEL + 1):
+        mlmc.run_level(solver, levels[l], PILOT[l], seed)
+    V = [max(st.moments()[2][1], 1e-300) for st in levels]
+    s_model = [mlmc.level_cost_model(solver.cfg, l) for l in range(MAX_LEVEL + 1)]
+    alloc = henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
+    cells_per_step = sum(m * mlmc.level_cost_model(solver.cfg, l) for l, m in enumerate(alloc))
+
+    stream = torch.cuda.current_stream()
+    # ---- inputs resident in HBM before the timed region: xi for every step
+    nsteps_all = args.warmup + args.steps
+    xis = []
+    for k in range(nsteps_all):
+        xis.append([henry.sample_xi(seed, l, 10 ** 7 + k * alloc[l], alloc[l], device=dev) for l in range(MAX_LEVEL + 1)])
+    outs = [(torch.empty((m, 2), dtype=torch.float64, device=dev),
+             torch.empty((m, 2), dtype=torch.float64, device=dev) if l > 0 else None,
+             torch.empty((m,), dtype=torch.int32, device=dev)) for l, m in enumerate(alloc)]
+    sums = torch.zeros((MAX_LEVEL + 1, 2, 2, 3), dtype=torch.float64, device=dev)
+    fails = [0]
+
+    def step(k):
+        for l in range(MAX_LEVEL + 1):
+            qf, qc, st, stats = solver.level_batch_solve(l, xis[k][l], with_coarse=l > 0, allow_failures=True,
+                                                         out=outs[l])
+            fails[0] += int(stats["failed_samples"])
+            henry.mlmc_accumulate(l, qf, qc, st, sums[l])
+        henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.warmup, nsteps_all):
+            step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed_max = reduce_max(elapsed, world)
+    total_cells = reduce_sum(cells_per_step * args.steps, world)
+    value = total_cells / elapsed_max
+    gpu_launches = None
+
+    # ---- e2e through the public API with host buffers (pinned), copies inside the timed region
+    xi_host = [[x.cpu().pin_memory() for x in xis[k]] for k in range(args.warmup, nsteps_all)]
+    q_host = [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc]
+    sums_host = torch.empty_like(sums, device="cpu").pin_memory()
+    h2d = sum(m * 3 * 8 for m in alloc)
+    d2h = sum(m * 2 * 8 * (2 if l > 0 else 1) + m * 4 for l, m in enumerate(alloc)) + sums.numel() * 8
+    xi_dev = [torch.empty((m, 3), dtype=torch.float64, device=dev) for m in alloc]
+    qc_host = [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc]
+    st_host = [torch.empty((m,), dtype=torch.int32).pin_memory() for m in alloc]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for l in range(MAX_LEVEL + 1):
+            xi_dev[l].copy_(xi_host[k][l], non_blocking=True)
+            qf, qc, st, stats = solver.level_batch_solve(l, xi_dev[l], with_coarse=l > 0, allow_failures=True,
+                                                         out=outs[l])
+            henry.mlmc_accumulate(l, qf, qc, st, sums[l])
+            q_host[l].copy_(qf, non_blocking=True)
+            if qc is not None:
+                qc_host[l].copy_(qc, non_blocking=True)
+            st_host[l].copy_(st, non_blocking=True)
+        sums_host.copy_(sums, non_blocking=True)
+        torch.cuda.synchronize()
+        henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e = total_cells / e2e_s
+
+    line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": "0-3 (32x16x20 .. 256x128x160 cells x steps)",
+                       "m_per_level": alloc, "coarse_partners": True, "cell_steps_per_step": cells_per_step,
+                       "eps": EPS, "var_budget": 0.5 * EPS * EPS, "pilot": list(PILOT),
+                       "V_pilot": V, "seed": inputs.SEED, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set > L2 (level-0 batch alone is GBs); no flush needed",
+                       "failed_samples": fails[0]},
+            "e2e": {"value": e2e, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk.summary()}
+
+    if rank == 0 and not args.no_extras:
+        # ---- roofline of the dominant kernel class: one extra profiled step
+        solver.profile(True)
+        step(args.warmup)
+        torch.cuda.synchronize()
+        prof = solver.profile_read()
+        solver.profile(False)
+        gpu_launches_step = sum(v[1] for v in prof.values())
+        gpu_launches = gpu_launches_step * args.steps
+        dom = max(prof.items(), key=lambda kv: kv[1][0])
+        peak, src = peaks()
+        ach = dom[1][2] / (dom[1][0] / 1e3) / 1e9 if dom[1][0] > 0 else 0.0
+        line["roofline"] = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
+                            "frac": ach / peak, "peak_source": src, "traffic": None,
+                            "avg_launch_us": 1e3 * dom[1][0] / max(1, dom[1][1]),
+                            "alg_bytes_per_launch": dom[1][2] / max(1, dom[1][1])}
+        line["kernel_classes"] = {k: {"ms": v[0], "launches": v[1],
+                                      "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
+                                  for k, v in prof.items()}
+        line["gpu_launches"] = gpu_launches
+        # ---- MLMC time to RMSE 1e-3, FP64 vs mixed (fresh counters)
+        times = {}
+        for name, prec in (("fp64", henry.HENRY_FP64), ("mixed", henry.HENRY_MIXED)):
+            s2 = henry.Solver(precision=prec, lin_rtol=1e-8 if prec == henry.HENRY_FP64 else 1e-4)
+            torch.cuda.synchronize()
+            r = mlmc.run_mlmc(s2, eps=EPS, max_level=MAX_LEVEL, pilot=PILOT, seed=inputs.SEED + 77)
+            times[name] = {"seconds": r["wall_seconds"], "estimate": r["estimate"], "rmse_stat": r["rmse_stat"],
+                           "alloc": r["alloc"], "cell_steps": r["cell_steps"]}
+            s2.close()
+        line["mlmc_time_to_rmse_1e-3"] = times
+        # ---- CPU oracle on the host cores (bounded sample)
+        try:
+            v, cores, desc, wall = oracle_sample()
+            line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                                    "sample": desc}
+        except Exception as exc:  # the baseline must not hide the GPU line
+            line["cpu_baseline"] = {"value": None, "unit": "cell-steps/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": "failed: %s" % exc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -193,6 +193,33 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
                        const double* state_old_dev, const double* b_dev, double* x_dev, int32_t* iters_dev,
                        void* stream);
 
+/* ---- Kernel timing.  Classes of kernels whose launches the timer brackets
+ * with CUDA events on the launching stream. */
+enum {
+  HENRY_K_ASSEMBLE = 0,          /* a4: fine-grid residual + Jacobian */
+  HENRY_K_COARSE_OPS = 1,        /* a5: coarse operators (rediscretised or Galerkin) + coarsest inverse */
+  HENRY_K_STATE_RESTRICT = 2,    /* a5: 2x2 averages of the state for rediscretisation */
+  HENRY_K_SMOOTH = 3,            /* a7: red-black block Gauss-Seidel half-sweeps */
+  HENRY_K_RESIDUAL_RESTRICT = 4, /* a7: residual + restriction (and x += P x_c without post-smoothing) */
+  HENRY_K_COARSE_SOLVE = 5,      /* a7: 4x4 solve on the 2 x 1 grid */
+  HENRY_K_SPMV = 6,              /* a8: y = J x with dot products */
+  HENRY_K_KRYLOV = 7,            /* a6: BiCGStab vector updates and reductions */
+  HENRY_K_NEWTON = 8,            /* a9, a10: Newton update, tests, step start */
+  HENRY_K_QOI = 9,               /* a2, a3, a11: coefficients, initial state, QoIs */
+  HENRY_K_COUNT = 10
+};
+
+/* Start (enable != 0: counters reset) or stop timing on this handle.  While
+ * on, each launch of the solver's kernels is bracketed by two CUDA events
+ * (which adds host overhead; time the workload with it off).  Host only. */
+int henry_profile(henry_handle* h, int enable);
+
+/* Per class since the last reset: summed event time [ms], launches, and the
+ * algorithmic (compulsory) DRAM bytes of those launches: every array a kernel
+ * touches counted once per launch, for the samples still iterating.
+ * Synchronises the device if events are pending.  Any output may be NULL. */
+int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,17 +147,78 @@ struct Group {
 
 }  // namespace
 
+// Per-kernel-class timing with CUDA events (off by default): each profiled
+// launch is bracketed by two events on its stream; pending pairs are read at
+// the next host synchronisation.  Algorithmic bytes per launch are counted
+// from the compulsory traffic of the kernel for the samples still iterating.
+struct Prof {
+  bool on = false;
+  struct Pend {
+    cudaEvent_t a, b;
+    int cls;
+    double bytes;
+  };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Pend> pend;
+  double ms[HENRY_K_COUNT] = {};
+  int64_t launches[HENRY_K_COUNT] = {};
+  double bytes[HENRY_K_COUNT] = {};
+};
+
 struct henry_handle {
   henry_config cfg;
   std::map<int, Group<double>> g64;
   std::map<int, Group<float>> g32;
   int* host_counter = nullptr;  // pinned
   unsigned long long* host_totals = nullptr;
+  Prof prof;
+  int nact = 0;  // samples iterating in the current Newton / Krylov iteration (for byte counts)
 };
 
 namespace {
 
+cudaEvent_t prof_event(Prof& P) {
+  if (!P.pool.empty()) {
+    cudaEvent_t e = P.pool.back();
+    P.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+template <typename F>
+void launch(henry_handle* H, cudaStream_t st, int cls, double bytes, F&& f) {
+  if (!H->prof.on) {
+    f();
+    return;
+  }
+  Prof& P = H->prof;
+  cudaEvent_t a = prof_event(P), b = prof_event(P);
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  P.pend.push_back({a, b, cls, bytes});
+}
+
+void prof_drain(henry_handle* H) {
+  Prof& P = H->prof;
+  for (auto& p : P.pend) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    P.ms[p.cls] += ms;
+    P.launches[p.cls] += 1;
+    P.bytes[p.cls] += p.bytes;
+    P.pool.push_back(p.a);
+    P.pool.push_back(p.b);
+  }
+  P.pend.clear();
+}
+
 Phys phys_of(const henry_config& c) {
+
   Phys p;
   p.rho0 = c.rho0; p.rho1 = c.rho1; p.drho = c.rho1 - c.rho0; p.g = c.g; p.Ly = c.Ly;
   return p;
@@ -237,7 +298,8 @@ template <typename T>
 int set_coefficients(henry_handle* H, Group<T>& G, const double* xi, int B, cudaStream_t st) {
   const henry_config& c = H->cfg;
   CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
-  k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status);
+  launch(H, st, HENRY_K_QOI, (double)B * (24 + 32 + 4),
+         [&] { k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status); });
   CKL();
   return HENRY_OK;
 }
@@ -249,33 +311,42 @@ template <typename T>
 int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st) {
   typedef typename VT<T>::b4 B4;
   const Phys ph = phys_of(H->cfg);
+  const double na = H->nact;
   for (int k = 1; k <= G.K; ++k) {
     Level& L = G.lv[k];
     if (H->cfg.coarse_op == HENRY_COARSE_GALERKIN) {
       Level& Lf = G.lv[k - 1];
-      k_galerkin<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)Lf.J, Lf.plane, (B4*)L.J,
-                                                             L.plane, G.lin_active);
+      launch(H, st, HENRY_K_COARSE_OPS, na * L.N * 26.0 * sizeof(B4), [&] {
+        k_galerkin<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)Lf.J, Lf.plane, (B4*)L.J,
+                                                               L.plane, G.lin_active);
+      });
     } else {
-      k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, inv_tau, inv_s,
-                                                                    L.x, L.xo, G.lin_active, nullptr, (B4*)L.J,
-                                                                    L.plane, nullptr);
+      launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
+        k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, inv_tau, inv_s,
+                                                                      L.x, L.xo, G.lin_active, nullptr, (B4*)L.J,
+                                                                      L.plane, nullptr);
+      });
     }
     CKL();
   }
   Level& Lc = G.lv[G.K];
-  k_coarse_inverse<T><<<nblk(B, 64), 64, 0, st>>>(B, (const B4*)Lc.J, Lc.plane, G.Ainv, G.lin_active);
+  launch(H, st, HENRY_K_COARSE_OPS, na * (4.0 * sizeof(B4) + 16.0 * sizeof(T)), [&] {
+    k_coarse_inverse<T><<<nblk(B, 64), 64, 0, st>>>(B, (const B4*)Lc.J, Lc.plane, G.Ainv, G.lin_active);
+  });
   CKL();
   return HENRY_OK;
 }
 
 // x_k -> x_{k+1} (mean of children) for all levels; `old` selects xo.
 template <typename T>
-int restrict_states(Group<T>& G, int B, bool old, const int* active, cudaStream_t st) {
+int restrict_states(henry_handle* H, Group<T>& G, int B, bool old, const int* active, cudaStream_t st) {
   for (int k = 0; k < G.K; ++k) {
     Level& Lf = G.lv[k];
     Level& Lc = G.lv[k + 1];
-    k_restrict_state<<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, old ? Lf.xo : Lf.x,
-                                                              old ? Lc.xo : Lc.x, active);
+    launch(H, st, HENRY_K_STATE_RESTRICT, (double)H->nact * Lc.N * 80.0, [&] {
+      k_restrict_state<<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, old ? Lf.xo : Lf.x,
+                                                                old ? Lc.xo : Lc.x, active);
+    });
     CKL();
   }
   return HENRY_OK;
@@ -289,32 +360,45 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
   typedef typename VT<T>::b4 B4;
   const int nu1 = H->cfg.nu1, nu2 = H->cfg.nu2;
   const int* act = G.lin_active;
+  const double na = H->nact;
+  const double b4 = sizeof(B4), v2 = sizeof(V2);
   for (int k = 0; k < G.K; ++k) {
     Level& L = G.lv[k];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
     const B4* J = (const B4*)L.J;
     const unsigned gh = nblk((int64_t)B * L.N / 2);
+    const double hc = na * L.N / 2;  // swept cells per half-sweep
     Level& Lc = G.lv[k + 1];
     if (nu1 > 0) {
-      k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
-      k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      launch(H, st, HENRY_K_SMOOTH, hc * (b4 + 2 * v2),
+             [&] { k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act); });
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+             [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu1; ++i) {
-        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
-        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+        for (int col = 0; col < 2; ++col)
+          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+                 [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
-      k_residual_restrict<T, 0><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
-                                                                        (V2*)Lc.mgb, act);
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * (10 * b4 + 7 * v2), [&] {
+        k_residual_restrict<T, 0><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
+                                                                          (V2*)Lc.mgb, act);
+      });
     } else {
-      k_zero<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>((int64_t)B * L.N, x);
-      k_residual_restrict<T, 1><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
-                                                                        (V2*)Lc.mgb, act);
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.N * v2,
+             [&] { k_zero<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>((int64_t)B * L.N, x); });
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * 5 * v2, [&] {
+        k_residual_restrict<T, 1><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
+                                                                          (V2*)Lc.mgb, act);
+      });
     }
     CKL();
   }
   {
     Level& Lc = G.lv[G.K];
-    k_coarse_solve<T><<<nblk(B, 64), 64, 0, st>>>(B, G.Ainv, (const V2*)Lc.mgb, (V2*)Lc.mgx, act);
+    launch(H, st, HENRY_K_COARSE_SOLVE, na * (16.0 * sizeof(T) + 4 * v2), [&] {
+      k_coarse_solve<T><<<nblk(B, 64), 64, 0, st>>>(B, G.Ainv, (const V2*)Lc.mgb, (V2*)Lc.mgx, act);
+    });
     CKL();
   }
   for (int k = G.K - 1; k >= 0; --k) {
@@ -324,15 +408,22 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
     const B4* J = (const B4*)L.J;
     const unsigned gh = nblk((int64_t)B * L.N / 2);
+    const double hc = na * L.N / 2;
     if (nu2 > 0) {
-      k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act);
-      k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3.5 * v2), [&] {
+        k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act);
+      });
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+             [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu2; ++i) {
-        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act);
-        k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act);
+        for (int col = 0; col < 2; ++col)
+          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+                 [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
     } else {
-      k_prolong_add<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, x, (const V2*)Lc.mgx, act);
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.N * 2.25 * v2, [&] {
+        k_prolong_add<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, x, (const V2*)Lc.mgx, act);
+      });
     }
     CKL();
   }
@@ -351,6 +442,7 @@ int read_counter(henry_handle* H, const int* dev, cudaStream_t st, int* out) {
   CK(cudaMemcpyAsync(H->host_counter, dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   *out = *H->host_counter;
+  if (H->prof.on) prof_drain(H);
   return HENRY_OK;
 }
 
@@ -358,32 +450,48 @@ int read_counter(henry_handle* H, const int* dev, cudaStream_t st, int* out) {
 // side -F; solution in G.dx.
 template <typename T>
 int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
   Level& L = G.lv[0];
   const int N = L.N;
   const unsigned g = nblk((int64_t)B * N);
-  k_bicg_init<T><<<g, TPB, 0, st>>>(B, N, G.F, G.r, G.rh, G.p, G.v, G.dx, G.part, G.lin_active);
+  const double b4 = sizeof(B4), v2 = sizeof(V2);
+  launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (16 + 5 * v2), [&] {
+    k_bicg_init<T><<<g, TPB, 0, st>>>(B, N, G.F, G.r, G.rh, G.p, G.v, G.dx, G.part, G.lin_active);
+  });
   CKL();
   const double rtol2 = H->cfg.lin_rtol * H->cfg.lin_rtol;
   for (int it = 0; it <= H->cfg.lin_maxit; ++it) {
     CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
-    k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, H->cfg.lin_maxit, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
-                                    G.iters, G.status, G.counter + 1, G.totals + 1);
+    launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (it == 0 ? 2 : 4) * v2, [&] {
+      k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, H->cfg.lin_maxit, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
+                                      G.iters, G.status, G.counter + 1, G.totals + 1);
+    });
     CKL();
     int n_act = 0;
     int rc = read_counter(H, G.counter + 1, st, &n_act);
     if (rc) return rc;
     if (n_act == 0) break;
+    H->nact = n_act;
+    const double nc = (double)n_act * N;
     rc = vcycle<T>(H, G, B, G.p, G.ph, st);
     if (rc) return rc;
-    k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const typename VT<T>::b4*)L.J, L.plane, G.ph, G.v, G.rh,
-                                     G.part, P_RV, 0, G.lin_active);
-    k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active);
+    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), [&] {
+      k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.ph, G.v, G.rh, G.part, P_RV, 0,
+                                       G.lin_active);
+    });
+    launch(H, st, HENRY_K_KRYLOV, nc * 3 * v2,
+           [&] { k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active); });
     CKL();
     rc = vcycle<T>(H, G, B, G.s, G.sh, st);
     if (rc) return rc;
-    k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const typename VT<T>::b4*)L.J, L.plane, G.sh, G.t, G.s,
-                                     G.part, P_TS, P_TT, G.lin_active);
-    k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active);
+    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), [&] {
+      k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.sh, G.t, G.s, G.part, P_TS, P_TT,
+                                       G.lin_active);
+    });
+    launch(H, st, HENRY_K_KRYLOV, nc * 8 * v2, [&] {
+      k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active);
+    });
     CKL();
   }
   return HENRY_OK;
@@ -393,6 +501,7 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
 template <typename T>
 int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t st) {
   typedef typename VT<T>::b4 B4;
+  typedef typename VT<T>::v2 V2;
   const henry_config& c = H->cfg;
   const LevelGeom lg = geom(c, G.level);
   const Phys ph = phys_of(c);
@@ -402,43 +511,57 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
   const double inv_tau = 1.0 / lg.tau;
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   const double inv_pref = 1.0 / (c.rho0 * c.g * c.Ly);
+  double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
   CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
-  k_init_state<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0 * c.g, c.Ly, L.x);
+  H->nact = B;
+  launch(H, st, HENRY_K_QOI, (double)n0 * 16,
+         [&] { k_init_state<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0 * c.g, c.Ly, L.x); });
   CKL();
   for (int step = 0; step < lg.steps; ++step) {
-    k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
-    k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
+    H->nact = B;
+    launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
+      k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+      k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
+    });
     CKL();
-    int rc = restrict_states<T>(G, B, true, G.newton_active, st);
+    int rc = restrict_states<T>(H, G, B, true, G.newton_active, st);
     if (rc) return rc;
     for (int it = 0; it <= c.newton_maxit; ++it) {
       CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
-      k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, inv_tau, inv_s, L.x, L.xo,
-                                                     G.newton_active, G.F, (B4*)L.J, L.plane, G.part + P_MAX * (int64_t)B * G.nct);
-      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit,
-                                                       G.part + P_MAX * (int64_t)B * G.nct, G.newton_active,
-                                                       G.lin_active, G.newton_it, G.status, G.counter, G.totals);
+      launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
+        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, inv_tau, inv_s, L.x, L.xo,
+                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
+      });
+      launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
+        k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+                                                         G.newton_active, G.lin_active, G.newton_it, G.status,
+                                                         G.counter, G.totals);
+      });
       CKL();
       int n_act = 0;
       rc = read_counter(H, G.counter, st, &n_act);
       if (rc) return rc;
       if (n_act == 0) break;
+      H->nact = n_act;
       if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
-        rc = restrict_states<T>(G, B, false, G.lin_active, st);
+        rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
         if (rc) return rc;
       }
       rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
       if (rc) return rc;
       rc = linear_solve<T>(H, G, B, st);
       if (rc) return rc;
-      k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, L.x, G.dx, G.part + P_MAX * (int64_t)B * G.nct,
-                                                    G.newton_active);
-      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, G.part + P_MAX * (int64_t)B * G.nct,
-                                                      G.newton_active, G.status);
+      H->nact = n_act;
+      launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
+        k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, L.x, G.dx, pmax, G.newton_active);
+        k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
+      });
       CKL();
     }
   }
-  k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi);
+  launch(H, st, HENRY_K_QOI, (double)n0 * 16, [&] {
+    k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi);
+  });
   CKL();
   return HENRY_OK;
 }
@@ -486,6 +609,7 @@ int setup_from_states(henry_handle* H, int level, const double* xi, int n, const
   Group<T>* G = nullptr;
   int rc = get_group<T>(H, level, n, &G);
   if (rc) return rc;
+  H->nact = n;
   rc = set_coefficients<T>(H, *G, xi, n, st);
   if (rc) return rc;
   Level& L = G->lv[0];
@@ -512,9 +636,9 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
                                                                L.plane, G.part + P_MAX * (int64_t)n * G.nct);
   CKL();
   if (!coarse) return HENRY_OK;
-  int rc = restrict_states<T>(G, n, true, G.lin_active, st);
+  int rc = restrict_states<T>(H, G, n, true, G.lin_active, st);
   if (rc) return rc;
-  rc = restrict_states<T>(G, n, false, G.lin_active, st);
+  rc = restrict_states<T>(H, G, n, false, G.lin_active, st);
   if (rc) return rc;
   return build_coarse_ops<T>(H, G, n, inv_tau, inv_s, st);
 }
@@ -626,6 +750,11 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
 void henry_destroy(henry_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (auto& p : h->prof.pend) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->prof.pool) cudaEventDestroy(e);
   for (auto& kv : h->g64)
     if (kv.second.mem) cudaFree(kv.second.mem);
   for (auto& kv : h->g32)
@@ -636,6 +765,38 @@ void henry_destroy(henry_handle* h) {
 }
 
 const char* henry_last_error(void) { return g_err.c_str(); }
+
+int henry_profile(henry_handle* h, int enable) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  Prof& P = h->prof;
+  if (!P.pend.empty()) {
+    CK(cudaDeviceSynchronize());
+    prof_drain(h);
+  }
+  if (enable) {
+    for (int k = 0; k < HENRY_K_COUNT; ++k) {
+      P.ms[k] = 0.0;
+      P.launches[k] = 0;
+      P.bytes[k] = 0.0;
+    }
+  }
+  P.on = enable != 0;
+  return HENRY_OK;
+}
+
+int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  if (kclass < 0 || kclass >= HENRY_K_COUNT) return set_err(HENRY_EINVAL, "kernel class %d out of range", kclass);
+  Prof& P = h->prof;
+  if (!P.pend.empty()) {
+    CK(cudaDeviceSynchronize());
+    prof_drain(h);
+  }
+  if (total_ms) *total_ms = P.ms[kclass];
+  if (launches) *launches = P.launches[kclass];
+  if (alg_bytes) *alg_bytes = P.bytes[kclass];
+  return HENRY_OK;
+}
 
 int henry_sample_xi(uint64_t seed, int level, uint64_t first_sample, int n, double* xi_dev, void* stream) {
   if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);

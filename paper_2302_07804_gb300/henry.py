@@ -22,7 +22,10 @@ N_XI = 3
 
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
-           "henry_apply_jacobian", "henry_precondition", "henry_linear_solve")
+           "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
+           "henry_profile_read")
+KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
+                  "spmv", "krylov", "newton", "qoi")
 
 
 class HenryConfig(ctypes.Structure):
@@ -76,6 +79,8 @@ def lib():
         L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_linear_solve.argtypes = [P, I, P, I, P, P, P, P, P, P]
+        L.henry_profile.argtypes = [P, I]
+        L.henry_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)]
         for name in EXPORTS:
             f = getattr(L, name)
             if name not in ("henry_default_config", "henry_destroy", "henry_last_error"):
@@ -167,6 +172,19 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable=True):
+        """Turn per-kernel-class event timing on (counters reset) or off."""
+        _check(lib().henry_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{class: (ms, launches, algorithmic bytes)} since the last reset."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+            _check(lib().henry_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            out[name] = (ms.value, n.value, b.value)
+        return out
 
     def grid(self, level):
         return (self.cfg.ny0 << level, self.cfg.nx0 << level)

@@ -1,0 +1,150 @@
+"""Host-side MLMC driver over libhenry (Sec. 3 of arXiv 2302.07804).
+
+For each level l the driver draws fresh xi with Philox (counters continue
+from the samples already used on that level, so batches are independent and
+a run resumes exactly from its counters), solves the fine scenario and its
+coarse partner with the same xi in one ``henry_level_batch_solve`` call, and
+merges Y_l = g_l - g_{l-1} into per-level running (count, mean, M2) sums on
+the device with ``mlmc_accumulate`` (Eqs. EgL, A and Def. Yell).  Sample
+numbers follow Eq. (M_ell) through ``mlmc_allocate``, with the variance
+budget eps^2 / 2 of Eq. (MSE) and the level cost s_l proportional to the
+cell-steps of a sample and its coarse partner (Eq. CompComplexity:
+s_l = O(n_l r_l)), or the measured GPU time per sample.
+"""
+import json
+import math
+import time
+
+import torch
+
+from . import henry
+
+
+def level_cost_model(cfg, level):
+    """Cell-steps of one level-l sample plus its coarse partner."""
+    def cs(l):
+        return (cfg.nx0 << l) * (cfg.ny0 << l) * (cfg.steps0 << l)
+    return cs(level) + (cs(level - 1) if level > 0 else 0)
+
+
+class LevelState:
+    def __init__(self, level, device):
+        self.level = level
+        self.n_used = 0          # Philox counter offset: samples drawn so far
+        self.sums = torch.zeros((2, henry.N_QOI, 3), dtype=torch.float64, device=device)
+        self.gpu_seconds = 0.0
+        self.cell_steps = 0.0
+        self.failed = 0
+
+    def moments(self):
+        """(count, mean[q], var[q]) of Y_l from the device sums."""
+        S = self.sums.cpu()
+        n = float(S[0, 0, 0])
+        mean = S[0, :, 1].tolist()
+        var = [(float(S[0, q, 2]) / (n - 1)) if n > 1 else float("nan") for q in range(henry.N_QOI)]
+        return n, mean, var
+
+    def to_json(self):
+        return {"level": self.level, "n_used": self.n_used, "sums": self.sums.cpu().tolist(),
+                "gpu_seconds": self.gpu_seconds, "cell_steps": self.cell_steps, "failed": self.failed}
+
+    @staticmethod
+    def from_json(d, device):
+        st = LevelState(d["level"], device)
+        st.n_used = d["n_used"]
+        st.sums = torch.tensor(d["sums"], dtype=torch.float64, device=device)
+        st.gpu_seconds = d["gpu_seconds"]
+        st.cell_steps = d["cell_steps"]
+        st.failed = d["failed"]
+        return st
+
+
+def run_level(solver, st, n, seed, stream=None, xi=None):
+    """Solve n new samples of level st.level (with coarse partners) and merge
+    them into st.sums; returns the henry_stats of the call."""
+    lev = st.level
+    if xi is None:
+        xi = henry.sample_xi(seed, lev, st.n_used, n, device=st.sums.device, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    e0.record(s)
+    qf, qc, status, stats = solver.level_batch_solve(lev, xi, with_coarse=lev > 0, stream=stream,
+                                                     allow_failures=True)
+    henry.mlmc_accumulate(lev, qf, qc, status, st.sums, stream=stream)
+    e1.record(s)
+    e1.synchronize()
+    st.gpu_seconds += e0.elapsed_time(e1) / 1e3
+    st.n_used += n
+    st.cell_steps += stats["cell_steps"]
+    st.failed += int(stats["failed_samples"])
+    return stats
+
+
+def merge_sums(parts):
+    """Chan's pairwise merge of a list of (count, mean, M2) tables, on the host
+    (used to combine replicas that ran disjoint counter ranges)."""
+    out = None
+    for p in parts:
+        p = torch.as_tensor(p, dtype=torch.float64).cpu().clone()
+        if out is None:
+            out = p
+            continue
+        na, ma, m2a = out[..., 0], out[..., 1], out[..., 2]
+        nb, mb, m2b = p[..., 0], p[..., 1], p[..., 2]
+        n = na + nb
+        d = mb - ma
+        safe = torch.where(n > 0, n, torch.ones_like(n))
+        mean = torch.where(n > 0, ma + d * nb / safe, ma)
+        m2 = torch.where(n > 0, m2a + m2b + d * d * na * nb / safe, m2a)
+        out = torch.stack([n, mean, m2], dim=-1)
+    return out
+
+
+def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None, qoi=1, cost="model",
+             var_fraction=0.5, max_rounds=4, state=None, log=None):
+    """MLMC estimate of E[g_L] for QoI ``qoi`` (0 salt mass, 1 c at the point)
+    to a variance budget var_fraction * eps^2 (Eq. MSE); returns a dict."""
+    from . import inputs
+    seed = inputs.SEED if seed is None else seed
+    dev = torch.device("cuda", torch.cuda.current_device())
+    levels = state or [LevelState(l, dev) for l in range(max_level + 1)]
+    t0 = time.perf_counter()
+    for l in range(max_level + 1):
+        need = max(0, pilot[l] - levels[l].n_used)
+        if need:
+            run_level(solver, levels[l], need, seed)
+    budget = var_fraction * eps * eps
+    alloc = None
+    for rnd in range(max_rounds):
+        V = []
+        s = []
+        for st in levels:
+            n, mean, var = st.moments()
+            V.append(max(var[qoi], 1e-300))
+            s.append(level_cost_model(solver.cfg, st.level) if cost == "model"
+                     else st.gpu_seconds / max(st.n_used, 1))
+        alloc = henry.mlmc_allocate(V, s, budget)
+        extra = [max(0, m - st.n_used) for m, st in zip(alloc, levels)]
+        if log:
+            log("round %d: V=%s m=%s extra=%s" % (rnd, ["%.3g" % v for v in V], alloc, extra))
+        if sum(extra) == 0:
+            break
+        for st, e in zip(levels, extra):
+            if e:
+                run_level(solver, st, e, seed)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    est = 0.0
+    var_est = 0.0
+    per = []
+    for st in levels:
+        n, mean, var = st.moments()
+        est += mean[qoi]
+        var_est += var[qoi] / n
+        per.append({"level": st.level, "n": int(n), "mean_Y": mean[qoi], "var_Y": var[qoi],
+                    "gpu_seconds": st.gpu_seconds, "cell_steps": st.cell_steps, "failed": st.failed})
+    return {"estimate": est, "variance": var_est, "rmse_stat": math.sqrt(var_est), "eps": eps,
+            "var_budget": budget, "alloc": alloc, "wall_seconds": wall,
+            "cell_steps": sum(p["cell_steps"] for p in per), "levels": per,
+            "checkpoint": json.dumps([st.to_json() for st in levels])}
