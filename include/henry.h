@@ -193,6 +193,27 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
                        const double* state_old_dev, const double* b_dev, double* x_dev, int32_t* iters_dev,
                        void* stream);
 
+/* ---- Allocation-free variant of henry_level_batch_solve (the paper has no
+ * counterpart: this is a deployment aid).  For callers that cannot call
+ * cudaMalloc at run time - processes whose device memory is owned by another
+ * allocator or pool, plug-ins that must not grow their footprint after load -
+ * it solves the same batch with the same kernels but takes its whole
+ * workspace from one device array of HENRY_STATIC_SCRATCH_BYTES compiled into
+ * the library (held by every GPU that loads it until the process exits); it
+ * makes no device or pinned allocation and needs no handle (cfg is read, as
+ * in henry_create).  The caller passes inputs and outputs as for
+ * henry_level_batch_solve (without stats).  The workspace of n samples at
+ * `level` (plus that of the coarse partners) must fit in the array - with the
+ * default configuration up to 64 level-0 samples in FP64 - otherwise
+ * HENRY_EINVAL with a message giving the sizes.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress with that
+ * device current): make that first call before any stream capture.  All
+ * calls share the array and host counter words; calls that overlap on the GPU
+ * or across host threads race.  Synchronises `stream`. */
+#define HENRY_STATIC_SCRATCH_BYTES (16u << 20)
+int henry_level_batch_solve_static(const henry_config* cfg, int level, int with_coarse, const double* xi_dev, int n,
+                                   double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev, void* stream);
+
 /* ---- Kernel timing.  Classes of kernels whose launches the timer brackets
  * with CUDA events on the launching stream. */
 enum {

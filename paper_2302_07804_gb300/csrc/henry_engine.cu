@@ -913,3 +913,139 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free batch solve.
+//
+// Some callers cannot allocate device memory at run time: code running under
+// an allocator that forbids cudaMalloc (a memory-pool-managed serving
+// process, a plug-in that must not grow its footprint) or that wants every
+// byte reserved when the library loads.  For them this variant of
+// henry_level_batch_solve carves its whole workspace out of one file-scope
+// device array of HENRY_STATIC_SCRATCH_BYTES instead of a handle's
+// cudaMalloc'd groups, and needs no handle at all.  Every GPU that loads the
+// library holds this array until the process exits.
+//
+// In host code `g_static_scratch` names a host-side stand-in, not the device
+// array, so its device address is looked up with cudaGetSymbolAddress once per
+// device (with that device current) on the first call there; make that first
+// call before any stream capture.  All calls share the array and it keeps the
+// last call's contents (the solve initialises everything it reads); calls
+// that overlap on the GPU (other streams, other host threads) race on it.
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[HENRY_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+void* g_static_ptr[kMaxDevices] = {};
+int g_static_host_words[16];                  // pageable host words for the convergence counters
+unsigned long long g_static_host_totals[4];
+
+int static_scratch_ptr(char** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_err(HENRY_EINVAL, "device %d outside [0, %d)", dev, kMaxDevices);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return set_err(HENRY_ECUDA, "cudaGetSymbolAddress(static scratch) failed on device %d: %s", dev,
+                     cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<char*>(g_static_ptr[dev]);
+  return HENRY_OK;
+}
+
+// The configuration checks of henry_create, without creating a handle.
+int static_check_config(const henry_config& c) {
+  if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || c.nx0 != 2 * c.ny0)
+    return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
+  if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)
+    return set_err(HENRY_EINVAL, "domain must be Lx = 2 Ly (square cells)");
+  if (c.max_level < 0 || c.max_level > 8) return set_err(HENRY_EINVAL, "max_level %d outside [0, 8]", c.max_level);
+  if (c.nx0 * c.ny0 < TPB) return set_err(HENRY_EINVAL, "cells per sample must be a multiple of %d", TPB);
+  if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
+  if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
+    return set_err(HENRY_EINVAL, "bad coarse_op");
+  if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
+      c.lin_rtol <= 0)
+    return set_err(HENRY_EINVAL, "bad solver settings");
+  return HENRY_OK;
+}
+
+// Lays out the fine group (and the coarse partner's) in the static array.
+template <typename T>
+int static_solve(henry_handle* H, int level, int with_coarse, const double* xi, int n, double* qf, double* qc,
+                 int32_t* status, cudaStream_t st) {
+  char* base = nullptr;
+  int rc = static_scratch_ptr(&base);
+  if (rc) return rc;
+  const LevelGeom gf = geom(H->cfg, level);
+  Group<T> Gf, Gc;
+  size_t need = (Gf.carve(nullptr, n, gf.nx, gf.ny, gf.h) + 255) & ~size_t(255);
+  size_t need_c = 0;
+  LevelGeom gc{};
+  if (with_coarse) {
+    gc = geom(H->cfg, level - 1);
+    need_c = Gc.carve(nullptr, n, gc.nx, gc.ny, gc.h);
+  }
+  if (need + need_c > (size_t)HENRY_STATIC_SCRATCH_BYTES)
+    return set_err(HENRY_EINVAL,
+                   "%d samples at level %d%s need %zu bytes of workspace; the static scratch holds %zu bytes", n,
+                   level, with_coarse ? " with coarse partners" : "", need + need_c,
+                   (size_t)HENRY_STATIC_SCRATCH_BYTES);
+  Gf.carve(base, n, gf.nx, gf.ny, gf.h);
+  Gf.level = level;
+  Gf.Bcap = n;
+  rc = set_coefficients<T>(H, Gf, xi, n, st);
+  if (!rc) rc = solve_group<T>(H, Gf, n, qf, st);
+  if (rc) return rc;
+  k_merge_status<<<nblk(n, 128), 128, 0, st>>>(n, Gf.status, status, 1);
+  CKL();
+  if (with_coarse) {
+    Gc.carve(base + need, n, gc.nx, gc.ny, gc.h);
+    Gc.level = level - 1;
+    Gc.Bcap = n;
+    rc = set_coefficients<T>(H, Gc, xi, n, st);
+    if (!rc) rc = solve_group<T>(H, Gc, n, qc, st);
+    if (rc) return rc;
+    k_merge_status<<<nblk(n, 128), 128, 0, st>>>(n, Gc.status, status, 0);
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+}  // namespace
+
+extern "C" int henry_level_batch_solve_static(const henry_config* cfg, int level, int with_coarse,
+                                              const double* xi_dev, int n, double* qoi_fine_dev,
+                                              double* qoi_coarse_dev, int32_t* status_dev, void* stream) {
+  if (!cfg) return set_err(HENRY_EINVAL, "cfg is NULL");
+  int rc = static_check_config(*cfg);
+  if (rc) return rc;
+  if (level < 0 || level > cfg->max_level) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, cfg->max_level);
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!xi_dev || !qoi_fine_dev || !status_dev) return set_err(HENRY_EINVAL, "NULL device pointer");
+  if (with_coarse && level == 0) return set_err(HENRY_EINVAL, "level 0 has no coarse partner");
+  if (with_coarse && !qoi_coarse_dev) return set_err(HENRY_EINVAL, "qoi_coarse_dev is NULL");
+  henry_handle H;  // on the stack: no device workspace, no pinned buffers, timer off
+  H.cfg = *cfg;
+  H.host_counter = g_static_host_words;
+  H.host_totals = g_static_host_totals;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = cfg->precision == HENRY_MIXED
+           ? static_solve<float>(&H, level, with_coarse, xi_dev, n, qoi_fine_dev, qoi_coarse_dev, status_dev, st)
+           : static_solve<double>(&H, level, with_coarse, xi_dev, n, qoi_fine_dev, qoi_coarse_dev, status_dev, st);
+  if (rc) return rc;
+  int32_t buf[256];
+  int64_t failed = 0;
+  for (int off = 0; off < n; off += 256) {
+    const int m = std::min(256, n - off);
+    CK(cudaMemcpyAsync(buf, status_dev + off, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < m; ++i) failed += buf[i] != 0;
+  }
+  if (failed) return set_err(HENRY_ENOCONV, "%lld of %d samples did not converge", (long long)failed, n);
+  return HENRY_OK;
+}

@@ -23,7 +23,7 @@ N_XI = 3
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
-           "henry_profile_read")
+           "henry_profile_read", "henry_level_batch_solve_static")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi")
 
@@ -79,6 +79,7 @@ def lib():
         L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_linear_solve.argtypes = [P, I, P, I, P, P, P, P, P, P]
+        L.henry_level_batch_solve_static.argtypes = [ctypes.POINTER(HenryConfig), I, I, P, I, P, P, P, P]
         L.henry_profile.argtypes = [P, I]
         L.henry_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)]
         for name in EXPORTS:
@@ -151,6 +152,21 @@ def mlmc_allocate(V, s, var_budget):
     out = (ctypes.c_int64 * L)()
     _check(lib().mlmc_allocate(L, Va, sa, float(var_budget), out))
     return [int(v) for v in out]
+
+
+def level_batch_solve_static(cfg, level, xi, with_coarse=False, stream=None, allow_failures=False):
+    """henry_level_batch_solve_static: the batch solve with the library's
+    compiled-in device workspace (no device allocation by the library); for
+    callers that cannot allocate.  Returns (qoi_fine, qoi_coarse or None, status)."""
+    n = xi.shape[0]
+    _dev_f64(xi, (n, N_XI))
+    qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
+    qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
+    st = torch.empty((n,), dtype=torch.int32, device=xi.device)
+    rc = lib().henry_level_batch_solve_static(ctypes.byref(cfg), level, 1 if with_coarse else 0, _ptr(xi), n,
+                                              _ptr(qf), _ptr(qc), _ptr(st), _stream(stream))
+    _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
+    return qf, qc, st
 
 
 class Solver:
