@@ -143,33 +143,33 @@ def reduce_sum(x, world):
 
 
 # ------------------------------------------------------------------ CPU oracle (reference arm / baseline)
-def oracle_sample(seconds_target=20.0):
+def oracle_sample(mix=((0, 3), (1, 1)), level2_per_4_cores=1):
     """The oracle as it stands on the host cores: a bounded sample of the
     workload (level-0..2 scenarios in the workload's level mix, one process
-    per core, spawn pool).  Returns (cell_steps_per_s, cores, description)."""
+    per core, spawn pool).  Returns (cell_steps_per_s, cores, description, wall)."""
     import multiprocessing as mp
-    import numpy as np
-    from oracle import henry as oh
     from oracle import philox as oph
     from paper_2302_07804_gb300 import inputs
     cores = os.cpu_count() or 1
-    prm = oh.Params()
-    # per core: 3 level-0, 1 level-1 scenarios; plus level-2 scenarios on a quarter of the cores
     jobs = []
-    for lev, per_core in ((0, 3), (1, 1)):
+    counts = {}
+    for lev, per_core in mix:
         xi = oph.sample_xi(inputs.SEED, lev, 10 ** 6, per_core * cores)
         jobs += [(lev, x) for x in xi]
-    xi2 = oph.sample_xi(inputs.SEED, 2, 10 ** 6, max(1, cores // 4))
-    jobs += [(2, x) for x in xi2]
+        counts[lev] = per_core * cores
+    if level2_per_4_cores:
+        xi2 = oph.sample_xi(inputs.SEED, 2, 10 ** 6, max(1, level2_per_4_cores * cores // 4))
+        jobs += [(2, x) for x in xi2]
+        counts[2] = len(xi2)
     t0 = time.perf_counter()
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         res = pool.map(_oracle_job, jobs)
     wall = time.perf_counter() - t0
     cs = sum(r for r in res)
-    desc = ("%d level-0, %d level-1, %d level-2 scenarios (32x16x20, 64x32x40, 128x64x80 cell-steps each) "
-            "of the MLMC workload, oracle Newton + sparse direct solve, spawn pool of %d processes, wall %.1f s"
-            % (3 * cores, cores, len(xi2), cores, wall))
+    desc = ("%s scenarios of the MLMC workload (level: count; 32x16x20, 64x32x40, 128x64x80 cell-steps), "
+            "oracle Newton + sparse direct solve, spawn pool of %d processes, wall %.1f s"
+            % (counts, cores, wall))
     return cs / wall, cores, desc, wall
 
 
@@ -183,23 +183,24 @@ def _oracle_job(args):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores, each step a bounded sample (2 level-0 and
+    1 level-1 scenario per core) of the workload; rank 0 only."""
     if rank != 0:
         return 0
+    for _ in range(args.warmup):
+        oracle_sample(mix=((0, 2), (1, 1)), level2_per_4_cores=0)
     vals = []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
     total_wall = 0.0
-    cores = 1
-    desc = ""
+    cores, desc = 1, ""
     for _ in range(max(1, args.steps)):
-        v, cores, desc, wall = oracle_sample()
+        v, cores, desc, wall = oracle_sample(mix=((0, 2), (1, 1)), level2_per_4_cores=0)
         vals.append(v)
         total_wall += wall
     value = sum(vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + "-bounded-sample", "levels": "0-2 sample of the level mix"},
+            "config": {"workload": WORKLOAD, "sample": "bounded: level-0 and level-1 scenarios per core"},
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -208,14 +209,136 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+class Workload:
+    """The MLMC pass: one handle and one CUDA stream per level, the levels run
+    concurrently from host threads (each level's solve synchronises only its
+    own stream), joined on the main stream."""
+
+    def __init__(self, henry, torch, dev, alloc, precision, xis):
+        import threading
+        self.h, self.t, self.dev, self.alloc = henry, torch, dev, alloc
+        self.L = len(alloc)
+        self.solvers = [henry.Solver(precision=precision) for _ in range(self.L)]
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.L)]
+        self.outs = [(torch.empty((m, 2), dtype=torch.float64, device=dev),
+                      torch.empty((m, 2), dtype=torch.float64, device=dev) if l > 0 else None,
+                      torch.empty((m,), dtype=torch.int32, device=dev)) for l, m in enumerate(alloc)]
+        self.sums = torch.zeros((self.L, 2, 2, 3), dtype=torch.float64, device=dev)
+        self.xis = xis
+        self.fails = [0] * self.L
+        self.errors = []
+        self.threading = threading
+        # order threads by work: finest level first
+        self.order = sorted(range(self.L), key=lambda l: -alloc[l] * (8 ** l))
+
+    def _level(self, l, xi, host=None):
+        torch, henry = self.t, self.h
+        try:
+            torch.cuda.set_device(self.dev)
+            s = self.streams[l]
+            with torch.cuda.stream(s):
+                if host is not None:
+                    host["xi_dev"][l].copy_(host["xi"][l], non_blocking=True)
+                    xi = host["xi_dev"][l]
+                qf, qc, st, stats = self.solvers[l].level_batch_solve(l, xi, with_coarse=l > 0, stream=s,
+                                                                      allow_failures=True, out=self.outs[l])
+                self.fails[l] += int(stats["failed_samples"])
+                henry.mlmc_accumulate(l, qf, qc, st, self.sums[l], stream=s)
+                if host is not None:
+                    host["qf"][l].copy_(qf, non_blocking=True)
+                    if qc is not None:
+                        host["qc"][l].copy_(qc, non_blocking=True)
+                    host["st"][l].copy_(st, non_blocking=True)
+        except Exception as exc:  # surfaced by run()
+            self.errors.append(exc)
+
+    def run(self, k=None, host=None, sequential=False):
+        torch = self.t
+        main = torch.cuda.current_stream(self.dev)
+        ev = torch.cuda.Event()
+        ev.record(main)
+        for s in self.streams:
+            s.wait_event(ev)
+        if sequential:  # for per-kernel timing: no overlap between levels
+            for l in self.order:
+                self._level(l, None if k is None else self.xis[k][l], host)
+                self.streams[l].synchronize()
+        else:
+            ths = [self.threading.Thread(target=self._level, args=(l, None if k is None else self.xis[k][l], host))
+                   for l in self.order]
+            for th in ths:
+                th.start()
+            for th in ths:
+                th.join()
+        if self.errors:
+            raise self.errors[0]
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def profile(self, on):
+        for s in self.solvers:
+            s.profile(on)
+
+    def profile_read(self):
+        tot = None
+        for s in self.solvers:
+            p = s.profile_read()
+            if tot is None:
+                tot = {k: list(v) for k, v in p.items()}
+            else:
+                for k, v in p.items():
+                    for i in range(3):
+                        tot[k][i] += v[i]
+        return tot
+
+    def close(self):
+        for s in self.solvers:
+            s.close()
+
+
+def run_case(args):
+    """Profiling case: one batch of N scenarios at one level (no MLMC)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_07804_gb300 import henry, inputs
+    lev, n = (int(v) for v in args.case.split(":"))
+    prec = henry.HENRY_MIXED if args.precision == "mixed" else henry.HENRY_FP64
+    s = henry.Solver(precision=prec)
+    xi = henry.sample_xi(inputs.SEED, lev, 0, n)
+    s.level_batch_solve(lev, xi[:8])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    qf, qc, st, stats = s.level_batch_solve(lev, xi)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    line = {"case": args.case, "precision": args.precision, "seconds": sec,
+            "cell_steps_per_s": stats["cell_steps"] / sec, "stats": stats}
+    if args.profile:
+        s.profile(True)
+        s.level_batch_solve(lev, xi)
+        line["kernel_classes"] = s.profile_read()
+        s.profile(False)
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="henry", choices=["henry", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-extras", action="store_true", help="skip mlmc-time, profile and cpu legs")
+    ap.add_argument("--case", default=None, help="LEVEL:N profiling case (one batch solve, no MLMC)")
+    ap.add_argument("--profile", action="store_true", help="with --case: also read the kernel timer")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -226,36 +349,29 @@ def main():
     from paper_2302_07804_gb300 import henry, inputs, mlmc
 
     dev = torch.device("cuda", local)
-    solver = henry.Solver(precision=henry.HENRY_FP64)
+    prec = henry.HENRY_MIXED if args.precision == "mixed" else henry.HENRY_FP64
+    pilot_solver = henry.Solver(precision=henry.HENRY_FP64)
     # Replicas: each rank draws from its own Philox counter range.
     seed = inputs.SEED + 1000003 * rank
     # ---- pilot (untimed): V_l of c(1.5, 0.25) -> m_l
     levels = [mlmc.LevelState(l, dev) for l in range(MAX_LEVEL + 1)]
     for l in range(MAX_LEVEL + 1):
-        mlmc.run_level(solver, levels[l], PILOT[l], seed)
+        mlmc.run_level(pilot_solver, levels[l], PILOT[l], seed)
+    pilot_solver.close()
     V = [max(st.moments()[2][1], 1e-300) for st in levels]
-    s_model = [mlmc.level_cost_model(solver.cfg, l) for l in range(MAX_LEVEL + 1)]
+    s_model = [mlmc.level_cost_model(henry.default_config(), l) for l in range(MAX_LEVEL + 1)]
     alloc = henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
-    cells_per_step = sum(m * mlmc.level_cost_model(solver.cfg, l) for l, m in enumerate(alloc))
+    cells_per_step = sum(m * mlmc.level_cost_model(henry.default_config(), l) for l, m in enumerate(alloc))
 
-    stream = torch.cuda.current_stream()
     # ---- inputs resident in HBM before the timed region: xi for every step
     nsteps_all = args.warmup + args.steps
-    xis = []
-    for k in range(nsteps_all):
-        xis.append([henry.sample_xi(seed, l, 10 ** 7 + k * alloc[l], alloc[l], device=dev) for l in range(MAX_LEVEL + 1)])
-    outs = [(torch.empty((m, 2), dtype=torch.float64, device=dev),
-             torch.empty((m, 2), dtype=torch.float64, device=dev) if l > 0 else None,
-             torch.empty((m,), dtype=torch.int32, device=dev)) for l, m in enumerate(alloc)]
-    sums = torch.zeros((MAX_LEVEL + 1, 2, 2, 3), dtype=torch.float64, device=dev)
-    fails = [0]
+    xis = [[henry.sample_xi(seed, l, 10 ** 7 + k * alloc[l], alloc[l], device=dev) for l in range(MAX_LEVEL + 1)]
+           for k in range(nsteps_all)]
+    W = Workload(henry, torch, dev, alloc, prec, xis)
+    stream = torch.cuda.current_stream()
 
     def step(k):
-        for l in range(MAX_LEVEL + 1):
-            qf, qc, st, stats = solver.level_batch_solve(l, xis[k][l], with_coarse=l > 0, allow_failures=True,
-                                                         out=outs[l])
-            fails[0] += int(stats["failed_samples"])
-            henry.mlmc_accumulate(l, qf, qc, st, sums[l])
+        W.run(k)
         henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
 
     for k in range(args.warmup):
@@ -276,31 +392,23 @@ def main():
     elapsed_max = reduce_max(elapsed, world)
     total_cells = reduce_sum(cells_per_step * args.steps, world)
     value = total_cells / elapsed_max
-    gpu_launches = None
 
     # ---- e2e through the public API with host buffers (pinned), copies inside the timed region
+    host = {"xi": None, "xi_dev": [torch.empty((m, 3), dtype=torch.float64, device=dev) for m in alloc],
+            "qf": [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc],
+            "qc": [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc],
+            "st": [torch.empty((m,), dtype=torch.int32).pin_memory() for m in alloc]}
     xi_host = [[x.cpu().pin_memory() for x in xis[k]] for k in range(args.warmup, nsteps_all)]
-    q_host = [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc]
-    sums_host = torch.empty_like(sums, device="cpu").pin_memory()
+    sums_host = torch.empty(W.sums.shape, dtype=torch.float64).pin_memory()
     h2d = sum(m * 3 * 8 for m in alloc)
-    d2h = sum(m * 2 * 8 * (2 if l > 0 else 1) + m * 4 for l, m in enumerate(alloc)) + sums.numel() * 8
-    xi_dev = [torch.empty((m, 3), dtype=torch.float64, device=dev) for m in alloc]
-    qc_host = [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc]
-    st_host = [torch.empty((m,), dtype=torch.int32).pin_memory() for m in alloc]
+    d2h = sum(m * 2 * 8 * (2 if l > 0 else 1) + m * 4 for l, m in enumerate(alloc)) + W.sums.numel() * 8
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        for l in range(MAX_LEVEL + 1):
-            xi_dev[l].copy_(xi_host[k][l], non_blocking=True)
-            qf, qc, st, stats = solver.level_batch_solve(l, xi_dev[l], with_coarse=l > 0, allow_failures=True,
-                                                         out=outs[l])
-            henry.mlmc_accumulate(l, qf, qc, st, sums[l])
-            q_host[l].copy_(qf, non_blocking=True)
-            if qc is not None:
-                qc_host[l].copy_(qc, non_blocking=True)
-            st_host[l].copy_(st, non_blocking=True)
-        sums_host.copy_(sums, non_blocking=True)
+        host["xi"] = xi_host[k]
+        W.run(None, host)
+        sums_host.copy_(W.sums, non_blocking=True)
         torch.cuda.synchronize()
         henry.mlmc_allocate(V, s_model, 0.5 * EPS * EPS)
     e2e_s = reduce_max(time.perf_counter() - t0, world)
@@ -308,40 +416,45 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": "0-3 (32x16x20 .. 256x128x160 cells x steps)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == henry.HENRY_FP64 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if prec == henry.HENRY_FP64 else WORKLOAD.replace("fp64", "mixed"),
+                       "levels": "0-3 (32x16x20 .. 256x128x160 cells x steps)",
                        "m_per_level": alloc, "coarse_partners": True, "cell_steps_per_step": cells_per_step,
                        "eps": EPS, "var_budget": 0.5 * EPS * EPS, "pilot": list(PILOT),
                        "V_pilot": V, "seed": inputs.SEED, "parallelism": "replicas" if world > 1 else "single",
+                       "levels_concurrent": "one stream and host thread per level",
                        "l2": "working set > L2 (level-0 batch alone is GBs); no flush needed",
-                       "failed_samples": fails[0]},
+                       "failed_samples": sum(W.fails)},
             "e2e": {"value": e2e, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary()}
 
     if rank == 0 and not args.no_extras:
         # ---- roofline of the dominant kernel class: one extra profiled step
-        solver.profile(True)
-        step(args.warmup)
+        W.profile(True)
+        W.run(args.warmup, sequential=True)
         torch.cuda.synchronize()
-        prof = solver.profile_read()
-        solver.profile(False)
+        prof = W.profile_read()
+        W.profile(False)
         gpu_launches_step = sum(v[1] for v in prof.values())
-        gpu_launches = gpu_launches_step * args.steps
         dom = max(prof.items(), key=lambda kv: kv[1][0])
         peak, src = peaks()
         ach = dom[1][2] / (dom[1][0] / 1e3) / 1e9 if dom[1][0] > 0 else 0.0
+        tot_ms = sum(v[0] for v in prof.values())
         line["roofline"] = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
                             "frac": ach / peak, "peak_source": src, "traffic": None,
                             "avg_launch_us": 1e3 * dom[1][0] / max(1, dom[1][1]),
-                            "alg_bytes_per_launch": dom[1][2] / max(1, dom[1][1])}
-        line["kernel_classes"] = {k: {"ms": v[0], "launches": v[1],
+                            "alg_bytes_per_launch": dom[1][2] / max(1, dom[1][1]),
+                            "timing": "CUDA events around every launch of the class during one extra step, "
+                                      "levels run one after another"}
+        line["kernel_classes"] = {k: {"ms": v[0], "share": v[0] / tot_ms if tot_ms else None, "launches": v[1],
                                       "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
                                   for k, v in prof.items()}
-        line["gpu_launches"] = gpu_launches
+        line["gpu_launches"] = gpu_launches_step * args.steps
         # ---- MLMC time to RMSE 1e-3, FP64 vs mixed (fresh counters)
         times = {}
-        for name, prec in (("fp64", henry.HENRY_FP64), ("mixed", henry.HENRY_MIXED)):
-            s2 = henry.Solver(precision=prec, lin_rtol=1e-8 if prec == henry.HENRY_FP64 else 1e-4)
+        for name, p2 in (("fp64", henry.HENRY_FP64), ("mixed", henry.HENRY_MIXED)):
+            s2 = henry.Solver(precision=p2)
             torch.cuda.synchronize()
             r = mlmc.run_mlmc(s2, eps=EPS, max_level=MAX_LEVEL, pilot=PILOT, seed=inputs.SEED + 77)
             times[name] = {"seconds": r["wall_seconds"], "estimate": r["estimate"], "rmse_stat": r["rmse_stat"],
@@ -358,7 +471,7 @@ def main():
                                     "kind": "oracle", "sample": "failed: %s" % exc}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    solver.close()
+    W.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -119,16 +119,25 @@ __device__ __forceinline__ double sample_max(const double* __restrict__ p, int n
   return v;
 }
 
-// 2x2 block helpers.
+// 2x2 block helpers as explicit fused multiply-add chains: two FMAs per row
+// (written as r - a x - b y the compiler would issue a MUL, an FMA and an
+// ADD, and on GB300 the FP64 pipe is the smoother's bottleneck).
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 template <typename B4, typename T>
 __device__ __forceinline__ void bmv_sub(const B4& A, T x0, T x1, T& r0, T& r1) {
-  r0 -= A.a00 * x0 + A.a01 * x1;
-  r1 -= A.a10 * x0 + A.a11 * x1;
+  r0 = fma_(-A.a00, x0, fma_(-A.a01, x1, r0));
+  r1 = fma_(-A.a10, x0, fma_(-A.a11, x1, r1));
 }
 template <typename B4, typename T>
 __device__ __forceinline__ void bmv_add(const B4& A, T x0, T x1, T& r0, T& r1) {
-  r0 += A.a00 * x0 + A.a01 * x1;
-  r1 += A.a10 * x0 + A.a11 * x1;
+  r0 = fma_(A.a00, x0, fma_(A.a01, x1, r0));
+  r1 = fma_(A.a10, x0, fma_(A.a11, x1, r1));
+}
+template <typename B4, typename T>
+__device__ __forceinline__ void bmv(const B4& A, T x0, T x1, T& y0, T& y1) {
+  y0 = fma_(A.a00, x0, A.a01 * x1);
+  y1 = fma_(A.a10, x0, A.a11 * x1);
 }
 template <typename B4>
 __device__ __forceinline__ B4 mkblk(double a00, double a01, double a10, double a11) {
@@ -417,7 +426,9 @@ __global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, c
     }
   }
   const B4 Ci = J[5 * plane + e];
-  x[e] = mk2<V2>(Ci.a00 * r0 + Ci.a01 * r1, Ci.a10 * r0 + Ci.a11 * r1);
+  T y0, y1;
+  bmv(Ci, r0, r1, y0, y1);
+  x[e] = mk2<V2>(y0, y1);
 }
 
 // Residual b - A x restricted by summation over the 2x2 children.  After a
@@ -519,8 +530,8 @@ __global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typen
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
   const V2 xx = x[e];
-  T r0 = 0, r1 = 0;
-  bmv_add(J[e], xx.x, xx.y, r0, r1);
+  T r0, r1;
+  bmv(J[e], xx.x, xx.y, r0, r1);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
@@ -766,6 +777,18 @@ __global__ void k_newton_dx_check(int B, int nct, double dxtol, const double* __
 __global__ void __launch_bounds__(TPB) k_step_begin(int64_t n, const double2* __restrict__ x, double2* __restrict__ xo) {
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   if (e < n) xo[e] = x[e];
+}
+// Start of a later time step with a linear-in-time predictor for Newton's
+// first iterate: x_old <- x^n, x <- x^n + w (x^n - x^{n-1}) (x^{n-1} is the
+// old state of the previous step).  Only the starting point changes; Newton
+// still stops on the residual and update tests of the step.
+__global__ void __launch_bounds__(TPB) k_step_begin_predict(int64_t n, double w, double2* __restrict__ x,
+                                                            double2* __restrict__ xo) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= n) return;
+  const double2 a = x[e], b = xo[e];
+  xo[e] = a;
+  x[e] = make_double2(fma(w, a.x - b.x, a.x), fma(w, a.y - b.y, a.y));
 }
 __global__ void k_step_flags(int B, const int* __restrict__ status, int* __restrict__ newton_active,
                              int* __restrict__ newton_it) {

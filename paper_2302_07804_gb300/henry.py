@@ -35,7 +35,7 @@ class HenryConfig(ctypes.Structure):
                [(n, ctypes.c_int32) for n in ("nx0", "ny0", "steps0", "max_level", "precision", "coarse_op")] + \
                [(n, ctypes.c_double) for n in ("newton_atol", "newton_dxtol", "lin_rtol")] + \
                [(n, ctypes.c_int32) for n in ("newton_maxit", "lin_maxit", "nu1", "nu2")] + \
-               [("workspace_bytes", ctypes.c_double)]
+               [("workspace_bytes", ctypes.c_double), ("newton_predictor", ctypes.c_double)]
 
 
 class HenryStats(ctypes.Structure):
