@@ -53,6 +53,31 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# ALU peaks from unit counts and clocks: 152 SMs x FMA/clock/SM x 2 flops x
+# 2.07 GHz; GB300 issues 2 FP64 FMAs and 128 FP32 FMAs per SM per clock.
+ALU_PEAK_TFLOPS = {"f64": 152 * 2 * 2 * 2.07e9 / 1e12, "f32": 152 * 128 * 2 * 2.07e9 / 1e12}
+SWEEP_COUNTERS = os.path.join(ROOT, "profiles", "k_sweep_counters.json")
+
+
+def sweep_traffic(alg_bytes_per_launch, precision):
+    """DRAM traffic of an average smoother launch of the bench, scaled from
+    the committed ncu capture of a fine-level sweep (traffic / algorithmic
+    bytes, which is per swept cell and so scales with the launch's cells);
+    None when the capture is missing or the smoother source changed since."""
+    import hashlib
+    try:
+        with open(SWEEP_COUNTERS) as f:
+            c = json.load(f)
+        src = os.path.join(ROOT, "paper_2302_07804_gb300", "csrc", "henry_kernels.cuh")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        rec = c.get(precision)
+        if not rec or rec.get("henry_kernels_cuh_sha256") != sha:
+            return None
+        return alg_bytes_per_launch * rec["traffic_bytes"] / rec["alg_bytes"]
+    except Exception:
+        return None
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -287,7 +312,7 @@ class Workload:
                 tot = {k: list(v) for k, v in p.items()}
             else:
                 for k, v in p.items():
-                    for i in range(3):
+                    for i in range(4):
                         tot[k][i] += v[i]
         return tot
 
@@ -298,6 +323,7 @@ class Workload:
 
 def run_case(args):
     """Profiling case: one batch of N scenarios at one level (no MLMC)."""
+    import numpy as np
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -306,6 +332,23 @@ def run_case(args):
     prec = henry.HENRY_MIXED if args.precision == "mixed" else henry.HENRY_FP64
     s = henry.Solver(precision=prec)
     xi = henry.sample_xi(inputs.SEED, lev, 0, n)
+    if args.vcycle:
+        # one V-cycle on a batch where every sample is active (kernel captures)
+        ny, nx = s.grid(lev)
+        p, c = inputs.random_states(7, n, ny, nx, 1.0e4 * 0.5 / ny, 1.0e4 * (1 - 0.5 / ny), 20.0)
+        st = torch.as_tensor(np.stack([p, c], axis=-1), dtype=torch.float64, device="cuda")
+        b = torch.as_tensor(inputs.random_vectors(8, n, ny, nx), dtype=torch.float64, device="cuda")
+        z = s.precondition(lev, xi, st, st, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        z = s.precondition(lev, xi, st, st, b)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "vcycle": True, "precision": args.precision,
+                          "ms": e0.elapsed_time(e1), "finite": bool(torch.isfinite(z).all())}), flush=True)
+        s.close()
+        return 0
     s.level_batch_solve(lev, xi[:8])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,6 +379,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip mlmc-time, profile and cpu legs")
     ap.add_argument("--case", default=None, help="LEVEL:N profiling case (one batch solve, no MLMC)")
     ap.add_argument("--profile", action="store_true", help="with --case: also read the kernel timer")
+    ap.add_argument("--vcycle", action="store_true", help="with --case: one assembly + V-cycle per call instead of a solve")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -438,13 +482,25 @@ def main():
         W.profile(False)
         gpu_launches_step = sum(v[1] for v in prof.values())
         dom = max(prof.items(), key=lambda kv: kv[1][0])
-        peak, src = peaks()
-        ach = dom[1][2] / (dom[1][0] / 1e3) / 1e9 if dom[1][0] > 0 else 0.0
         tot_ms = sum(v[0] for v in prof.values())
-        line["roofline"] = {"bound": "hbm", "kernel": dom[0], "achieved": ach, "peak": peak, "unit": "GB/s",
-                            "frac": ach / peak, "peak_source": src, "traffic": None,
-                            "avg_launch_us": 1e3 * dom[1][0] / max(1, dom[1][1]),
-                            "alg_bytes_per_launch": dom[1][2] / max(1, dom[1][1]),
+        name, (ms, nl, nbytes, nflops) = dom
+        peak, src = peaks()
+        sec = ms / 1e3
+        gbs = nbytes / sec / 1e9 if sec > 0 else 0.0
+        tfl = nflops / sec / 1e12 if sec > 0 else 0.0
+        alu_key = "f64" if prec == henry.HENRY_FP64 else "f32"
+        f_hbm = gbs / peak
+        f_alu = tfl / ALU_PEAK_TFLOPS[alu_key]
+        traffic = sweep_traffic(nbytes / max(1, nl), alu_key) if name == "smooth" else None
+        hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": f_hbm, "peak_source": src + " (MEASURED_PEAKS.json copy)"}
+        alu = {"achieved": tfl, "peak": ALU_PEAK_TFLOPS[alu_key], "unit": "TFLOP/s", "frac": f_alu,
+               "peak_source": "unit counts x 2.07 GHz (%s)" % alu_key}
+        main = alu if f_alu > f_hbm else hbm
+        line["roofline"] = {"bound": "alu" if f_alu > f_hbm else "hbm", "kernel": name,
+                            "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
+                            "frac": main["frac"], "traffic": traffic, "hbm": hbm, "alu": alu,
+                            "avg_launch_us": 1e3 * ms / max(1, nl), "alg_bytes_per_launch": nbytes / max(1, nl),
+                            "alg_flops_per_launch": nflops / max(1, nl),
                             "timing": "CUDA events around every launch of the class during one extra step, "
                                       "levels run one after another"}
         line["kernel_classes"] = {k: {"ms": v[0], "share": v[0] / tot_ms if tot_ms else None, "launches": v[1],

@@ -98,6 +98,9 @@ typedef struct {
   double workspace_bytes;                    /* device workspace budget per batch (chunking) */
   double newton_predictor; /* Newton's first iterate of step n+1: x^n + w (x^n - x^{n-1}), w in [0, 1]
                               (0: x^n; default 1, linear extrapolation in time) */
+  int32_t fused_small_grids; /* grids of <= 512 cells solved by one CTA per sample with the whole hierarchy in
+                                shared memory: 1 (default) in HENRY_MIXED only, 2 also in HENRY_FP64,
+                                0 never (always the multi-kernel path) */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -229,7 +232,8 @@ enum {
   HENRY_K_KRYLOV = 7,            /* a6: BiCGStab vector updates and reductions */
   HENRY_K_NEWTON = 8,            /* a9, a10: Newton update, tests, step start */
   HENRY_K_QOI = 9,               /* a2, a3, a11: coefficients, initial state, QoIs */
-  HENRY_K_COUNT = 10
+  HENRY_K_FUSED = 10,            /* a3-a11 for a small grid: the one-CTA-per-sample solver */
+  HENRY_K_COUNT = 11
 };
 
 /* Start (enable != 0: counters reset) or stop timing on this handle.  While
@@ -237,11 +241,14 @@ enum {
  * (which adds host overhead; time the workload with it off).  Host only. */
 int henry_profile(henry_handle* h, int enable);
 
-/* Per class since the last reset: summed event time [ms], launches, and the
- * algorithmic (compulsory) DRAM bytes of those launches: every array a kernel
- * touches counted once per launch, for the samples still iterating.
- * Synchronises the device if events are pending.  Any output may be NULL. */
-int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes);
+/* Per class since the last reset: summed event time [ms], launches, the
+ * algorithmic (compulsory) DRAM bytes of those launches - every array a kernel
+ * touches counted once per launch, for the samples still iterating - and the
+ * algorithmic floating-point operations (FMA = 2) of the block-stencil
+ * classes (smooth, residual_restrict, spmv; 0 for the others).  Synchronises
+ * the device if events are pending.  Any output may be NULL. */
+int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes,
+                       double* alg_flops);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,7 @@
 #include "henry.h"
 #include "henry_kernels.cuh"
 #include "henry_misc.cuh"
+#include "henry_cta.cuh"
 
 using namespace hk;
 
@@ -86,6 +87,7 @@ struct Group {
   typedef typename VT<T>::v2 V2;
   typedef typename VT<T>::b4 B4;
   int level = -1, Bcap = 0, K = 0, nct = 0;
+  bool light = false;  // workspace of the fused small-grid solver only
   char* mem = nullptr;
   size_t bytes = 0;
   std::vector<Level> lv;
@@ -99,7 +101,9 @@ struct Group {
   T* Ainv;
 
   // Lay out (or size, with base == nullptr) the workspace for B samples.
-  size_t carve(char* base, int B, int nx0, int ny0, double h0) {
+  // `light`: only what the fused small-grid solver uses (fine old state,
+  // coefficients, status, counters); every other pointer is left null.
+  size_t carve(char* base, int B, int nx0, int ny0, double h0, bool light_ws = false) {
     Carver c{base, 0};
     std::vector<Level> L;
     int nx = nx0, ny = ny0;
@@ -108,26 +112,35 @@ struct Group {
       Level l;
       l.nx = nx; l.ny = ny; l.N = nx * ny; l.h = h;
       l.plane = (int64_t)B * l.N;
-      l.x = c.take<double2>(sizeof(double2) * l.plane);
-      l.xo = c.take<double2>(sizeof(double2) * l.plane);
-      l.J = c.take<B4>(sizeof(B4) * 6 * l.plane);
-      if (L.empty()) {
-        l.mgx = l.mgb = nullptr;
+      l.x = l.xo = nullptr;
+      l.J = l.mgx = l.mgb = nullptr;
+      if (light_ws) {
+        if (L.empty()) l.xo = c.take<double2>(sizeof(double2) * l.plane);
       } else {
-        l.mgx = c.take<V2>(sizeof(V2) * l.plane);
-        l.mgb = c.take<V2>(sizeof(V2) * l.plane);
+        l.x = c.take<double2>(sizeof(double2) * l.plane);
+        l.xo = c.take<double2>(sizeof(double2) * l.plane);
+        l.J = c.take<B4>(sizeof(B4) * 6 * l.plane);
+        if (!L.empty()) {
+          l.mgx = c.take<V2>(sizeof(V2) * l.plane);
+          l.mgb = c.take<V2>(sizeof(V2) * l.plane);
+        }
       }
       L.push_back(l);
       if (nx <= 2 || ny <= 1) break;
       nx /= 2; ny /= 2; h *= 2.0;
     }
     const int64_t n0 = (int64_t)B * nx0 * ny0;
-    F = c.take<double2>(sizeof(double2) * n0);
     V2** vecs[9] = {&r, &rh, &p, &v, &s, &t, &ph, &sh, &dx};
-    for (auto vp : vecs) *vp = c.take<V2>(sizeof(V2) * n0);
+    if (light_ws) {
+      F = nullptr;
+      for (auto vp : vecs) *vp = nullptr;
+    } else {
+      F = c.take<double2>(sizeof(double2) * n0);
+      for (auto vp : vecs) *vp = c.take<V2>(sizeof(V2) * n0);
+    }
     coef = c.take<Coef>(sizeof(Coef) * B);
     nct = nx0 * ny0 / TPB;
-    part = c.take<double>(sizeof(double) * NPART * (size_t)B * nct);
+    part = light_ws ? nullptr : c.take<double>(sizeof(double) * NPART * (size_t)B * nct);
     newton_active = c.take<int>(sizeof(int) * B);
     lin_active = c.take<int>(sizeof(int) * B);
     newton_it = c.take<int>(sizeof(int) * B);
@@ -135,11 +148,12 @@ struct Group {
     iters = c.take<int>(sizeof(int) * B);
     counter = c.take<int>(sizeof(int) * 4);
     totals = c.take<unsigned long long>(sizeof(unsigned long long) * 4);
-    sc = c.take<LinScal>(sizeof(LinScal) * B);
-    Ainv = c.take<T>(sizeof(T) * 16 * B);
+    sc = light_ws ? nullptr : c.take<LinScal>(sizeof(LinScal) * B);
+    Ainv = light_ws ? nullptr : c.take<T>(sizeof(T) * 16 * B);
     if (base) {
       lv = L;
       K = (int)L.size() - 1;
+      light = light_ws;
     }
     return c.off + 256;
   }
@@ -156,13 +170,14 @@ struct Prof {
   struct Pend {
     cudaEvent_t a, b;
     int cls;
-    double bytes;
+    double bytes, flops;
   };
   std::vector<cudaEvent_t> pool;
   std::vector<Pend> pend;
   double ms[HENRY_K_COUNT] = {};
   int64_t launches[HENRY_K_COUNT] = {};
   double bytes[HENRY_K_COUNT] = {};
+  double flops[HENRY_K_COUNT] = {};
 };
 
 struct henry_handle {
@@ -189,7 +204,7 @@ cudaEvent_t prof_event(Prof& P) {
 }
 
 template <typename F>
-void launch(henry_handle* H, cudaStream_t st, int cls, double bytes, F&& f) {
+void launch(henry_handle* H, cudaStream_t st, int cls, double bytes, double flops, F&& f) {
   if (!H->prof.on) {
     f();
     return;
@@ -199,7 +214,26 @@ void launch(henry_handle* H, cudaStream_t st, int cls, double bytes, F&& f) {
   cudaEventRecord(a, st);
   f();
   cudaEventRecord(b, st);
-  P.pend.push_back({a, b, cls, bytes});
+  P.pend.push_back({a, b, cls, bytes, flops});
+}
+template <typename F>
+void launch(henry_handle* H, cudaStream_t st, int cls, double bytes, F&& f) {
+  launch(H, st, cls, bytes, 0.0, f);
+}
+
+// Algorithmic flop counts (FMA = 2) of the block-stencil kernels on an
+// nx x ny grid: directed neighbour links 4 N - 2 nx - 2 ny, each a 2x2
+// block-vector product (8 flops).
+inline double links(int nx, int ny) { return 4.0 * nx * ny - 2.0 * nx - 2.0 * ny; }
+inline double sweep_flops(int nx, int ny, int mode) {  // one half-sweep
+  const double hc = 0.5 * nx * ny;
+  return (mode == 0 ? 0.0 : 0.5 * links(nx, ny) * 8.0) + hc * 6.0;
+}
+inline double spmv_flops(int nx, int ny, int ndot) {
+  return links(nx, ny) * 8.0 + nx * ny * (6.0 + 4.0 * ndot);
+}
+inline double restrict_flops(int nx, int ny) {  // residual of the colour-0 cells + sum
+  return 0.5 * links(nx, ny) * 8.0 + 0.5 * nx * ny * (8.0 + 2.0);
 }
 
 void prof_drain(henry_handle* H) {
@@ -211,6 +245,7 @@ void prof_drain(henry_handle* H) {
     P.ms[p.cls] += ms;
     P.launches[p.cls] += 1;
     P.bytes[p.cls] += p.bytes;
+    P.flops[p.cls] += p.flops;
     P.pool.push_back(p.a);
     P.pool.push_back(p.b);
   }
@@ -239,10 +274,33 @@ LevelGeom geom(const henry_config& c, int level) {
 }
 
 template <typename T>
-size_t bytes_per_sample(const henry_config& c, int level) {
+size_t bytes_per_sample(const henry_config& c, int level, bool light = false) {
   Group<T> g;
   LevelGeom lg = geom(c, level);
-  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h);
+  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h, light);
+}
+
+// The fused one-CTA-per-sample solver is used when enabled, the sample's
+// hierarchy fits the shared-memory layout and the device grants that much
+// shared memory per CTA.
+int g_smem_optin[64] = {};
+template <typename T>
+bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
+  // 1 (default): only with FP32 linear algebra, where it measured faster; on
+  // GB300 the FP64 variant (one CTA per SM for lack of shared memory) is
+  // FP64-latency bound and slower than the multi-kernel path.  2: always.
+  if (c.fused_small_grids <= 0) return false;
+  if (c.fused_small_grids == 1 && sizeof(T) != sizeof(float)) return false;
+  const LevelGeom lg = geom(c, level);
+  if (!cta_layout(lg.nx, lg.ny, (int)sizeof(T), L)) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (!g_smem_optin[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    g_smem_optin[dev] = v;
+  }
+  return L->bytes <= g_smem_optin[dev];
 }
 
 template <typename T>
@@ -256,12 +314,12 @@ int ensure_pinned(henry_handle* H);
 
 // Workspace for B samples at `level` (reused when large enough).
 template <typename T>
-int get_group(henry_handle* H, int level, int B, Group<T>** out) {
+int get_group(henry_handle* H, int level, int B, Group<T>** out, bool light = false) {
   int rc0 = ensure_pinned(H);
   if (rc0) return rc0;
   auto& m = groups<T>(H);
   Group<T>& g = m[level];
-  if (g.mem && g.Bcap >= B) {
+  if (g.mem && g.Bcap >= B && (light || !g.light)) {
     *out = &g;
     return HENRY_OK;
   }
@@ -271,7 +329,7 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out) {
     g.mem = nullptr;
   }
   LevelGeom lg = geom(H->cfg, level);
-  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h);
+  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h, light);
   char* mem = nullptr;
   if (cudaMalloc(&mem, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -279,7 +337,7 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out) {
   }
   g.mem = mem;
   g.bytes = bytes;
-  g.carve(mem, B, lg.nx, lg.ny, lg.h);
+  g.carve(mem, B, lg.nx, lg.ny, lg.h, light);
   g.level = level;
   g.Bcap = B;
   *out = &g;
@@ -287,8 +345,8 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out) {
 }
 
 template <typename T>
-int max_batch(const henry_config& c, int level) {
-  const double per = (double)bytes_per_sample<T>(c, level);
+int max_batch(const henry_config& c, int level, bool light = false) {
+  const double per = (double)bytes_per_sample<T>(c, level, light);
   const double b = std::floor(c.workspace_bytes / per);
   return (int)std::max(1.0, std::min(b, 1.0e6));
 }
@@ -322,9 +380,10 @@ int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double
       });
     } else {
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
-        k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, inv_tau, inv_s,
-                                                                      L.x, L.xo, G.lin_active, nullptr, (B4*)L.J,
-                                                                      L.plane, nullptr);
+        k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
+                                                                      L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                                      G.lin_active, nullptr, (B4*)L.J, L.plane,
+                                                                      nullptr);
       });
     }
     CKL();
@@ -371,16 +430,16 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     const double hc = na * L.N / 2;  // swept cells per half-sweep
     Level& Lc = G.lv[k + 1];
     if (nu1 > 0) {
-      launch(H, st, HENRY_K_SMOOTH, hc * (b4 + 2 * v2),
+      launch(H, st, HENRY_K_SMOOTH, hc * (b4 + 2 * v2), na * sweep_flops(L.nx, L.ny, 0),
              [&] { k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act); });
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
              [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu1; ++i) {
         for (int col = 0; col < 2; ++col)
-          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
                  [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
-      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * (10 * b4 + 7 * v2), [&] {
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * (10 * b4 + 7 * v2), na * restrict_flops(L.nx, L.ny), [&] {
         k_residual_restrict<T, 0><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
                                                                           (V2*)Lc.mgb, act);
       });
@@ -410,14 +469,13 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     const unsigned gh = nblk((int64_t)B * L.N / 2);
     const double hc = na * L.N / 2;
     if (nu2 > 0) {
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3.5 * v2), [&] {
-        k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act);
-      });
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3.5 * v2), na * (sweep_flops(L.nx, L.ny, 1) + L.N),
+             [&] { k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act); });
+      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
              [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu2; ++i) {
         for (int col = 0; col < 2; ++col)
-          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2),
+          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
                  [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
     } else {
@@ -476,7 +534,7 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
     const double nc = (double)n_act * N;
     rc = vcycle<T>(H, G, B, G.p, G.ph, st);
     if (rc) return rc;
-    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), [&] {
+    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 1), [&] {
       k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.ph, G.v, G.rh, G.part, P_RV, 0,
                                        G.lin_active);
     });
@@ -485,7 +543,7 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
     CKL();
     rc = vcycle<T>(H, G, B, G.s, G.sh, st);
     if (rc) return rc;
-    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), [&] {
+    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 2), [&] {
       k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.sh, G.t, G.s, G.part, P_TS, P_TT,
                                        G.lin_active);
     });
@@ -532,7 +590,8 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
     for (int it = 0; it <= c.newton_maxit; ++it) {
       CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
       launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
-        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, inv_tau, inv_s, L.x, L.xo,
+        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                       lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
                                                        G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
       });
       launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
@@ -577,19 +636,57 @@ __global__ void k_merge_status(int n, const int* __restrict__ a, int32_t* __rest
   else if (out[i] == 0) out[i] = v;
 }
 
+// The whole scenario solve of B samples with the fused one-CTA-per-sample
+// kernel (coefficients and status set).
+template <typename T>
+int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, double* qoi, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  CtaParams P;
+  P.ph = phys_of(c);
+  P.nx0 = lg.nx;
+  P.ny0 = lg.ny;
+  P.steps = lg.steps;
+  P.nu1 = c.nu1;
+  P.nu2 = c.nu2;
+  P.newton_maxit = c.newton_maxit;
+  P.lin_maxit = c.lin_maxit;
+  P.h0 = lg.h;
+  P.tau = lg.tau;
+  P.inv_s = 1.0 / (c.rho0 * lg.h * lg.h / lg.tau);
+  P.inv_pref = 1.0 / (c.rho0 * c.g * c.Ly);
+  P.atol = c.newton_atol;
+  P.dxtol = c.newton_dxtol;
+  P.rtol2 = c.lin_rtol * c.lin_rtol;
+  P.predictor = c.newton_predictor;
+  P.rho0g = c.rho0 * c.g;
+  P.Ly = c.Ly;
+  CK(cudaFuncSetAttribute(k_cta_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes));
+  CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
+  H->nact = B;
+  launch(H, st, HENRY_K_FUSED, (double)B * (double)lg.nx * lg.ny * lg.steps * 64.0 + (double)B * 48.0, [&] {
+    k_cta_solve<T><<<B, CTA_THREADS, L.bytes, st>>>(P, L, B, G.coef, G.lv[0].xo, qoi, G.status, G.totals);
+  });
+  CKL();
+  return HENRY_OK;
+}
+
 template <typename T>
 int batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status, bool first,
                       henry_stats* stats, cudaStream_t st) {
-  const int Bmax = max_batch<T>(H->cfg, level);
+  CtaLayout CL;
+  const bool fused = fused_eligible<T>(H->cfg, level, &CL);
+  const int Bmax = max_batch<T>(H->cfg, level, fused);
   const LevelGeom lg = geom(H->cfg, level);
   for (int off = 0; off < n; off += Bmax) {
     const int B = std::min(Bmax, n - off);
     Group<T>* G = nullptr;
-    int rc = get_group<T>(H, level, std::min(Bmax, n), &G);
+    int rc = get_group<T>(H, level, std::min(Bmax, n), &G, fused);
     if (rc) return rc;
     rc = set_coefficients<T>(H, *G, xi + 3 * (int64_t)off, B, st);
     if (rc) return rc;
-    rc = solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
+    rc = fused ? solve_group_fused<T>(H, *G, B, CL, qoi + 2 * (int64_t)off, st)
+               : solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
     if (rc) return rc;
     k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, first ? 1 : 0);
     CKL();
@@ -634,9 +731,10 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
   const double inv_tau = 1.0 / lg.tau;
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   Level& L = G.lv[0];
-  k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, inv_tau,
-                                                               inv_s, L.x, L.xo, G.newton_active, G.F, (B4*)L.J,
-                                                               L.plane, G.part + P_MAX * (int64_t)n * G.nct);
+  k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                               lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                               G.newton_active, G.F, (B4*)L.J, L.plane,
+                                                               G.part + P_MAX * (int64_t)n * G.nct);
   CKL();
   if (!coarse) return HENRY_OK;
   int rc = restrict_states<T>(H, G, n, true, G.lin_active, st);
@@ -726,6 +824,7 @@ void henry_default_config(henry_config* c) {
   c->nu1 = 2; c->nu2 = 2;
   c->workspace_bytes = 16.0e9;
   c->newton_predictor = 1.0;
+  c->fused_small_grids = 1;
 }
 
 int henry_create(const henry_config* cfg, henry_handle** out) {
@@ -782,13 +881,15 @@ int henry_profile(henry_handle* h, int enable) {
       P.ms[k] = 0.0;
       P.launches[k] = 0;
       P.bytes[k] = 0.0;
+      P.flops[k] = 0.0;
     }
   }
   P.on = enable != 0;
   return HENRY_OK;
 }
 
-int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes) {
+int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* launches, double* alg_bytes,
+                       double* alg_flops) {
   if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
   if (kclass < 0 || kclass >= HENRY_K_COUNT) return set_err(HENRY_EINVAL, "kernel class %d out of range", kclass);
   Prof& P = h->prof;
@@ -799,6 +900,7 @@ int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* l
   if (total_ms) *total_ms = P.ms[kclass];
   if (launches) *launches = P.launches[kclass];
   if (alg_bytes) *alg_bytes = P.bytes[kclass];
+  if (alg_flops) *alg_flops = P.flops[kclass];
   return HENRY_OK;
 }
 

@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace hk {
 
 constexpr int TPB = 256;  // threads per CTA of every cell kernel
@@ -147,17 +149,125 @@ __device__ __forceinline__ B4 mkblk(double a00, double a01, double a10, double a
 }
 
 // ---------------------------------------------------------------------------
-// a4 (and coarse operators by rediscretisation): residual and Jacobian.
+// a4 (and coarse operators by rediscretisation): residual and Jacobian of one
+// cell.  `xs`, `xos` point at the cell arrays of one sample (storage layout;
+// global or shared memory).  The per-sample K/mu and phi Dm and the
+// accumulation factor h^2/tau arrive already multiplied by inv_s, so every
+// flux and derivative comes out scaled.  Fluxes and residuals are formed in S
+// (FP64 on the fine grid), derivative blocks in T; in the mixed mode
+// (T = float) the coarse operators are assembled entirely in FP32 (S = T) and
+// the fine Jacobian's derivative terms are formed in FP32 from FP64 fluxes.
+template <typename T, typename S>
+struct CellSys {
+  S fm, fs;      // scaled residuals (fluid mass, salt)
+  T C[4];        // centre block
+  T Nb[4][4];    // W, E, S, N blocks
+};
+
+template <typename T, typename S>
+__device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, int nx, int ny, double h, double inv_h,
+                                              double vt_s, double inv_s, const double2* xs, const double2* xos,
+                                              int st, int ix, int iy, CellSys<T, S>& o) {
+  const S kmu = (S)(cf.kmu * inv_s), PD = (S)(cf.PD * inv_s), phi = (S)cf.phi;
+  const S hS = (S)h, ihS = (S)inv_h, drho = (S)ph.drho, rho0 = (S)ph.rho0;
+  const double2 xP = xs[st], xO = xos[st];
+  const S pP = (S)xP.x, cP = (S)xP.y, cO = (S)xO.y;
+  const S rhoP = rho0 + drho * cP;
+  const S rhoO = rho0 + drho * cO;
+  const S vt = (S)vt_s;
+  S Rm = phi * (rhoP - rhoO) * vt;
+  S Rs = phi * (rhoP * cP - rhoO * cO) * vt;
+  T C00 = (T)0, C01 = (T)(phi * drho * vt), C10 = (T)0, C11 = (T)(phi * (drho * cP + rhoP) * vt);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.Nb[k][0] = o.Nb[k][1] = o.Nb[k][2] = o.Nb[k][3] = (T)0;
+  const T kmuT = (T)kmu, PDT = (T)PD, hT = (T)h, hdT = (T)(0.5 * ph.drho);
+
+  // interior faces W, E, S, N
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const S sg = (S)(k == 2 ? -ph.g : (k == 3 ? ph.g : 0.0));
+    const double2 xN = xs[st_of(jx, jy, nx)];
+    const S pN = (S)xN.x, cN = (S)xN.y;
+    const S rhoN = rho0 + drho * cN;
+    const S rhof = (S)0.5 * (rhoP + rhoN);
+    const S q = -kmu * fma_((pN - pP), ihS, sg * rhof);
+    const S Ff = rhof * q * hS;
+    const bool up = Ff >= (S)0;
+    const S cup = up ? cP : cN;
+    const S dif = PD * (cN - cP);
+    Rm += Ff;
+    Rs += fma_(Ff, cup, -rhof * dif);
+    // derivatives of (F, G) w.r.t. the unknowns of P and of the neighbour
+    const T rhofT = (T)rhof, cupT = (T)cup, FfT = (T)Ff, difT = (T)dif;
+    const T dFdp = rhofT * kmuT;
+    const T dFdc = hdT * hT * fma_((T)q, (T)1, -rhofT * kmuT * (T)sg);
+    const T dGdifP = fma_(hdT, difT, -rhofT * PDT);
+    const T dGdifN = fma_(hdT, difT, rhofT * PDT);
+    C00 += dFdp;
+    C01 += dFdc;
+    C10 = fma_(dFdp, cupT, C10);
+    C11 += fma_(dFdc, cupT, (up ? FfT : (T)0) - dGdifP);
+    o.Nb[k][0] = -dFdp;
+    o.Nb[k][1] = dFdc;
+    o.Nb[k][2] = -dFdp * cupT;
+    o.Nb[k][3] = fma_(dFdc, cupT, (up ? (T)0 : FfT) - dGdifN);
+  }
+  if (ix == 0) {  // land side: prescribed inflow of fresh water, c_b = 0
+    const S Fl = -rho0 * (S)(cf.qin * inv_s) * hS;
+    const S rb = (S)0.5 * (rhoP + rho0);
+    const bool up = Fl >= (S)0;
+    Rm += Fl;
+    Rs += fma_(Fl, up ? cP : (S)0, (S)2 * rb * PD * cP);
+    C11 += (up ? (T)Fl : (T)0) + PDT * (T)fma_(drho, cP, (S)2 * rb);
+  }
+  if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
+    const S yP = ((S)iy + (S)0.5) * hS;
+    const S pb = (S)ph.rho1 * (S)ph.g * ((S)ph.Ly - yP);
+    const S rb = (S)0.5 * (rhoP + (S)ph.rho1);
+    const S q = -kmu * (pb - pP) * ((S)2 * ihS);
+    const S Fr = rb * q * hS;
+    const bool up = Fr >= (S)0;
+    const S cup = up ? cP : (S)1;
+    const S dif = PD * ((S)1 - cP);
+    Rm += Fr;
+    Rs += fma_(Fr, cup, -(S)2 * rb * dif);
+    const T dFdp = (T)2 * (T)rb * kmuT;
+    const T dFdc = hdT * (T)q * hT;
+    C00 += dFdp;
+    C01 += dFdc;
+    C10 = fma_(dFdp, (T)cup, C10);
+    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDT));
+  }
+  o.fm = Rm;
+  o.fs = Rs;
+  o.C[0] = C00; o.C[1] = C01; o.C[2] = C10; o.C[3] = C11;
+}
+
+// Store a cell's Jacobian blocks (6 planes with stride `ps`, incl. C^-1).
+template <typename T>
+__device__ __forceinline__ void store_blocks(typename VT<T>::b4* J, int64_t ps, int64_t i, const T C[4],
+                                             const T Nb[4][4]) {
+  typedef typename VT<T>::b4 B4;
+  J[i] = mkblk<B4>(C[0], C[1], C[2], C[3]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) J[(k + 1) * ps + i] = mkblk<B4>(Nb[k][0], Nb[k][1], Nb[k][2], Nb[k][3]);
+  const T idet = (T)1 / (C[0] * C[3] - C[1] * C[2]);
+  J[5 * ps + i] = mkblk<B4>(C[3] * idet, -C[1] * idet, -C[2] * idet, C[0] * idet);
+}
+
 // One thread per cell; FINE: CTAs never straddle samples (N % TPB == 0) and
 // write the per-CTA max |F| (inf for non-finite) to rmax_part[s][ct].
 template <typename T, bool FINE>
 __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
-                                                  double h, double inv_tau, double inv_s,
+                                                  double h, double inv_h, double vt_s, double inv_s,
                                                   const double2* __restrict__ x, const double2* __restrict__ xo,
                                                   const int* __restrict__ active, double2* __restrict__ F,
                                                   typename VT<T>::b4* __restrict__ J, int64_t plane,
                                                   double* __restrict__ rmax_part) {
-  typedef typename VT<T>::b4 B4;
+  typedef typename std::conditional<FINE, double, T>::type S;
   __shared__ double sh[40];
   const int N = nx * ny;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -172,77 +282,10 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
   int ix, iy;
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
-  const Coef cf = coef[s];
-  const double inv_h = 1.0 / h;
-  const double2 xP = x[e], xO = xo[e];
-  const double pP = xP.x, cP = xP.y;
-  const double rhoP = ph.rho0 + ph.drho * cP;
-  const double rhoO = ph.rho0 + ph.drho * xO.y;
-  const double Vt = h * h * inv_tau;
-  double Rm = cf.phi * (rhoP - rhoO) * Vt;
-  double Rs = cf.phi * (rhoP * cP - rhoO * xO.y) * Vt;
-  double C00 = 0.0, C01 = cf.phi * ph.drho * Vt, C10 = 0.0, C11 = cf.phi * (ph.drho * cP + rhoP) * Vt;
-  double Nb[4][4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = 0.0;
-
-  // interior faces W, E, S, N
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
-    const double sg = (k == 2 ? -ph.g : (k == 3 ? ph.g : 0.0));
-    const double2 xN = x[base + st_of(jx, jy, nx)];
-    const double pN = xN.x, cN = xN.y;
-    const double rhoN = ph.rho0 + ph.drho * cN;
-    const double rhof = 0.5 * (rhoP + rhoN);
-    const double q = -cf.kmu * ((pN - pP) * inv_h + sg * rhof);
-    const double Ff = rhof * q * h;
-    const bool up = Ff >= 0.0;
-    const double cup = up ? cP : cN;
-    const double dFdp = rhof * cf.kmu;
-    const double dFdc = 0.5 * ph.drho * q * h - rhof * cf.kmu * 0.5 * ph.drho * sg * h;
-    const double dif = cf.PD * (cN - cP);
-    Rm += Ff;
-    Rs += Ff * cup - rhof * dif;
-    C00 += dFdp;
-    C01 += dFdc;
-    C10 += dFdp * cup;
-    C11 += dFdc * cup + (up ? Ff : 0.0) - (0.5 * ph.drho * dif - rhof * cf.PD);
-    Nb[k][0] = -dFdp;
-    Nb[k][1] = dFdc;
-    Nb[k][2] = -dFdp * cup;
-    Nb[k][3] = dFdc * cup + (up ? 0.0 : Ff) - (0.5 * ph.drho * dif + rhof * cf.PD);
-  }
-  if (ix == 0) {  // land side: prescribed inflow of fresh water, c_b = 0
-    const double Fl = -ph.rho0 * cf.qin * h;
-    const double rb = 0.5 * (rhoP + ph.rho0);
-    const bool up = Fl >= 0.0;
-    Rm += Fl;
-    Rs += Fl * (up ? cP : 0.0) + 2.0 * rb * cf.PD * cP;
-    C11 += (up ? Fl : 0.0) + cf.PD * (ph.drho * cP + 2.0 * rb);
-  }
-  if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
-    const double yP = (iy + 0.5) * h;
-    const double pb = ph.rho1 * ph.g * (ph.Ly - yP);
-    const double rb = 0.5 * (rhoP + ph.rho1);
-    const double q = -cf.kmu * (pb - pP) * (2.0 * inv_h);
-    const double Fr = rb * q * h;
-    const bool up = Fr >= 0.0;
-    const double cup = up ? cP : 1.0;
-    const double dif = cf.PD * (1.0 - cP);
-    const double dFdp = 2.0 * rb * cf.kmu;
-    const double dFdc = 0.5 * ph.drho * q * h;
-    Rm += Fr;
-    Rs += Fr * cup - 2.0 * rb * dif;
-    C00 += dFdp;
-    C01 += dFdc;
-    C10 += dFdp * cup;
-    C11 += dFdc * cup + (up ? Fr : 0.0) - (ph.drho * dif - 2.0 * rb * cf.PD);
-  }
+  CellSys<T, S> o;
+  assemble_cell<T, S>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o);
   if (FINE) {
-    const double fm = Rm * inv_s, fs = Rs * inv_s;
+    const double fm = (double)o.fm, fs = (double)o.fs;
     if (F) F[e] = make_double2(fm, fs);
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
@@ -252,15 +295,7 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
       rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
     }
   }
-  if (J) {
-    const double a = C00 * inv_s, b = C01 * inv_s, c = C10 * inv_s, d = C11 * inv_s;
-    J[e] = mkblk<B4>(a, b, c, d);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      J[(k + 1) * plane + e] = mkblk<B4>(Nb[k][0] * inv_s, Nb[k][1] * inv_s, Nb[k][2] * inv_s, Nb[k][3] * inv_s);
-    const double idet = 1.0 / (a * d - b * c);
-    J[5 * plane + e] = mkblk<B4>(d * idet, -b * idet, -c * idet, a * idet);
-  }
+  if (J) store_blocks<T>(J, plane, e, o.C, o.Nb);
 }
 
 // Coarse states: mean of the 2x2 children (both the iterate and the old state).
@@ -388,14 +423,43 @@ __global__ void k_coarse_solve(int B, const T* __restrict__ Ainv, const typename
 //         x += P x_c followed by the sweep (the swept cells' own old values do
 //         not enter point Gauss-Seidel, and the other colour is overwritten by
 //         the next half-sweep).
+// Cell form: J, b, x point at one sample's arrays (plane stride ps), xc at the
+// sample's coarse vector; i = storage index of the swept cell (ix, iy).
+template <typename T, int MODE>
+__device__ __forceinline__ typename VT<T>::v2 sweep_cell(int nx, int ny, int ix, int iy, int i,
+                                                         const typename VT<T>::b4* J, int64_t ps,
+                                                         const typename VT<T>::v2* b, const typename VT<T>::v2* x,
+                                                         const typename VT<T>::v2* xc) {
+  typedef typename VT<T>::v2 V2;
+  const V2 bb = b[i];
+  T r0 = bb.x, r1 = bb.y;
+  if (MODE != 0) {
+    const int ncx = nx >> 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+      const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+      if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+      V2 xn = x[st_of(jx, jy, nx)];
+      if (MODE == 2) {
+        const V2 cc = xc[st_of(jx >> 1, jy >> 1, ncx)];
+        xn.x += cc.x;
+        xn.y += cc.y;
+      }
+      bmv_sub(J[(k + 1) * ps + i], xn.x, xn.y, r0, r1);
+    }
+  }
+  T y0, y1;
+  bmv(J[5 * ps + i], r0, r1, y0, y1);
+  return mk2<V2>(y0, y1);
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, const typename VT<T>::b4* __restrict__ J,
                                                int64_t plane, const typename VT<T>::v2* __restrict__ b,
                                                typename VT<T>::v2* __restrict__ x,
                                                const typename VT<T>::v2* __restrict__ xc,
                                                const int* __restrict__ active) {
-  typedef typename VT<T>::v2 V2;
-  typedef typename VT<T>::b4 B4;
   const int N = nx * ny, halfN = N >> 1, half = nx >> 1;
   const int64_t t = (int64_t)blockIdx.x * TPB + threadIdx.x;
   if (t >= (int64_t)B * halfN) return;
@@ -405,36 +469,63 @@ __global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, c
   const int iy = u / half, j = u - iy * half;
   const int ix = 2 * j + ((col ^ iy) & 1);
   const int64_t base = (int64_t)s * N;
-  const int64_t e = base + iy * nx + col * half + j;
-  const V2 bb = b[e];
-  T r0 = bb.x, r1 = bb.y;
-  if (MODE != 0) {
-    const int ncx = nx >> 1;
-    const int64_t basec = (int64_t)s * (N >> 2);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-      const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-      if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
-      V2 xn = x[base + st_of(jx, jy, nx)];
-      if (MODE == 2) {
-        const V2 cc = xc[basec + st_of(jx >> 1, jy >> 1, ncx)];
-        xn.x += cc.x;
-        xn.y += cc.y;
-      }
-      bmv_sub(J[(k + 1) * plane + e], xn.x, xn.y, r0, r1);
-    }
-  }
-  const B4 Ci = J[5 * plane + e];
-  T y0, y1;
-  bmv(Ci, r0, r1, y0, y1);
-  x[e] = mk2<V2>(y0, y1);
+  const int i = iy * nx + col * half + j;
+  x[base + i] = sweep_cell<T, MODE>(nx, ny, ix, iy, i, J + base, plane, b + base, x + base,
+                                    MODE == 2 ? xc + (int64_t)s * (N >> 2) : nullptr);
 }
 
-// Residual b - A x restricted by summation over the 2x2 children.  After a
-// red-black sweep the black cells' residuals vanish (point Gauss-Seidel makes
-// each swept equation hold), so RED_ONLY sums the two colour-0 children only;
-// ZERO_X (no pre-smoothing, x = 0) restricts b itself.
+// Residual r_P = b_P - (A x)_P of one cell (sample-relative arrays).
+template <typename T>
+__device__ __forceinline__ void residual_cell(int nx, int ny, int ix, int iy, int i, const typename VT<T>::b4* J,
+                                              int64_t ps, const typename VT<T>::v2* b,
+                                              const typename VT<T>::v2* x, T& r0, T& r1) {
+  typedef typename VT<T>::v2 V2;
+  const V2 bb = b[i], xx = x[i];
+  r0 = bb.x;
+  r1 = bb.y;
+  bmv_sub(J[i], xx.x, xx.y, r0, r1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const V2 xn = x[st_of(jx, jy, nx)];
+    bmv_sub(J[(k + 1) * ps + i], xn.x, xn.y, r0, r1);
+  }
+}
+
+// Residual b - A x restricted by summation over the 2x2 children of coarse
+// cell (IX, IY).  After a red-black sweep the black cells' residuals vanish
+// (point Gauss-Seidel makes each swept equation hold), so MODE 0 sums the two
+// colour-0 children only; MODE 1 (no pre-smoothing, x = 0) restricts b itself.
+template <typename T, int MODE>
+__device__ __forceinline__ typename VT<T>::v2 restrict_cell(int ncx, int ncy, int IX, int IY,
+                                                            const typename VT<T>::b4* J, int64_t ps,
+                                                            const typename VT<T>::v2* b,
+                                                            const typename VT<T>::v2* x) {
+  typedef typename VT<T>::v2 V2;
+  const int nx = 2 * ncx, ny = 2 * ncy;
+  T s0 = 0, s1 = 0;
+  if (MODE == 1) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const V2 bb = b[st_of(2 * IX + (c & 1), 2 * IY + (c >> 1), nx)];
+      s0 += bb.x;
+      s1 += bb.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int ix = 2 * IX + c, iy = 2 * IY + c;  // (0,0) and (1,1): colour 0
+      T r0, r1;
+      residual_cell<T>(nx, ny, ix, iy, st_of(ix, iy, nx), J, ps, b, x, r0, r1);
+      s0 += r0;
+      s1 += r1;
+    }
+  }
+  return mk2<V2>(s0, s1);
+}
+
 template <typename T, int MODE>  // MODE 0: RED_ONLY, 1: ZERO_X
 __global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int ncy,
                                                            const typename VT<T>::b4* __restrict__ J, int64_t plane,
@@ -442,7 +533,6 @@ __global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int n
                                                            const typename VT<T>::v2* __restrict__ x,
                                                            typename VT<T>::v2* __restrict__ bc,
                                                            const int* __restrict__ active) {
-  typedef typename VT<T>::v2 V2;
   const int Nc = ncx * ncy;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   if (e >= (int64_t)B * Nc) return;
@@ -451,37 +541,8 @@ __global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int n
   const int stc = (int)(e - (int64_t)s * Nc);
   int IX, IY;
   xy_of(stc, ncx, IX, IY);
-  const int nx = 2 * ncx, ny = 2 * ncy;
   const int64_t base = (int64_t)s * Nc * 4;
-  T s0 = 0, s1 = 0;
-  if (MODE == 1) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const V2 bb = b[base + st_of(2 * IX + (c & 1), 2 * IY + (c >> 1), nx)];
-      s0 += bb.x;
-      s1 += bb.y;
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int ix = 2 * IX + c, iy = 2 * IY + c;  // (0,0) and (1,1): colour 0
-      const int64_t i = base + st_of(ix, iy, nx);
-      const V2 bb = b[i], xx = x[i];
-      T r0 = bb.x, r1 = bb.y;
-      bmv_sub(J[i], xx.x, xx.y, r0, r1);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-        const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-        if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
-        const V2 xn = x[base + st_of(jx, jy, nx)];
-        bmv_sub(J[(k + 1) * plane + i], xn.x, xn.y, r0, r1);
-      }
-      s0 += r0;
-      s1 += r1;
-    }
-  }
-  bc[e] = mk2<V2>(s0, s1);
+  bc[e] = restrict_cell<T, MODE>(ncx, ncy, IX, IY, J + base, plane, b + base, x + base);
 }
 
 // x += P x_c (used only when there is no post-smoothing to fuse it into).
@@ -511,7 +572,27 @@ __global__ void __launch_bounds__(TPB) k_zero(int64_t n, typename VT<T>::v2* __r
 }
 
 // ---------------------------------------------------------------------------
-// a8: y = A x (fine level, all cells) with per-CTA partial dot products:
+// a8: y_P = (A x)_P of one cell (sample-relative arrays).
+template <typename T>
+__device__ __forceinline__ typename VT<T>::v2 spmv_cell(int nx, int ny, int ix, int iy, int i,
+                                                        const typename VT<T>::b4* J, int64_t ps,
+                                                        const typename VT<T>::v2* x) {
+  typedef typename VT<T>::v2 V2;
+  const V2 xx = x[i];
+  T r0, r1;
+  bmv(J[i], xx.x, xx.y, r0, r1);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
+    const V2 xn = x[st_of(jx, jy, nx)];
+    bmv_add(J[(k + 1) * ps + i], xn.x, xn.y, r0, r1);
+  }
+  return mk2<V2>(r0, r1);
+}
+
+// y = A x (fine level, all cells) with per-CTA partial dot products:
 //   NDOT 1: <w1, y>;  NDOT 2: <w1, y>, <y, y>.
 template <typename T, int NDOT>
 __global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typename VT<T>::b4* __restrict__ J,
@@ -529,24 +610,14 @@ __global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typen
   int ix, iy;
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
-  const V2 xx = x[e];
-  T r0, r1;
-  bmv(J[e], xx.x, xx.y, r0, r1);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int jx = ix + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-    const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-    if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
-    const V2 xn = x[base + st_of(jx, jy, nx)];
-    bmv_add(J[(k + 1) * plane + e], xn.x, xn.y, r0, r1);
-  }
-  y[e] = mk2<V2>(r0, r1);
+  const V2 yy = spmv_cell<T>(nx, ny, ix, iy, st, J + base, plane, x + base);
+  y[e] = yy;
   if (NDOT >= 1 && part) {
+    // per-cell products in T, widened once for the FP64 CTA reduction
     const V2 ww = w1[e];
-    double d1 = (double)ww.x * (double)r0 + (double)ww.y * (double)r1;
-    d1 = block_reduce<false>(d1, sh);
+    const double d1 = block_reduce<false>((double)fma_(ww.x, yy.x, ww.y * yy.y), sh);
     double d2 = 0.0;
-    if (NDOT == 2) d2 = block_reduce<false>((double)r0 * (double)r0 + (double)r1 * (double)r1, sh);
+    if (NDOT == 2) d2 = block_reduce<false>((double)fma_(yy.x, yy.x, yy.y * yy.y), sh);
     if (threadIdx.x == 0) {
       const int64_t pi = (int64_t)s * nct + st / TPB, stride = (int64_t)B * nct;
       part[slot1 * stride + pi] = d1;
@@ -581,8 +652,7 @@ __global__ void __launch_bounds__(TPB) k_bicg_init(int B, int N, const double2* 
   p[e] = z;
   v[e] = z;
   dx[e] = z;
-  const double d = (double)rr.x * (double)rr.x + (double)rr.y * (double)rr.y;
-  const double bs = block_reduce<false>(d, sh);
+  const double bs = block_reduce<false>((double)fma_(rr.x, rr.x, rr.y * rr.y), sh);
   if (threadIdx.x == 0) {
     const int64_t pi = (int64_t)s * nct + (e - (int64_t)s * N) / TPB, stride = (int64_t)B * nct;
     part[P_RR * stride + pi] = bs;
@@ -697,8 +767,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
   dx[e] = mk2<V2>(x0.x + a * p0.x + w * s0.x, x0.y + a * p0.y + w * s0.y);
   const V2 rn = mk2<V2>(sv0.x - w * t0.x, sv0.y - w * t0.y);
   r[e] = rn;
-  const double d1 = block_reduce<false>((double)rh0.x * (double)rn.x + (double)rh0.y * (double)rn.y, sh);
-  const double d2 = block_reduce<false>((double)rn.x * (double)rn.x + (double)rn.y * (double)rn.y, sh);
+  const double d1 = block_reduce<false>((double)fma_(rh0.x, rn.x, rh0.y * rn.y), sh);
+  const double d2 = block_reduce<false>((double)fma_(rn.x, rn.x, rn.y * rn.y), sh);
   if (threadIdx.x == 0) {
     const int64_t pi = (int64_t)s * nct + ct;
     part[P_RR * stride + pi] = d1;

@@ -25,7 +25,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
-                  "spmv", "krylov", "newton", "qoi")
+                  "spmv", "krylov", "newton", "qoi", "fused")
 
 
 class HenryConfig(ctypes.Structure):
@@ -35,7 +35,8 @@ class HenryConfig(ctypes.Structure):
                [(n, ctypes.c_int32) for n in ("nx0", "ny0", "steps0", "max_level", "precision", "coarse_op")] + \
                [(n, ctypes.c_double) for n in ("newton_atol", "newton_dxtol", "lin_rtol")] + \
                [(n, ctypes.c_int32) for n in ("newton_maxit", "lin_maxit", "nu1", "nu2")] + \
-               [("workspace_bytes", ctypes.c_double), ("newton_predictor", ctypes.c_double)]
+               [("workspace_bytes", ctypes.c_double), ("newton_predictor", ctypes.c_double),
+                ("fused_small_grids", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -81,7 +82,8 @@ def lib():
         L.henry_linear_solve.argtypes = [P, I, P, I, P, P, P, P, P, P]
         L.henry_level_batch_solve_static.argtypes = [ctypes.POINTER(HenryConfig), I, I, P, I, P, P, P, P]
         L.henry_profile.argtypes = [P, I]
-        L.henry_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D)]
+        L.henry_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
+                                         ctypes.POINTER(D)]
         for name in EXPORTS:
             f = getattr(L, name)
             if name not in ("henry_default_config", "henry_destroy", "henry_last_error"):
@@ -194,12 +196,13 @@ class Solver:
         _check(lib().henry_profile(self._h, 1 if enable else 0))
 
     def profile_read(self):
-        """{class: (ms, launches, algorithmic bytes)} since the last reset."""
+        """{class: (ms, launches, algorithmic bytes, algorithmic flops)} since the last reset."""
         out = {}
         for k, name in enumerate(KERNEL_CLASSES):
-            ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
-            _check(lib().henry_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
-            out[name] = (ms.value, n.value, b.value)
+            ms, n, b, f = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            _check(lib().henry_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                            ctypes.byref(f)))
+            out[name] = (ms.value, n.value, b.value, f.value)
         return out
 
     def grid(self, level):

@@ -184,7 +184,11 @@ def _qoi_check(q_gpu, q_ref):
     np.testing.assert_allclose(q_gpu[:, 1], q_ref[:, 1], rtol=0, atol=1e-10)
 
 
-def test_level0_batch_solve_matches_oracle(hl, solver):
+@pytest.mark.parametrize("fused,precision", [(2, 0), (0, 0), (1, 1), (0, 1)])
+def test_level0_batch_solve_matches_oracle(hl, fused, precision):
+    """Level 0 through the fused one-CTA-per-sample solver and through the
+    multi-kernel path, in FP64 and mixed precision."""
+    solver = hl.Solver(fused_small_grids=fused, precision=precision)
     n = 16
     xi_d = hl.sample_xi(inputs.SEED, 0, 0, n)
     qf, qc, st, stats = solver.level_batch_solve(0, xi_d)
@@ -195,6 +199,20 @@ def test_level0_batch_solve_matches_oracle(hl, solver):
     _qoi_check(qf.cpu().numpy(), ref)
     assert stats["cell_steps"] == n * 512 * 20
     assert stats["newton_iters"] >= n * 20 and stats["linear_iters"] > 0
+    solver.close()
+
+
+def test_fused_and_multikernel_paths_agree(hl):
+    n = 40
+    xi_d = hl.sample_xi(inputs.SEED, 0, 300, n)
+    a = hl.Solver(fused_small_grids=2)
+    b = hl.Solver(fused_small_grids=0)
+    qa, _, sa, _ = a.level_batch_solve(0, xi_d)
+    qb, _, sb, _ = b.level_batch_solve(0, xi_d)
+    assert int(sa.abs().sum()) == 0 and int(sb.abs().sum()) == 0
+    _qoi_check(qa.cpu().numpy(), qb.cpu().numpy())
+    a.close()
+    b.close()
 
 
 def test_level1_with_coarse_partner(hl, solver):
