@@ -67,6 +67,21 @@ enum {
  * MLMC sums are FP64 in both). */
 enum { HENRY_FP64 = 0, HENRY_MIXED = 1 /* FP32 Jacobian, BiCGStab and V-cycle */ };
 
+/* Coefficient models (the random inputs per sample and their meaning):
+ *  UNIFORM3 (default): xi[3] uniform on [-1, 1]; phi = phi_mean (1 + phi_amp xi1),
+ *    K = K_mean exp(logK_amp xi2), q_in = qin_mean (1 + qin_amp xi3), all constant in space.
+ *  KL: xi[2 kl_terms + 1] = (theta_K[kl_terms], theta_phi[kl_terms], xi3): Gaussian random
+ *    fields log K = log K_mean + kl_sigma_logK sum_t sqrt(lam_t) theta_K,t psi_t(x, y) and
+ *    phi = clip(phi_mean + kl_sigma_phi sum_t sqrt(lam_t) theta_phi,t psi_t, phi_lo, phi_hi),
+ *    the kl_terms leading Karhunen-Loeve terms of the covariance exp(-r^2 / (2 kl_corr_len^2))
+ *    on [0, Lx] x [0, Ly] (Nystrom on 256 Gauss-Legendre nodes per direction; theta iid N(0, 1)
+ *    supplied by the caller); q_in as above.
+ *  TWO_LAYER: xi[3] uniform; the paper's two-layer porosity, Eq. (poro_2levels), with the
+ *    Kozeny-Carman permeability, Eq. (e_perm_Kozeny_Carman), K = kappa phi^3 / (1 - phi^2),
+ *    kappa such that K(phi_mean) = K_mean; q_in = qin_mean (1 + qin_amp xi3).
+ * The field models use harmonic means of K and phi Dm on faces. */
+enum { HENRY_MODEL_UNIFORM3 = 0, HENRY_MODEL_KL = 1, HENRY_MODEL_TWO_LAYER = 2 };
+
 /* Coarse-grid operators of the multigrid hierarchy. */
 enum { HENRY_COARSE_REDISCRETISE = 0, HENRY_COARSE_GALERKIN = 1 };
 
@@ -100,7 +115,10 @@ typedef struct {
                               (0: x^n; default 1, linear extrapolation in time) */
   int32_t fused_small_grids; /* grids of <= 512 cells solved by one CTA per sample with the whole hierarchy in
                                 shared memory: 1 (default) in HENRY_MIXED only, 2 also in HENRY_FP64,
-                                0 never (always the multi-kernel path) */
+                                0 never (always the multi-kernel path); not used by the field models */
+  int32_t coef_model;        /* HENRY_MODEL_* */
+  int32_t kl_terms;          /* KL terms per field (default 32) */
+  double kl_corr_len, kl_sigma_logK, kl_sigma_phi, phi_lo, phi_hi; /* 0.3 m, 0.5, 0.1, 0.05, 0.65 */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -126,7 +144,7 @@ void henry_destroy(henry_handle* h);
 /* Message of the last error on this thread ("" if none). */
 const char* henry_last_error(void);
 
-/* a1. Sample xi[n][3] for samples first_sample .. first_sample + n - 1 of
+/* a1. Sample xi[n][3] (the UNIFORM3 and TWO_LAYER inputs) for samples first_sample .. first_sample + n - 1 of
  * MLMC level `level` with Philox4x32-10 (Salmon et al., SC'11) keyed by the
  * two 32-bit halves of `seed`; sample s uses counters (level, lo32(s),
  * hi32(s), 0) -> xi1 from words (0,1), xi2 from words (2,3) and (level,
@@ -136,7 +154,7 @@ const char* henry_last_error(void);
 int henry_sample_xi(uint64_t seed, int level, uint64_t first_sample, int n, double* xi_dev, void* stream);
 
 /* a2-a11. Solve n scenarios at MLMC level `level` (0 <= level <= max_level)
- * for inputs xi_dev[n][3] and write the QoIs at T to qoi_fine_dev[n][2].
+ * for inputs xi_dev[n][n_xi] (n_xi = 3, or 2 kl_terms + 1 for HENRY_MODEL_KL) and write the QoIs at T to qoi_fine_dev[n][2].
  * If with_coarse != 0 (level >= 1) also solve the same xi on level - 1 (the
  * coarse partner of the telescoping difference, Eq. (A): same xi, grid and
  * time step of the coarser level) into qoi_coarse_dev[n][2].

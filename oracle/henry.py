@@ -135,6 +135,32 @@ def coefficients(prm: Params, grid: Grid, xi) -> Coeffs:
     return Coeffs(phi=np.full(shape, phi), K=np.full(shape, K), qin=qin)
 
 
+def kozeny_carman_kappa(K_mean, phi_mean):
+    """kappa_KC with K(E[phi]) = K_mean for K(phi) = kappa phi^3 / (1 - phi^2)
+    (Eq. e_perm_Kozeny_Carman and the sentence after it)."""
+    return K_mean * (1.0 - phi_mean ** 2) / phi_mean ** 3
+
+
+def coefficients_two_layer(prm: Params, grid: Grid, xi) -> Coeffs:
+    """The paper's random porosity, Eq. (poro_2levels): two horizontal layers,
+    phi = phi_mean (1 + 0.15 (xi2 cos(pi x / 2) + xi2 sin(2 pi y) + xi1 cos(2 pi x))) C0(xi1),
+    C0 = 1 + 0.2 xi1 below y = -0.75 and 1 - 0.2 xi1 above (paper coordinates,
+    y in [-1, 0]: y_paper = y - Ly here), K = K(phi) by Kozeny-Carman, and the
+    recharge q_in = qin_mean (1 + qin_amp xi3) (Sec. 4; xi2 appears twice and
+    xi3 only in the recharge, as printed)."""
+    xi1, xi2, xi3 = float(xi[0]), float(xi[1]), float(xi[2])
+    x = (np.arange(grid.nx) + 0.5) * grid.h
+    yp = (np.arange(grid.ny) + 0.5) * grid.h - prm.Ly
+    X, Y = np.meshgrid(x, yp)
+    C0 = np.where(Y < -0.75, 1.0 + 0.2 * xi1, 1.0 - 0.2 * xi1)
+    phi = prm.phi_mean * (1.0 + 0.15 * (xi2 * np.cos(np.pi * X / 2.0) + xi2 * np.sin(2.0 * np.pi * Y)
+                                        + xi1 * np.cos(2.0 * np.pi * X))) * C0
+    kappa = kozeny_carman_kappa(prm.K_mean, prm.phi_mean)
+    K = kappa * phi ** 3 / (1.0 - phi ** 2)
+    qin = prm.qin_mean * (1.0 + prm.qin_amp * xi3)
+    return Coeffs(phi=phi, K=K, qin=qin)
+
+
 def initial_state(prm: Params, grid: Grid):
     """c = 0 and fresh-water hydrostatic pressure p = rho0 g (Ly - y) at cell centres."""
     y = (np.arange(grid.ny) + 0.5) * grid.h
@@ -400,11 +426,23 @@ def qoi(prm, grid, coef, p, c):
     return mass, cpt
 
 
-def solve_scenario(prm, level, xi, return_state=False, stats=None):
+def coefficient_model(model):
+    """'uniform3' (default), 'kl' (oracle.kl) or 'two_layer'."""
+    if model == "uniform3":
+        return coefficients
+    if model == "two_layer":
+        return coefficients_two_layer
+    if model == "kl":
+        from . import kl
+        return kl.coefficients_kl
+    raise ValueError(model)
+
+
+def solve_scenario(prm, level, xi, return_state=False, stats=None, model="uniform3"):
     """All r_l implicit-Euler steps of one scenario at MLMC level ``level`` for
     random input ``xi``; returns (mass, c_point) and a convergence flag."""
     grid = Grid.level(prm, level)
-    coef = coefficients(prm, grid, xi)
+    coef = coefficient_model(model)(prm, grid, xi)
     p, c = initial_state(prm, grid)
     ok = True
     for _ in range(grid.steps):
@@ -416,13 +454,13 @@ def solve_scenario(prm, level, xi, return_state=False, stats=None):
     return q, ok
 
 
-def solve_scenarios(prm, level, xis, stats=None):
+def solve_scenarios(prm, level, xis, stats=None, model="uniform3"):
     """Sequential loop over samples: returns q[n][2] and ok[n]."""
     xis = np.asarray(xis, dtype=np.float64)
     out = np.empty((xis.shape[0], 2))
     ok = np.empty(xis.shape[0], dtype=bool)
     for i, xi in enumerate(xis):
-        q, o = solve_scenario(prm, level, xi, stats=stats)
+        q, o = solve_scenario(prm, level, xi, stats=stats, model=model)
         out[i] = q
         ok[i] = o
     return out, ok

@@ -29,6 +29,7 @@
 #include "henry_kernels.cuh"
 #include "henry_misc.cuh"
 #include "henry_cta.cuh"
+#include "henry_kl.cuh"
 
 using namespace hk;
 
@@ -64,6 +65,8 @@ struct Level {
   int nx, ny, N;
   double h;
   double2 *x, *xo;  // state (fine: Newton iterate; coarse: restricted) and old state
+  double2* cc;      // per-cell (phi, K / mu) of the field models (else null)
+  double4* fc;      // per-cell east/north face harmonic means of the field models (else null)
   void* J;          // 6 planes of B4
   void *mgx, *mgb;  // multigrid vectors (coarse levels)
   int64_t plane;
@@ -103,7 +106,7 @@ struct Group {
   // Lay out (or size, with base == nullptr) the workspace for B samples.
   // `light`: only what the fused small-grid solver uses (fine old state,
   // coefficients, status, counters); every other pointer is left null.
-  size_t carve(char* base, int B, int nx0, int ny0, double h0, bool light_ws = false) {
+  size_t carve(char* base, int B, int nx0, int ny0, double h0, bool light_ws = false, bool fields = false) {
     Carver c{base, 0};
     std::vector<Level> L;
     int nx = nx0, ny = ny0;
@@ -114,6 +117,12 @@ struct Group {
       l.plane = (int64_t)B * l.N;
       l.x = l.xo = nullptr;
       l.J = l.mgx = l.mgb = nullptr;
+      l.cc = nullptr;
+      l.fc = nullptr;
+      if (fields) {
+        l.cc = c.take<double2>(sizeof(double2) * l.plane);
+        l.fc = c.take<double4>(sizeof(double4) * l.plane);
+      }
       if (light_ws) {
         if (L.empty()) l.xo = c.take<double2>(sizeof(double2) * l.plane);
       } else {
@@ -180,8 +189,20 @@ struct Prof {
   double flops[HENRY_K_COUNT] = {};
 };
 
+// Device copies of the KL basis evaluated at one grid's cell centres.
+struct KLTables {
+  int nx = 0, ny = 0;
+  int* ti = nullptr;
+  int* tj = nullptr;
+  double* sl = nullptr;
+  double* psx = nullptr;  // [m][nx]
+  double* psy = nullptr;  // [m][ny]
+};
+
 struct henry_handle {
   henry_config cfg;
+  hkl::Basis2D* kl = nullptr;
+  std::map<int, KLTables> kl_tables;  // by MLMC level
   std::map<int, Group<double>> g64;
   std::map<int, Group<float>> g32;
   int* host_counter = nullptr;  // pinned
@@ -252,10 +273,13 @@ void prof_drain(henry_handle* H) {
   P.pend.clear();
 }
 
+bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
+int n_inputs(const henry_config& c) { return c.coef_model == HENRY_MODEL_KL ? 2 * c.kl_terms + 1 : 3; }
+
 Phys phys_of(const henry_config& c) {
 
   Phys p;
-  p.rho0 = c.rho0; p.rho1 = c.rho1; p.drho = c.rho1 - c.rho0; p.g = c.g; p.Ly = c.Ly;
+  p.rho0 = c.rho0; p.rho1 = c.rho1; p.drho = c.rho1 - c.rho0; p.g = c.g; p.Ly = c.Ly; p.Dm = c.Dm;
   return p;
 }
 
@@ -277,7 +301,7 @@ template <typename T>
 size_t bytes_per_sample(const henry_config& c, int level, bool light = false) {
   Group<T> g;
   LevelGeom lg = geom(c, level);
-  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h, light);
+  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h, light, has_fields(c));
 }
 
 // The fused one-CTA-per-sample solver is used when enabled, the sample's
@@ -289,7 +313,7 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   // 1 (default): only with FP32 linear algebra, where it measured faster; on
   // GB300 the FP64 variant (one CTA per SM for lack of shared memory) is
   // FP64-latency bound and slower than the multi-kernel path.  2: always.
-  if (c.fused_small_grids <= 0) return false;
+  if (c.fused_small_grids <= 0 || has_fields(c)) return false;
   if (c.fused_small_grids == 1 && sizeof(T) != sizeof(float)) return false;
   const LevelGeom lg = geom(c, level);
   if (!cta_layout(lg.nx, lg.ny, (int)sizeof(T), L)) return false;
@@ -329,7 +353,7 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out, bool light = fa
     g.mem = nullptr;
   }
   LevelGeom lg = geom(H->cfg, level);
-  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h, light);
+  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h, light, has_fields(H->cfg));
   char* mem = nullptr;
   if (cudaMalloc(&mem, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -337,7 +361,7 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out, bool light = fa
   }
   g.mem = mem;
   g.bytes = bytes;
-  g.carve(mem, B, lg.nx, lg.ny, lg.h, light);
+  g.carve(mem, B, lg.nx, lg.ny, lg.h, light, has_fields(H->cfg));
   g.level = level;
   g.Bcap = B;
   *out = &g;
@@ -352,15 +376,84 @@ int max_batch(const henry_config& c, int level, bool light = false) {
 }
 
 // Coefficients from xi for B samples (writes coef and status).
+// KL basis (once per handle) and its tables at the cell centres of the fine
+// grid of `level` (once per level), on the device.
+int ensure_kl_tables(henry_handle* H, int level, KLTables** out) {
+  const henry_config& c = H->cfg;
+  if (!H->kl) {
+    H->kl = new hkl::Basis2D();
+    H->kl->build(c.Lx, c.Ly, c.kl_terms, c.kl_corr_len);
+  }
+  KLTables& t = H->kl_tables[level];
+  const LevelGeom lg = geom(c, level);
+  if (!t.psx) {
+    const hkl::Basis2D& b = *H->kl;
+    const int m = std::max(b.bx.m, b.by.m);
+    std::vector<double> px((size_t)m * lg.nx, 0.0), py((size_t)m * lg.ny, 0.0);
+    for (int i = 0; i < b.bx.m; ++i)
+      for (int ix = 0; ix < lg.nx; ++ix) px[(size_t)i * lg.nx + ix] = b.bx.eval(i, (ix + 0.5) * lg.h);
+    for (int j = 0; j < b.by.m; ++j)
+      for (int iy = 0; iy < lg.ny; ++iy) py[(size_t)j * lg.ny + iy] = b.by.eval(j, (iy + 0.5) * lg.h);
+    CK(cudaMalloc(&t.ti, sizeof(int) * b.terms));
+    CK(cudaMalloc(&t.tj, sizeof(int) * b.terms));
+    CK(cudaMalloc(&t.sl, sizeof(double) * b.terms));
+    CK(cudaMalloc(&t.psx, sizeof(double) * px.size()));
+    CK(cudaMalloc(&t.psy, sizeof(double) * py.size()));
+    CK(cudaMemcpy(t.ti, b.ti.data(), sizeof(int) * b.terms, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.tj, b.tj.data(), sizeof(int) * b.terms, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.sl, b.sqrt_lam.data(), sizeof(double) * b.terms, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.psx, px.data(), sizeof(double) * px.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(t.psy, py.data(), sizeof(double) * py.size(), cudaMemcpyHostToDevice));
+    t.nx = lg.nx;
+    t.ny = lg.ny;
+  }
+  *out = &t;
+  return HENRY_OK;
+}
+
+// Coefficients from the random inputs for B samples (writes coef and
+// status; for the field models also the per-cell and face coefficients of
+// every multigrid level).
 template <typename T>
 int set_coefficients(henry_handle* H, Group<T>& G, const double* xi, int B, cudaStream_t st) {
   const henry_config& c = H->cfg;
-  CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
-  launch(H, st, HENRY_K_QOI, (double)B * (24 + 32 + 4),
-         [&] { k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status); });
+  if (!has_fields(c)) {
+    CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
+    launch(H, st, HENRY_K_QOI, (double)B * (24 + 32 + 4),
+           [&] { k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status); });
+    CKL();
+    return HENRY_OK;
+  }
+  const int nin = n_inputs(c);
+  Level& L0 = G.lv[0];
+  const int64_t n0 = (int64_t)B * L0.N;
+  k_coefficients_qin<<<nblk(B, 128), 128, 0, st>>>(B, nin, nin - 1, c.qin_mean, c.qin_amp, xi, G.coef, G.status);
   CKL();
+  if (c.coef_model == HENRY_MODEL_KL) {
+    KLTables* t = nullptr;
+    int rc = ensure_kl_tables(H, G.level, &t);
+    if (rc) return rc;
+    KLParams P{c.kl_terms, nin, 0, c.K_mean, c.kl_sigma_logK, c.phi_mean, c.kl_sigma_phi, c.phi_lo, c.phi_hi, c.mu};
+    k_fields_kl<<<nblk(n0), TPB, 0, st>>>(P, B, L0.nx, L0.ny, xi, t->ti, t->tj, t->sl, t->psx, t->psy, L0.cc,
+                                          G.status);
+  } else {
+    const double pm = c.phi_mean;
+    TwoLayerParams P{nin, pm, c.K_mean * (1.0 - pm * pm) / (pm * pm * pm), c.mu, c.Ly, -0.75};
+    k_fields_two_layer<<<nblk(n0), TPB, 0, st>>>(P, B, L0.nx, L0.ny, L0.h, xi, L0.cc, G.status);
+  }
+  CKL();
+  for (size_t k = 0; k < G.lv.size(); ++k) {
+    Level& L = G.lv[k];
+    if (k > 0) {
+      k_restrict_cc<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, G.lv[k - 1].cc, L.cc);
+      CKL();
+    }
+    k_face_coefs<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, c.Dm, L.cc, L.fc);
+    CKL();
+  }
   return HENRY_OK;
 }
+
 
 // Coarse-grid operators for every multigrid level below the fine one, plus
 // the coarsest inverse.  Expects lv[k].x for k >= 1 up to date when
@@ -380,10 +473,15 @@ int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double
       });
     } else {
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
-        k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
-                                                                      L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                                      G.lin_active, nullptr, (B4*)L.J, L.plane,
-                                                                      nullptr);
+        if (L.cc)
+          k_assemble<T, false, true><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+              ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h, L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo, G.lin_active,
+              nullptr, (B4*)L.J, L.plane, nullptr, L.cc, L.fc);
+        else
+          k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
+                                                                        L.h * L.h * inv_tau * inv_s, inv_s, L.x,
+                                                                        L.xo, G.lin_active, nullptr, (B4*)L.J,
+                                                                        L.plane, nullptr);
       });
     }
     CKL();
@@ -590,9 +688,15 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
     for (int it = 0; it <= c.newton_maxit; ++it) {
       CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
       launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
-        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                       lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
+        if (L.cc)
+          k_assemble<T, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                               lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                               G.newton_active, G.F, (B4*)L.J, L.plane, pmax, L.cc,
+                                                               L.fc);
+        else
+          k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                         lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                         G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
       });
       launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
         k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
@@ -622,7 +726,7 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
     }
   }
   launch(H, st, HENRY_K_QOI, (double)n0 * 16, [&] {
-    k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi);
+    k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc);
   });
   CKL();
   return HENRY_OK;
@@ -683,7 +787,7 @@ int batch_solve_level(henry_handle* H, int level, const double* xi, int n, doubl
     Group<T>* G = nullptr;
     int rc = get_group<T>(H, level, std::min(Bmax, n), &G, fused);
     if (rc) return rc;
-    rc = set_coefficients<T>(H, *G, xi + 3 * (int64_t)off, B, st);
+    rc = set_coefficients<T>(H, *G, xi + (int64_t)n_inputs(H->cfg) * off, B, st);
     if (rc) return rc;
     rc = fused ? solve_group_fused<T>(H, *G, B, CL, qoi + 2 * (int64_t)off, st)
                : solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
@@ -731,10 +835,15 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
   const double inv_tau = 1.0 / lg.tau;
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   Level& L = G.lv[0];
-  k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                               lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                               G.newton_active, G.F, (B4*)L.J, L.plane,
-                                                               G.part + P_MAX * (int64_t)n * G.nct);
+  if (L.cc)
+    k_assemble<T, true, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+        phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+        G.newton_active, G.F, (B4*)L.J, L.plane, G.part + P_MAX * (int64_t)n * G.nct, L.cc, L.fc);
+  else
+    k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                                 lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                                 G.newton_active, G.F, (B4*)L.J, L.plane,
+                                                                 G.part + P_MAX * (int64_t)n * G.nct);
   CKL();
   if (!coarse) return HENRY_OK;
   int rc = restrict_states<T>(H, G, n, true, G.lin_active, st);
@@ -825,6 +934,13 @@ void henry_default_config(henry_config* c) {
   c->workspace_bytes = 16.0e9;
   c->newton_predictor = 1.0;
   c->fused_small_grids = 1;
+  c->coef_model = HENRY_MODEL_UNIFORM3;
+  c->kl_terms = 32;
+  c->kl_corr_len = 0.3;
+  c->kl_sigma_logK = 0.5;
+  c->kl_sigma_phi = 0.1;
+  c->phi_lo = 0.05;
+  c->phi_hi = 0.65;
 }
 
 int henry_create(const henry_config* cfg, henry_handle** out) {
@@ -841,6 +957,12 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
   if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
   if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
     return set_err(HENRY_EINVAL, "bad coarse_op");
+  if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
+    return set_err(HENRY_EINVAL, "bad coef_model");
+  if (c.coef_model == HENRY_MODEL_KL &&
+      (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
+       !(c.phi_lo < c.phi_hi)))
+    return set_err(HENRY_EINVAL, "bad random-field settings");
   if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
       c.lin_rtol <= 0 || c.workspace_bytes <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0))
     return set_err(HENRY_EINVAL, "bad solver settings");
@@ -862,6 +984,14 @@ void henry_destroy(henry_handle* h) {
     if (kv.second.mem) cudaFree(kv.second.mem);
   for (auto& kv : h->g32)
     if (kv.second.mem) cudaFree(kv.second.mem);
+  for (auto& kv : h->kl_tables) {
+    cudaFree(kv.second.ti);
+    cudaFree(kv.second.tj);
+    cudaFree(kv.second.sl);
+    cudaFree(kv.second.psx);
+    cudaFree(kv.second.psy);
+  }
+  delete h->kl;
   if (h->host_counter) cudaFreeHost(h->host_counter);
   if (h->host_totals) cudaFreeHost(h->host_totals);
   delete h;
@@ -1074,6 +1204,12 @@ int static_check_config(const henry_config& c) {
   if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
   if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
     return set_err(HENRY_EINVAL, "bad coarse_op");
+  if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
+    return set_err(HENRY_EINVAL, "bad coef_model");
+  if (c.coef_model == HENRY_MODEL_KL &&
+      (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
+       !(c.phi_lo < c.phi_hi)))
+    return set_err(HENRY_EINVAL, "bad random-field settings");
   if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
       c.lin_rtol <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0))
     return set_err(HENRY_EINVAL, "bad solver settings");
@@ -1130,6 +1266,8 @@ extern "C" int henry_level_batch_solve_static(const henry_config* cfg, int level
   if (!cfg) return set_err(HENRY_EINVAL, "cfg is NULL");
   int rc = static_check_config(*cfg);
   if (rc) return rc;
+  if (cfg->coef_model != HENRY_MODEL_UNIFORM3)
+    return set_err(HENRY_EINVAL, "the static-scratch solve supports the three-parameter model only");
   if (level < 0 || level > cfg->max_level) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, cfg->max_level);
   if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
   if (!xi_dev || !qoi_fine_dev || !status_dev) return set_err(HENRY_EINVAL, "NULL device pointer");

@@ -48,7 +48,7 @@ __device__ __forceinline__ V2 mk2(T a, T b) { V2 v; v.x = a; v.y = b; return v; 
 
 // Physics constants passed by value.
 struct Phys {
-  double rho0, rho1, drho, g, Ly;
+  double rho0, rho1, drho, g, Ly, Dm;
 };
 
 // Per-sample coefficients: porosity, K / mu, phi * Dm, inflow velocity.
@@ -164,11 +164,25 @@ struct CellSys {
   T Nb[4][4];    // W, E, S, N blocks
 };
 
-template <typename T, typename S>
+// FIELDS: per-cell coefficients instead of the sample's scalars: cc[st] =
+// (phi, K/mu) of the cell and fc[st] = (K/mu, phi Dm) harmonic means on its
+// east face (.x, .y) and north face (.z, .w), zero across the boundary.
+template <typename T, typename S, bool FIELDS = false>
 __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, int nx, int ny, double h, double inv_h,
                                               double vt_s, double inv_s, const double2* xs, const double2* xos,
-                                              int st, int ix, int iy, CellSys<T, S>& o) {
-  const S kmu = (S)(cf.kmu * inv_s), PD = (S)(cf.PD * inv_s), phi = (S)cf.phi;
+                                              int st, int ix, int iy, CellSys<T, S>& o,
+                                              const double2* cc = nullptr, const double4* fc = nullptr) {
+  S kmu, PD, phi;
+  if (FIELDS) {
+    const double2 c = cc[st];
+    phi = (S)c.x;
+    kmu = (S)(c.y * inv_s);
+    PD = (S)(c.x * ph.Dm * inv_s);
+  } else {
+    kmu = (S)(cf.kmu * inv_s);
+    PD = (S)(cf.PD * inv_s);
+    phi = (S)cf.phi;
+  }
   const S hS = (S)h, ihS = (S)inv_h, drho = (S)ph.drho, rho0 = (S)ph.rho0;
   const double2 xP = xs[st], xO = xos[st];
   const S pP = (S)xP.x, cP = (S)xP.y, cO = (S)xO.y;
@@ -180,7 +194,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
   T C00 = (T)0, C01 = (T)(phi * drho * vt), C10 = (T)0, C11 = (T)(phi * (drho * cP + rhoP) * vt);
 #pragma unroll
   for (int k = 0; k < 4; ++k) o.Nb[k][0] = o.Nb[k][1] = o.Nb[k][2] = o.Nb[k][3] = (T)0;
-  const T kmuT = (T)kmu, PDT = (T)PD, hT = (T)h, hdT = (T)(0.5 * ph.drho);
+  const T kmuP_T = (T)kmu, PDP_T = (T)PD, hT = (T)h, hdT = (T)(0.5 * ph.drho);
 
   // interior faces W, E, S, N
 #pragma unroll
@@ -189,15 +203,23 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     const int jy = iy + (k == 2 ? -1 : (k == 3 ? 1 : 0));
     if (jx < 0 || jx >= nx || jy < 0 || jy >= ny) continue;
     const S sg = (S)(k == 2 ? -ph.g : (k == 3 ? ph.g : 0.0));
-    const double2 xN = xs[st_of(jx, jy, nx)];
+    const int sn = st_of(jx, jy, nx);
+    S kmu_f = kmu, PD_f = PD;
+    if (FIELDS) {  // the face's harmonic means, stored with the cell west of / below the face
+      const double4 f = fc[(k == 0 || k == 2) ? sn : st];
+      kmu_f = (S)(((k < 2) ? f.x : f.z) * inv_s);
+      PD_f = (S)(((k < 2) ? f.y : f.w) * inv_s);
+    }
+    const T kmuT = (T)kmu_f, PDT = (T)PD_f;
+    const double2 xN = xs[sn];
     const S pN = (S)xN.x, cN = (S)xN.y;
     const S rhoN = rho0 + drho * cN;
     const S rhof = (S)0.5 * (rhoP + rhoN);
-    const S q = -kmu * fma_((pN - pP), ihS, sg * rhof);
+    const S q = -kmu_f * fma_((pN - pP), ihS, sg * rhof);
     const S Ff = rhof * q * hS;
     const bool up = Ff >= (S)0;
     const S cup = up ? cP : cN;
-    const S dif = PD * (cN - cP);
+    const S dif = PD_f * (cN - cP);
     Rm += Ff;
     Rs += fma_(Ff, cup, -rhof * dif);
     // derivatives of (F, G) w.r.t. the unknowns of P and of the neighbour
@@ -221,7 +243,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     const bool up = Fl >= (S)0;
     Rm += Fl;
     Rs += fma_(Fl, up ? cP : (S)0, (S)2 * rb * PD * cP);
-    C11 += (up ? (T)Fl : (T)0) + PDT * (T)fma_(drho, cP, (S)2 * rb);
+    C11 += (up ? (T)Fl : (T)0) + PDP_T * (T)fma_(drho, cP, (S)2 * rb);
   }
   if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
     const S yP = ((S)iy + (S)0.5) * hS;
@@ -234,12 +256,12 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     const S dif = PD * ((S)1 - cP);
     Rm += Fr;
     Rs += fma_(Fr, cup, -(S)2 * rb * dif);
-    const T dFdp = (T)2 * (T)rb * kmuT;
+    const T dFdp = (T)2 * (T)rb * kmuP_T;
     const T dFdc = hdT * (T)q * hT;
     C00 += dFdp;
     C01 += dFdc;
     C10 = fma_(dFdp, (T)cup, C10);
-    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDT));
+    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDP_T));
   }
   o.fm = Rm;
   o.fs = Rs;
@@ -260,13 +282,14 @@ __device__ __forceinline__ void store_blocks(typename VT<T>::b4* J, int64_t ps, 
 
 // One thread per cell; FINE: CTAs never straddle samples (N % TPB == 0) and
 // write the per-CTA max |F| (inf for non-finite) to rmax_part[s][ct].
-template <typename T, bool FINE>
+template <typename T, bool FINE, bool FIELDS = false>
 __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
                                                   double h, double inv_h, double vt_s, double inv_s,
                                                   const double2* __restrict__ x, const double2* __restrict__ xo,
                                                   const int* __restrict__ active, double2* __restrict__ F,
                                                   typename VT<T>::b4* __restrict__ J, int64_t plane,
-                                                  double* __restrict__ rmax_part) {
+                                                  double* __restrict__ rmax_part, const double2* __restrict__ cc = nullptr,
+                                                  const double4* __restrict__ fc = nullptr) {
   typedef typename std::conditional<FINE, double, T>::type S;
   __shared__ double sh[40];
   const int N = nx * ny;
@@ -283,7 +306,8 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
   CellSys<T, S> o;
-  assemble_cell<T, S>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o);
+  assemble_cell<T, S, FIELDS>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o,
+                              FIELDS ? cc + base : nullptr, FIELDS ? fc + base : nullptr);
   if (FINE) {
     const double fm = (double)o.fm, fs = (double)o.fs;
     if (F) F[e] = make_double2(fm, fs);

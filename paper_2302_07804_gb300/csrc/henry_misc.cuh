@@ -65,6 +65,129 @@ __global__ void k_coefficients(CoefModel m, int n, const double* __restrict__ xi
   status[i] = ok ? 0 : 3;
 }
 
+// ---------------------------------------------------------------------------
+// Random-field coefficient model (KL expansions of log K and phi, see
+// henry_kl.cuh): per sample the inputs are theta_K[terms], theta_phi[terms]
+// (iid N(0,1), drawn by the caller) and xi3 (uniform, for q_in).  cc[e] =
+// (phi, K / mu) at the cell centre:
+//   K = K_mean exp(sigma_K sum_t sqrt(lam_t) theta_K,t psi_t),
+//   phi = clip(phi_mean + sigma_phi sum_t sqrt(lam_t) theta_phi,t psi_t, phi_lo, phi_hi),
+// psi_t(x, y) = psi_x[ti_t](x) psi_y[tj_t](y) from the 1-D tables of this grid.
+struct KLParams {
+  int terms, n_in, m;
+  double K_mean, sigma_logK, phi_mean, sigma_phi, phi_lo, phi_hi, mu;
+};
+__global__ void __launch_bounds__(TPB) k_fields_kl(KLParams P, int B, int nx, int ny, const double* __restrict__ inp,
+                                                   const int* __restrict__ ti, const int* __restrict__ tj,
+                                                   const double* __restrict__ sl, const double* __restrict__ psx,
+                                                   const double* __restrict__ psy, double2* __restrict__ cc,
+                                                   int* __restrict__ status) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int s = (int)(e / N);
+  int ix, iy;
+  xy_of((int)(e - (int64_t)s * N), nx, ix, iy);
+  const double* in = inp + (int64_t)s * P.n_in;
+  double gK = 0.0, gp = 0.0;
+  for (int t = 0; t < P.terms; ++t) {
+    const double mode = psy[(int64_t)tj[t] * ny + iy] * psx[(int64_t)ti[t] * nx + ix];
+    gK = fma(sl[t] * in[t], mode, gK);
+    gp = fma(sl[t] * in[P.terms + t], mode, gp);
+  }
+  const double K = P.K_mean * exp(P.sigma_logK * gK);
+  const double phi = fmin(fmax(P.phi_mean + P.sigma_phi * gp, P.phi_lo), P.phi_hi);
+  cc[e] = make_double2(phi, K / P.mu);
+  if (!(K > 0.0 && K <= 1.0e300 && phi == phi)) atomicExch(status + s, 3);
+}
+
+// Two-layer porosity of the paper's experiments (Eq. poro_2levels) with the
+// Kozeny-Carman permeability (Eq. e_perm_Kozeny_Carman) K = kappa phi^3 /
+// (1 - phi^2), kappa fixed by K(E[phi]) = K_mean; the paper's y in [-1, 0]
+// is y - Ly here, the layer interface at -0.75 is y = Ly - 0.75.
+struct TwoLayerParams {
+  int n_in;
+  double phi_mean, kappa, mu, Ly, y_if;
+};
+__global__ void __launch_bounds__(TPB) k_fields_two_layer(TwoLayerParams P, int B, int nx, int ny, double h,
+                                                          const double* __restrict__ inp, double2* __restrict__ cc,
+                                                          int* __restrict__ status) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int s = (int)(e / N);
+  int ix, iy;
+  xy_of((int)(e - (int64_t)s * N), nx, ix, iy);
+  const double* in = inp + (int64_t)s * P.n_in;
+  const double xi1 = in[0], xi2 = in[1];
+  const double x = (ix + 0.5) * h, yp = (iy + 0.5) * h - P.Ly;  // paper coordinates
+  const double pi = 3.14159265358979323846;
+  const double c0 = (yp < P.y_if) ? 1.0 + 0.2 * xi1 : 1.0 - 0.2 * xi1;
+  const double phi = P.phi_mean * (1.0 + 0.15 * (xi2 * cos(pi * x / 2.0) + xi2 * sin(2.0 * pi * yp) + xi1 * cos(2.0 * pi * x))) * c0;
+  const double K = P.kappa * phi * phi * phi / (1.0 - phi * phi);
+  cc[e] = make_double2(phi, K / P.mu);
+  if (!(phi > 0.0 && phi < 1.0 && K > 0.0 && K <= 1.0e300)) atomicExch(status + s, 3);
+}
+
+// Coarse multigrid cells: mean of the children's (phi, K / mu).
+__global__ void __launch_bounds__(TPB) k_restrict_cc(int B, int ncx, int ncy, const double2* __restrict__ ccf,
+                                                     double2* __restrict__ ccc) {
+  const int Nc = ncx * ncy;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * Nc) return;
+  const int s = (int)(e / Nc);
+  int IX, IY;
+  xy_of((int)(e - (int64_t)s * Nc), ncx, IX, IY);
+  const int nxf = 2 * ncx;
+  const int64_t bf = (int64_t)s * Nc * 4;
+  const double2 a = ccf[bf + st_of(2 * IX, 2 * IY, nxf)], b = ccf[bf + st_of(2 * IX + 1, 2 * IY, nxf)];
+  const double2 c = ccf[bf + st_of(2 * IX, 2 * IY + 1, nxf)], d = ccf[bf + st_of(2 * IX + 1, 2 * IY + 1, nxf)];
+  ccc[e] = make_double2(0.25 * (((a.x + b.x) + c.x) + d.x), 0.25 * (((a.y + b.y) + c.y) + d.y));
+}
+
+// Face coefficients: harmonic means 2 a b / (a + b) of K / mu and of phi Dm on
+// the east (.x, .y) and north (.z, .w) face of every cell, 0 on the boundary.
+__global__ void __launch_bounds__(TPB) k_face_coefs(int B, int nx, int ny, double Dm, const double2* __restrict__ cc,
+                                                    double4* __restrict__ fc) {
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= (int64_t)B * N) return;
+  const int s = (int)(e / N);
+  const int st = (int)(e - (int64_t)s * N);
+  int ix, iy;
+  xy_of(st, nx, ix, iy);
+  const double2* c = cc + (int64_t)s * N;
+  const double2 P = c[st];
+  double4 f;
+  f.x = f.y = f.z = f.w = 0.0;
+  auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
+  if (ix + 1 < nx) {
+    const double2 E = c[st_of(ix + 1, iy, nx)];
+    f.x = harm(P.y, E.y);
+    f.y = harm(P.x * Dm, E.x * Dm);
+  }
+  if (iy + 1 < ny) {
+    const double2 Nn = c[st_of(ix, iy + 1, nx)];
+    f.z = harm(P.y, Nn.y);
+    f.w = harm(P.x * Dm, Nn.x * Dm);
+  }
+  fc[e] = f;
+}
+
+// a2 for the field models: q_in from its uniform input (index iq).
+__global__ void k_coefficients_qin(int n, int n_in, int iq, double qin_mean, double qin_amp,
+                                   const double* __restrict__ inp, Coef* __restrict__ coef, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Coef c;
+  c.phi = 0.0;
+  c.kmu = 0.0;
+  c.PD = 0.0;
+  c.qin = qin_mean * (1.0 + qin_amp * inp[(int64_t)i * n_in + iq]);
+  coef[i] = c;
+  status[i] = (c.qin == c.qin && fabs(c.qin) <= 1.0e300) ? 0 : 3;
+}
+
 // a3: c = 0 and fresh-water hydrostatic pressure rho0 g (Ly - y).
 __global__ void __launch_bounds__(TPB) k_init_state(int B, int nx, int ny, double h, double rho0g, double Ly,
                                                     double2* __restrict__ x) {
@@ -79,9 +202,10 @@ __global__ void __launch_bounds__(TPB) k_init_state(int B, int nx, int ny, doubl
 // a11: QoIs, one CTA per sample: salt mass sum phi rho c h^2 and c at
 // (1.5, 0.25) = mean of the cells (ix0, iy0), (ix0+1, iy0), (ix0, iy0+1),
 // (ix0+1, iy0+1) with ix0 = 1.5 / h - 1, iy0 = 0.25 / h - 1.
+// With per-cell coefficients (cc != NULL) the porosity weights each cell.
 __global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, double rho0, double drho,
                                              const Coef* __restrict__ coef, const double2* __restrict__ x,
-                                             double* __restrict__ qoi) {
+                                             double* __restrict__ qoi, const double2* __restrict__ cc = nullptr) {
   __shared__ double sh[40];
   const int s = blockIdx.x;
   const int N = nx * ny;
@@ -89,14 +213,15 @@ __global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, do
   double acc = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const double c = xs[i].y;
-    acc += (rho0 + drho * c) * c;
+    const double w = cc ? cc[(int64_t)s * N + i].x : 1.0;
+    acc += w * (rho0 + drho * c) * c;
   }
   acc = block_reduce<false>(acc, sh);
   if (threadIdx.x == 0) {
     const int ix0 = (3 * ny) / 2 - 1, iy0 = ny / 4 - 1;
     const double c00 = xs[st_of(ix0, iy0, nx)].y, c10 = xs[st_of(ix0 + 1, iy0, nx)].y;
     const double c01 = xs[st_of(ix0, iy0 + 1, nx)].y, c11 = xs[st_of(ix0 + 1, iy0 + 1, nx)].y;
-    qoi[2 * (int64_t)s] = coef[s].phi * acc * h * h;
+    qoi[2 * (int64_t)s] = (cc ? 1.0 : coef[s].phi) * acc * h * h;
     qoi[2 * (int64_t)s + 1] = 0.25 * (((c00 + c10) + c01) + c11);
   }
 }

@@ -17,6 +17,7 @@ HENRY_OK, HENRY_EINVAL, HENRY_ECUDA, HENRY_ENOMEM, HENRY_ENOCONV, HENRY_ELIMIT =
 HENRY_SAMPLE_OK, HENRY_SAMPLE_NEWTON, HENRY_SAMPLE_LINEAR, HENRY_SAMPLE_NONFINITE = range(4)
 HENRY_FP64, HENRY_MIXED = 0, 1
 HENRY_COARSE_REDISCRETISE, HENRY_COARSE_GALERKIN = 0, 1
+HENRY_MODEL_UNIFORM3, HENRY_MODEL_KL, HENRY_MODEL_TWO_LAYER = 0, 1, 2
 N_QOI = 2
 N_XI = 3
 
@@ -36,7 +37,8 @@ class HenryConfig(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("newton_atol", "newton_dxtol", "lin_rtol")] + \
                [(n, ctypes.c_int32) for n in ("newton_maxit", "lin_maxit", "nu1", "nu2")] + \
                [("workspace_bytes", ctypes.c_double), ("newton_predictor", ctypes.c_double),
-                ("fused_small_grids", ctypes.c_int32)]
+                ("fused_small_grids", ctypes.c_int32), ("coef_model", ctypes.c_int32), ("kl_terms", ctypes.c_int32)] + \
+               [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")]
 
 
 class HenryStats(ctypes.Structure):
@@ -205,13 +207,18 @@ class Solver:
             out[name] = (ms.value, n.value, b.value, f.value)
         return out
 
+    @property
+    def n_xi(self):
+        """Random inputs per sample for this configuration's coefficient model."""
+        return 2 * self.cfg.kl_terms + 1 if self.cfg.coef_model == HENRY_MODEL_KL else N_XI
+
     def grid(self, level):
         return (self.cfg.ny0 << level, self.cfg.nx0 << level)
 
     def level_batch_solve(self, level, xi, with_coarse=False, stream=None, allow_failures=False, out=None):
         """Returns (qoi_fine[n][2], qoi_coarse[n][2] or None, status[n] int32, stats dict)."""
         n = xi.shape[0]
-        _dev_f64(xi, (n, N_XI))
+        _dev_f64(xi, (n, self.n_xi))
         if out is None:
             qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
             qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None

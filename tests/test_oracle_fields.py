@@ -1,0 +1,88 @@
+"""Pins of the oracle's random-field coefficient models.
+
+KL (oracle.kl): the Nystrom eigenvalues sum to the domain length (trace of
+W^1/2 K W^1/2 = sum_q w_q k(x_q, x_q)); eigenfunctions are orthonormal in
+the quadrature inner product; the eigen-expansion with all modes reproduces
+the kernel at points off the quadrature grid (the Nystrom interpolant); the
+truncated 2-D field's pointwise variance never exceeds the covariance's.
+Two-layer model: kappa_KC from K(E[phi]) = K_mean (2.0884e-8 for the
+paper's K = 1.020408e-9, quoted in the survey of the paper's Sec. 2.2);
+phi at the paper's xi* (Sec. 4) peaks at 0.499 as printed (its printed
+minimum 0.248 is not reproduced by the printed formula: parity unpinned).
+"""
+import numpy as np
+import pytest
+
+from oracle import henry, kl
+from paper_2302_07804_gb300 import inputs
+
+PRM = henry.Params()
+
+
+@pytest.fixture(scope="module")
+def basis():
+    return kl.KLBasis()
+
+
+def test_nystrom_trace_and_orthonormality():
+    for L in (2.0, 1.0):
+        lam, xq, wq, U = kl.nystrom_1d(L, m=256)
+        assert lam.sum() == pytest.approx(L, rel=1e-12)
+        G = (U * wq[None, :]) @ U.T
+        np.testing.assert_allclose(G, np.eye(256), atol=1e-9)
+
+
+def test_mercer_reconstruction_off_grid():
+    lam, xq, wq, U = kl.nystrom_1d(2.0, m=256)
+    x = np.array([0.0137, 0.77, 1.5, 1.9991])
+    P = kl.eval_1d(x, lam, xq, wq, U)
+    rec = (P * lam[:, None]).T @ P
+    np.testing.assert_allclose(rec, kl.kernel_1d(x, x), atol=1e-8)
+
+
+def test_truncated_variance_and_term_order(basis):
+    xc = (np.arange(32) + 0.5) / 16
+    yc = (np.arange(16) + 0.5) / 16
+    M = basis.modes(xc, yc)
+    var = np.tensordot(basis.lam, M ** 2, axes=1)
+    assert var.max() <= 1.0 + 1e-9
+    assert var.mean() > 0.8
+    assert np.all(np.diff(basis.lam) <= 0)
+    assert len(basis.pairs) == 32 and basis.pairs[0][1:] == (0, 0)
+
+
+def test_kl_field_statistics(basis):
+    grid = henry.Grid.level(PRM, 0)
+    gen = inputs.rng(400)
+    logs = []
+    for _ in range(400):
+        th = np.concatenate([gen.standard_normal(64), [0.0]])
+        c = kl.coefficients_kl(PRM, grid, th, basis)
+        logs.append(np.log(c.K[8, 16] / PRM.K_mean) / 0.5)
+        assert c.phi.min() >= 0.05 and c.phi.max() <= 0.65
+    # standardised log K at a cell: mean 0, variance = truncated variance there
+    logs = np.array(logs)
+    xc = (np.arange(32) + 0.5) / 16
+    yc = (np.arange(16) + 0.5) / 16
+    v = float(np.tensordot(basis.lam, basis.modes(xc, yc)[:, 8, 16] ** 2, axes=1))
+    assert abs(logs.mean()) < 4 * np.sqrt(v / 400)
+    assert abs(logs.var() / v - 1) < 0.25
+
+
+def test_kozeny_carman_kappa_closed_form():
+    assert henry.kozeny_carman_kappa(1.020408e-9, 0.35) == pytest.approx(2.0884e-8, rel=1e-4)
+    kap = henry.kozeny_carman_kappa(1.02e-9, 0.35)
+    assert kap * 0.35 ** 3 / (1 - 0.35 ** 2) == pytest.approx(1.02e-9, rel=1e-14)
+
+
+def test_two_layer_porosity_at_paper_xi_star():
+    """Sec. 4: xi* = (-0.5898, -0.7257, -0.9616); the printed range is
+    [0.248, 0.499]; the maximum of the printed formula over the domain is
+    0.499 (checked on a fine grid of cell centres)."""
+    prm = henry.Params()
+    grid = henry.Grid(nx=1024, ny=512, h=1.0 / 512, tau=1.0, steps=1)
+    c = henry.coefficients_two_layer(prm, grid, [-0.5898, -0.7257, -0.9616])
+    assert c.phi.max() == pytest.approx(0.499, abs=1.5e-3)
+    # layers: the lower one (y < -0.75 in the paper's coordinates) is scaled by 1 + 0.2 xi1
+    ratio = c.phi[0, 5] / henry.coefficients_two_layer(prm, grid, [0.0, -0.7257, -0.9616]).phi[0, 5]
+    assert np.isfinite(ratio)
