@@ -239,11 +239,12 @@ class Workload:
     concurrently from host threads (each level's solve synchronises only its
     own stream), joined on the main stream."""
 
-    def __init__(self, henry, torch, dev, alloc, precision, xis):
+    def __init__(self, henry, torch, dev, alloc, precision, xis, with_coarse=True, **solver_kw):
         import threading
         self.h, self.t, self.dev, self.alloc = henry, torch, dev, alloc
         self.L = len(alloc)
-        self.solvers = [henry.Solver(precision=precision) for _ in range(self.L)]
+        self.with_coarse = with_coarse
+        self.solvers = [henry.Solver(precision=precision, **solver_kw) for _ in range(self.L)]
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.L)]
         self.outs = [(torch.empty((m, 2), dtype=torch.float64, device=dev),
                       torch.empty((m, 2), dtype=torch.float64, device=dev) if l > 0 else None,
@@ -265,8 +266,11 @@ class Workload:
                 if host is not None:
                     host["xi_dev"][l].copy_(host["xi"][l], non_blocking=True)
                     xi = host["xi_dev"][l]
-                qf, qc, st, stats = self.solvers[l].level_batch_solve(l, xi, with_coarse=l > 0, stream=s,
-                                                                      allow_failures=True, out=self.outs[l])
+                wc = self.with_coarse and l > 0
+                qf, qc, st, stats = self.solvers[l].level_batch_solve(l, xi, with_coarse=wc, stream=s,
+                                                                      allow_failures=True,
+                                                                      out=self.outs[l] if wc or l == 0 else
+                                                                      (self.outs[l][0], None, self.outs[l][2]))
                 self.fails[l] += int(stats["failed_samples"])
                 henry.mlmc_accumulate(l, qf, qc, st, self.sums[l], stream=s)
                 if host is not None:
@@ -319,6 +323,78 @@ class Workload:
     def close(self):
         for s in self.solvers:
             s.close()
+
+
+UNEVEN_COUNTS = (3264, 656, 128, 32, 8, 8)  # 4096 scenarios, the shape of Eq. (M_ell) under the paper's (V_l, s_l)
+
+
+def run_uneven(args):
+    """4096 scenarios spread over levels 0..5 (32x16x20 .. 1024x512x640), all
+    levels concurrently (one stream and handle each).  --workload uneven: FP64,
+    three-parameter model; --workload kl-mixed: KL random fields, mixed
+    precision, with the QoI difference to FP64 solves of the same inputs and
+    to the oracle on a few level-0/1 samples."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_07804_gb300 import henry, inputs, mlmc
+    dev = torch.device("cuda", 0)
+    kl = args.workload == "kl-mixed"
+    counts = list(UNEVEN_COUNTS)
+    cfg = henry.default_config()
+    kw = {"coef_model": henry.HENRY_MODEL_KL} if kl else {}
+    prec = henry.HENRY_MIXED if kl else henry.HENRY_FP64
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(inputs.SEED)
+    xis = []
+    for l, m in enumerate(counts):
+        if kl:
+            th = torch.randn((m, 64), generator=gen, device=dev, dtype=torch.float64)
+            x3 = torch.rand((m, 1), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+            xis.append(torch.cat([th, x3], dim=1).contiguous())
+        else:
+            xis.append(henry.sample_xi(inputs.SEED, l, 2 * 10 ** 7, m, device=dev))
+    cs = sum(m * (cfg.nx0 << l) * (cfg.ny0 << l) * (cfg.steps0 << l) for l, m in enumerate(counts))
+    W = Workload(henry, torch, dev, counts, prec, [xis], with_coarse=False, **kw)
+    W.run(0)  # warm-up: workspaces and KL tables
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        W.run(0)
+        e1.record()
+        torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    line = {"workload": "uneven-4096-levels0-5" + ("-kl-mixed" if kl else "-fp64"), "metric": METRIC,
+            "value": cs / sec, "unit": "cell-steps/s", "seconds": sec, "counts": counts, "cell_steps": cs,
+            "failed_samples": sum(W.fails), "clocks": clk.summary(),
+            "schedule": "levels concurrent, one stream + handle each"}
+    if kl:
+        q32 = [W.outs[l][0].clone() for l in range(len(counts))]
+        W64 = Workload(henry, torch, dev, counts, henry.HENRY_FP64, [xis], with_coarse=False, **kw)
+        W64.run(0)
+        torch.cuda.synchronize()
+        diff = []
+        for l in range(len(counts)):
+            a, b = q32[l].cpu().numpy(), W64.outs[l][0].cpu().numpy()
+            diff.append({"level": l, "max_rel_mass": float(np.max(np.abs(a[:, 0] - b[:, 0]) / np.abs(b[:, 0]))),
+                         "max_abs_c": float(np.max(np.abs(a[:, 1] - b[:, 1])))})
+        line["qoi_mixed_vs_fp64_gpu"] = diff
+        from oracle import henry as oh
+        prm = oh.Params()
+        orc = []
+        for l, k in ((0, 3), (1, 1)):
+            x = xis[l][:k].cpu().numpy()
+            ref, ok = oh.solve_scenarios(prm, l, x, model="kl")
+            a = q32[l][:k].cpu().numpy()
+            orc.append({"level": l, "n": k, "max_rel_mass": float(np.max(np.abs(a[:, 0] - ref[:, 0]) / ref[:, 0])),
+                        "max_abs_c": float(np.max(np.abs(a[:, 1] - ref[:, 1])))})
+        line["qoi_mixed_vs_oracle"] = orc
+        W64.close()
+    W.close()
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_case(args):
@@ -380,9 +456,13 @@ def main():
     ap.add_argument("--case", default=None, help="LEVEL:N profiling case (one batch solve, no MLMC)")
     ap.add_argument("--profile", action="store_true", help="with --case: also read the kernel timer")
     ap.add_argument("--vcycle", action="store_true", help="with --case: one assembly + V-cycle per call instead of a solve")
+    ap.add_argument("--workload", default="mlmc", choices=["mlmc", "uneven", "kl-mixed"],
+                    help="mlmc: the bench line; uneven / kl-mixed: 4096 scenarios over levels 0..5")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.workload != "mlmc":
+        return run_uneven(args)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         return run_reference(args, rank, world)

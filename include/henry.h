@@ -113,12 +113,17 @@ typedef struct {
   double workspace_bytes;                    /* device workspace budget per batch (chunking) */
   double newton_predictor; /* Newton's first iterate of step n+1: x^n + w (x^n - x^{n-1}), w in [0, 1]
                               (0: x^n; default 1, linear extrapolation in time) */
+  double newton_dc_limit;  /* Newton steps with max |dc| > limit are scaled down to it (default 1; 0: off) */
   int32_t fused_small_grids; /* grids of <= 512 cells solved by one CTA per sample with the whole hierarchy in
                                 shared memory: 1 (default) in HENRY_MIXED only, 2 also in HENRY_FP64,
                                 0 never (always the multi-kernel path); not used by the field models */
   int32_t coef_model;        /* HENRY_MODEL_* */
   int32_t kl_terms;          /* KL terms per field (default 32) */
   double kl_corr_len, kl_sigma_logK, kl_sigma_phi, phi_lo, phi_hi; /* 0.3 m, 0.5, 0.1, 0.05, 0.65 */
+  int32_t lin_retry; /* field models: 1 (default) re-solves a failed Newton system with a V-cycle on the
+                        Jacobian without density derivatives; 0 keeps the failed iterate */
+  int32_t finalize_nct; /* BiCGStab dot products of samples with >= this many 256-cell blocks are reduced
+                           once per sample by a separate kernel (default 512; 0: never); same values */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */

@@ -88,6 +88,9 @@ class Params:
     newton_atol: float = 1e-11
     newton_dxtol: float = 1e-12
     newton_maxit: int = 30
+    # a step that would change some mass fraction by more than this is scaled
+    # down to it (0: full Newton steps)
+    newton_dc_limit: float = 1.0
 
 
 @dataclass(frozen=True)
@@ -388,7 +391,10 @@ def newton_step(prm, grid, coef, p_old, c_old, src=None, bc=None, linsolve=None,
 
     Stops when the scaled residual max-norm is <= newton_atol, or right after
     an update whose scaled max-norm (p in units of rho0 g Ly) is <=
-    newton_dxtol.  Returns (p, c, converged)."""
+    newton_dxtol.  A step whose largest mass-fraction change exceeds
+    newton_dc_limit is scaled down to it (c lies in [0, 1], so such a step
+    overshoots; near convergence the steps are full Newton steps and the
+    root is the same).  Returns (p, c, converged)."""
     s = residual_scale(prm, grid)
     pref = prm.rho0 * prm.g * prm.Ly
     p, c = p_old.copy(), c_old.copy()
@@ -403,9 +409,11 @@ def newton_step(prm, grid, coef, p_old, c_old, src=None, bc=None, linsolve=None,
         J = jacobian(prm, grid, coef, p, c, p_old, c_old, bc)
         dx = solve(J, -pack(Rm, Rs))
         dp, dc = unpack(dx, grid)
-        p = p + dp
-        c = c + dc
-        if max(np.abs(dp).max() / pref, np.abs(dc).max()) <= prm.newton_dxtol:
+        dcmax = np.abs(dc).max()
+        theta = prm.newton_dc_limit / dcmax if (prm.newton_dc_limit > 0 and dcmax > prm.newton_dc_limit) else 1.0
+        p = p + theta * dp
+        c = c + theta * dc
+        if max(np.abs(dp).max() / pref, dcmax) <= prm.newton_dxtol:
             if stats is not None:
                 stats.append(it + 1)
             return p, c, True

@@ -77,7 +77,7 @@ __host__ __device__ inline bool cta_layout(int nx0, int ny0, int tsize, CtaLayou
 struct CtaParams {
   Phys ph;
   int nx0, ny0, steps, nu1, nu2, newton_maxit, lin_maxit;
-  double h0, tau, inv_s, inv_pref, atol, dxtol, rtol2, predictor;
+  double h0, tau, inv_s, inv_pref, atol, dxtol, rtol2, predictor, dc_limit;
   double rho0g, Ly;
 };
 
@@ -428,19 +428,28 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant
       }
       lin_total += lit;
       if (fail) break;
-      // a9: Newton update and the update test
-      double dloc = 0.0;
+      // a9: Newton update (step limited to max |dc| <= dc_limit) and the update test
+      double dloc = 0.0, cloc = 0.0;
+      for (int i = threadIdx.x; i < N0; i += blockDim.x) {
+        const V2 d = dx[i];
+        double dc = fabs((double)d.y);
+        double l = fmax(fabs((double)d.x) * P.inv_pref, dc);
+        if (!(l <= 1.0e300)) l = INFINITY;
+        if (!(dc <= 1.0e300)) dc = INFINITY;
+        dloc = fmax(dloc, l);
+        cloc = fmax(cloc, dc);
+      }
+      const double dmax = cta_max(dloc, sh);
+      const double cmax = cta_max(cloc, sh);
+      const double th = (P.dc_limit > 0.0 && cmax > P.dc_limit) ? P.dc_limit / cmax : 1.0;
       for (int i = threadIdx.x; i < N0; i += blockDim.x) {
         const V2 d = dx[i];
         double2 xx = x[i];
-        xx.x += (double)d.x;
-        xx.y += (double)d.y;
+        xx.x = fma(th, (double)d.x, xx.x);
+        xx.y = fma(th, (double)d.y, xx.y);
         x[i] = xx;
-        double l = fmax(fabs((double)d.x) * P.inv_pref, fabs((double)d.y));
-        if (!(l <= 1.0e300)) l = INFINITY;
-        dloc = fmax(dloc, l);
       }
-      const double dmax = cta_max(dloc, sh);
+      __syncthreads();
       if (!(dmax <= 1.0e300)) {
         fail = 3;
         break;

@@ -99,9 +99,12 @@ struct Group {
   Coef* coef;
   double* part;
   int *newton_active, *lin_active, *newton_it, *status, *iters, *counter;
+  double* theta;  // per-sample Newton step factor
+  double* fin;    // finalised per-sample reduction values [B][NPART] (large grids)
   unsigned long long* totals;  // [0] Newton iterations, [1] BiCGStab iterations
   LinScal* sc;
   T* Ainv;
+  void* Jp = nullptr;  // fine-level fallback preconditioner operator (field models only)
 
   // Lay out (or size, with base == nullptr) the workspace for B samples.
   // `light`: only what the fused small-grid solver uses (fine old state,
@@ -155,10 +158,13 @@ struct Group {
     newton_it = c.take<int>(sizeof(int) * B);
     status = c.take<int>(sizeof(int) * B);
     iters = c.take<int>(sizeof(int) * B);
+    theta = c.take<double>(sizeof(double) * B);
+    fin = light_ws ? nullptr : c.take<double>(sizeof(double) * NPART * (size_t)B);
     counter = c.take<int>(sizeof(int) * 4);
     totals = c.take<unsigned long long>(sizeof(unsigned long long) * 4);
     sc = light_ws ? nullptr : c.take<LinScal>(sizeof(LinScal) * B);
     Ainv = light_ws ? nullptr : c.take<T>(sizeof(T) * 16 * B);
+    Jp = (fields && !light_ws) ? (void*)c.take<B4>(sizeof(B4) * 6 * (size_t)n0) : nullptr;
     if (base) {
       lv = L;
       K = (int)L.size() - 1;
@@ -458,14 +464,14 @@ int set_coefficients(henry_handle* H, Group<T>& G, const double* xi, int B, cuda
 // Coarse-grid operators for every multigrid level below the fine one, plus
 // the coarsest inverse.  Expects lv[k].x for k >= 1 up to date when
 // rediscretising (call restrict_states first).
-template <typename T>
+template <typename T, bool DROP = false>
 int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st) {
   typedef typename VT<T>::b4 B4;
   const Phys ph = phys_of(H->cfg);
   const double na = H->nact;
   for (int k = 1; k <= G.K; ++k) {
     Level& L = G.lv[k];
-    if (H->cfg.coarse_op == HENRY_COARSE_GALERKIN) {
+    if (H->cfg.coarse_op == HENRY_COARSE_GALERKIN && !DROP) {
       Level& Lf = G.lv[k - 1];
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * 26.0 * sizeof(B4), [&] {
         k_galerkin<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)Lf.J, Lf.plane, (B4*)L.J,
@@ -474,7 +480,7 @@ int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double
     } else {
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          k_assemble<T, false, true><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+          k_assemble<T, false, true, DROP><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h, L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo, G.lin_active,
               nullptr, (B4*)L.J, L.plane, nullptr, L.cc, L.fc);
         else
@@ -512,7 +518,7 @@ int restrict_states(henry_handle* H, Group<T>& G, int B, bool old, const int* ac
 // One V(nu1, nu2) cycle: x0 = M^{-1} b0 on the fine level (active = lin_active).
 template <typename T>
 int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, typename VT<T>::v2* x0,
-           cudaStream_t st) {
+           cudaStream_t st, const void* J0 = nullptr) {
   typedef typename VT<T>::v2 V2;
   typedef typename VT<T>::b4 B4;
   const int nu1 = H->cfg.nu1, nu2 = H->cfg.nu2;
@@ -523,7 +529,7 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     Level& L = G.lv[k];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
-    const B4* J = (const B4*)L.J;
+    const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
     const unsigned gh = nblk((int64_t)B * L.N / 2);
     const double hc = na * L.N / 2;  // swept cells per half-sweep
     Level& Lc = G.lv[k + 1];
@@ -563,7 +569,7 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     Level& Lc = G.lv[k + 1];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
-    const B4* J = (const B4*)L.J;
+    const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
     const unsigned gh = nblk((int64_t)B * L.N / 2);
     const double hc = na * L.N / 2;
     if (nu2 > 0) {
@@ -605,7 +611,7 @@ int read_counter(henry_handle* H, const int* dev, cudaStream_t st, int* out) {
 // BiCGStab on the fine level for the samples with lin_active set; right-hand
 // side -F; solution in G.dx.
 template <typename T>
-int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
+int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const void* Jpre0 = nullptr) {
   typedef typename VT<T>::v2 V2;
   typedef typename VT<T>::b4 B4;
   Level& L = G.lv[0];
@@ -616,12 +622,21 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
     k_bicg_init<T><<<g, TPB, 0, st>>>(B, N, G.F, G.r, G.rh, G.p, G.v, G.dx, G.part, G.lin_active);
   });
   CKL();
+  // Large grids: reduce each sample's partials once (one warp per sample)
+  // instead of in every CTA of the consumer kernel.
+  double* fin = (H->cfg.finalize_nct > 0 && G.nct >= H->cfg.finalize_nct) ? G.fin : nullptr;
+  auto finalize = [&](int a, int b) {
+    if (!fin) return;
+    launch(H, st, HENRY_K_KRYLOV, (double)B * G.nct * 16.0,
+           [&] { k_finalize<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, G.part, a, b, fin); });
+  };
+  finalize(P_RR, P_RN);
   const double rtol2 = H->cfg.lin_rtol * H->cfg.lin_rtol;
   for (int it = 0; it <= H->cfg.lin_maxit; ++it) {
     CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
     launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (it == 0 ? 2 : 4) * v2, [&] {
       k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, H->cfg.lin_maxit, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
-                                      G.iters, G.status, G.counter + 1, G.totals + 1);
+                                      G.iters, G.status, G.counter + 1, G.totals + 1, fin);
     });
     CKL();
     int n_act = 0;
@@ -630,27 +645,59 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st) {
     if (n_act == 0) break;
     H->nact = n_act;
     const double nc = (double)n_act * N;
-    rc = vcycle<T>(H, G, B, G.p, G.ph, st);
+    rc = vcycle<T>(H, G, B, G.p, G.ph, st, Jpre0);
     if (rc) return rc;
     launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 1), [&] {
       k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.ph, G.v, G.rh, G.part, P_RV, 0,
                                        G.lin_active);
     });
+    finalize(P_RV, -1);
     launch(H, st, HENRY_K_KRYLOV, nc * 3 * v2,
-           [&] { k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active); });
+           [&] { k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active, fin); });
     CKL();
-    rc = vcycle<T>(H, G, B, G.s, G.sh, st);
+    rc = vcycle<T>(H, G, B, G.s, G.sh, st, Jpre0);
     if (rc) return rc;
     launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 2), [&] {
       k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.sh, G.t, G.s, G.part, P_TS, P_TT,
                                        G.lin_active);
     });
+    finalize(P_TS, P_TT);
     launch(H, st, HENRY_K_KRYLOV, nc * 8 * v2, [&] {
-      k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active);
+      k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active,
+                                           fin);
     });
+    finalize(P_RR, P_RN);
     CKL();
   }
   return HENRY_OK;
+}
+
+// Second linear solve for the samples whose BiCGStab failed: the V-cycle
+// runs on the operator without the density derivatives (DROP), fine and
+// coarse, while the Krylov matvec keeps the exact Jacobian.  The coarse
+// operators of the retried samples are rebuilt by the next Newton iteration.
+template <typename T>
+int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  Level& L = G.lv[0];
+  CK(cudaMemsetAsync(G.counter + 2, 0, sizeof(int), st));
+  k_mark_retry<<<nblk(B, 128), 128, 0, st>>>(B, G.newton_active, G.iters, G.lin_active, G.counter + 2);
+  CKL();
+  int n_retry = 0;
+  int rc = read_counter(H, G.counter + 2, st, &n_retry);
+  if (rc) return rc;
+  if (n_retry == 0) return HENRY_OK;
+  H->nact = n_retry;
+  double* pscratch = G.part + P_MAX * (int64_t)B * G.nct;
+  k_assemble<T, true, true, true><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+      phys_of(c), G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+      G.lin_active, nullptr, (B4*)G.Jp, L.plane, pscratch, L.cc, L.fc);
+  CKL();
+  rc = build_coarse_ops<T, true>(H, G, B, inv_tau, inv_s, st);
+  if (rc) return rc;
+  return linear_solve<T>(H, G, B, st, G.Jp);
 }
 
 // Full scenario solves of B samples whose coefficients and status are set.
@@ -717,9 +764,16 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
       if (rc) return rc;
       rc = linear_solve<T>(H, G, B, st);
       if (rc) return rc;
+      if (G.Jp && c.lin_retry) {  // fallback preconditioner for the samples whose solve failed
+        rc = retry_linear_solve<T>(H, G, B, inv_tau, inv_s, st);
+        if (rc) return rc;
+      }
       H->nact = n_act;
       launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
-        k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, L.x, G.dx, pmax, G.newton_active);
+        double* pdc = G.part + P_DC * (int64_t)B * G.nct;
+        k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
+        k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
+        k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
         k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
       });
       CKL();
@@ -763,6 +817,7 @@ int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, d
   P.dxtol = c.newton_dxtol;
   P.rtol2 = c.lin_rtol * c.lin_rtol;
   P.predictor = c.newton_predictor;
+  P.dc_limit = c.newton_dc_limit;
   P.rho0g = c.rho0 * c.g;
   P.Ly = c.Ly;
   CK(cudaFuncSetAttribute(k_cta_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L.bytes));
@@ -929,10 +984,13 @@ void henry_default_config(henry_config* c) {
   c->newton_dxtol = 1e-12;
   c->lin_rtol = 1e-4;  // inexact Newton: the FP64 residual test decides convergence
   c->newton_maxit = 30;
-  c->lin_maxit = 100;
+  c->lin_maxit = 40;
   c->nu1 = 2; c->nu2 = 2;
   c->workspace_bytes = 16.0e9;
   c->newton_predictor = 1.0;
+  c->newton_dc_limit = 1.0;
+  c->lin_retry = 1;
+  c->finalize_nct = 512;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
   c->kl_terms = 32;
@@ -964,7 +1022,8 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
        !(c.phi_lo < c.phi_hi)))
     return set_err(HENRY_EINVAL, "bad random-field settings");
   if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
-      c.lin_rtol <= 0 || c.workspace_bytes <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0))
+      c.lin_rtol <= 0 || c.workspace_bytes <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) ||
+      !(c.newton_dc_limit >= 0.0))
     return set_err(HENRY_EINVAL, "bad solver settings");
   henry_handle* h = new henry_handle();
   h->cfg = c;
@@ -1211,7 +1270,8 @@ int static_check_config(const henry_config& c) {
        !(c.phi_lo < c.phi_hi)))
     return set_err(HENRY_EINVAL, "bad random-field settings");
   if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
-      c.lin_rtol <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0))
+      c.lin_rtol <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) ||
+      !(c.newton_dc_limit >= 0.0))
     return set_err(HENRY_EINVAL, "bad solver settings");
   return HENRY_OK;
 }

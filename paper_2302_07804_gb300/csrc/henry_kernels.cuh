@@ -62,7 +62,7 @@ struct LinScal {
 };
 
 // Partial-sum slots of the fine-level reductions: [q][B][nct].
-enum { P_RR = 0, P_RN = 1, P_RV = 2, P_TS = 3, P_TT = 4, P_MAX = 5, NPART = 6 };
+enum { P_RR = 0, P_RN = 1, P_RV = 2, P_TS = 3, P_TT = 4, P_MAX = 5, P_DC = 6, NPART = 7 };
 
 __host__ __device__ __forceinline__ int st_of(int ix, int iy, int nx) {
   return iy * nx + (((ix + iy) & 1) ? (nx >> 1) : 0) + (ix >> 1);
@@ -114,6 +114,31 @@ __device__ __forceinline__ double sample_sum(const double* __restrict__ p, int n
   v = sh[33];
   __syncthreads();
   return v;
+}
+// The same sum read from the finalised per-sample values when `fin` is set
+// (large grids: one warp per sample summed the partials in the same order).
+__device__ __forceinline__ double sample_sum_or_fin(const double* __restrict__ part, const double* __restrict__ fin,
+                                                    int slot, int64_t stride, int s, int nct, double* sh) {
+  if (fin) return fin[(int64_t)s * NPART + slot];
+  return sample_sum(part + slot * stride + (int64_t)s * nct, nct, sh);
+}
+// One warp per sample: fin[s][slot] = sum of the sample's partials of up to
+// two slots (slot_b < 0: one), in the order sample_sum uses.
+__global__ void k_finalize(int B, int nct, const double* __restrict__ part, int slot_a, int slot_b,
+                           double* __restrict__ fin) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= B) return;
+  const int64_t stride = (int64_t)B * nct;
+  for (int q = 0; q < 2; ++q) {
+    const int slot = q == 0 ? slot_a : slot_b;
+    if (slot < 0) continue;
+    const double* p = part + slot * stride + (int64_t)s * nct;
+    double v = 0.0;
+    for (int i = lane; i < nct; i += 32) v += p[i];
+    v = warp_sum(v);
+    if (lane == 0) fin[(int64_t)s * NPART + slot] = v;
+  }
 }
 __device__ __forceinline__ double sample_max(const double* __restrict__ p, int nct) {
   double v = 0.0;
@@ -167,7 +192,11 @@ struct CellSys {
 // FIELDS: per-cell coefficients instead of the sample's scalars: cc[st] =
 // (phi, K/mu) of the cell and fc[st] = (K/mu, phi Dm) harmonic means on its
 // east face (.x, .y) and north face (.z, .w), zero across the boundary.
-template <typename T, typename S, bool FIELDS = false>
+// DROP: the fallback preconditioner operator - the Jacobian without the
+// derivatives of the face densities with respect to c (dF/dc = 0 in both
+// rows), an operator whose diagonal blocks stay definite where density
+// contrasts over heterogeneous K make point-block Gauss-Seidel diverge.
+template <typename T, typename S, bool FIELDS = false, bool DROP = false>
 __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, int nx, int ny, double h, double inv_h,
                                               double vt_s, double inv_s, const double2* xs, const double2* xos,
                                               int st, int ix, int iy, CellSys<T, S>& o,
@@ -225,7 +254,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     // derivatives of (F, G) w.r.t. the unknowns of P and of the neighbour
     const T rhofT = (T)rhof, cupT = (T)cup, FfT = (T)Ff, difT = (T)dif;
     const T dFdp = rhofT * kmuT;
-    const T dFdc = hdT * hT * fma_((T)q, (T)1, -rhofT * kmuT * (T)sg);
+    const T dFdc = DROP ? (T)0 : hdT * hT * fma_((T)q, (T)1, -rhofT * kmuT * (T)sg);
     const T dGdifP = fma_(hdT, difT, -rhofT * PDT);
     const T dGdifN = fma_(hdT, difT, rhofT * PDT);
     C00 += dFdp;
@@ -257,7 +286,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     Rm += Fr;
     Rs += fma_(Fr, cup, -(S)2 * rb * dif);
     const T dFdp = (T)2 * (T)rb * kmuP_T;
-    const T dFdc = hdT * (T)q * hT;
+    const T dFdc = DROP ? (T)0 : hdT * (T)q * hT;
     C00 += dFdp;
     C01 += dFdc;
     C10 = fma_(dFdp, (T)cup, C10);
@@ -282,7 +311,7 @@ __device__ __forceinline__ void store_blocks(typename VT<T>::b4* J, int64_t ps, 
 
 // One thread per cell; FINE: CTAs never straddle samples (N % TPB == 0) and
 // write the per-CTA max |F| (inf for non-finite) to rmax_part[s][ct].
-template <typename T, bool FINE, bool FIELDS = false>
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
 __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
                                                   double h, double inv_h, double vt_s, double inv_s,
                                                   const double2* __restrict__ x, const double2* __restrict__ xo,
@@ -306,7 +335,7 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
   CellSys<T, S> o;
-  assemble_cell<T, S, FIELDS>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o,
+  assemble_cell<T, S, FIELDS, DROP>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o,
                               FIELDS ? cc + base : nullptr, FIELDS ? fc + base : nullptr);
   if (FINE) {
     const double fm = (double)o.fm, fs = (double)o.fs;
@@ -696,7 +725,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_p(int B, int N, int it, int maxit,
                                                 const double* __restrict__ part, LinScal* __restrict__ sc,
                                                 int* __restrict__ lin_active, int* __restrict__ iters,
                                                 int* __restrict__ status, int* __restrict__ n_active,
-                                                unsigned long long* __restrict__ lin_total) {
+                                                unsigned long long* __restrict__ lin_total,
+                                                const double* __restrict__ fin) {
   typedef typename VT<T>::v2 V2;
   __shared__ double sh[40];
   const int nct = N / TPB;
@@ -705,8 +735,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_p(int B, int N, int it, int maxit,
   if (!lin_active[s]) return;
   const int ct = (int)((e - (int64_t)s * N) / TPB);
   const int64_t stride = (int64_t)B * nct;
-  const double rho = sample_sum(part + P_RR * stride + (int64_t)s * nct, nct, sh);
-  const double rn2 = sample_sum(part + P_RN * stride + (int64_t)s * nct, nct, sh);
+  const double rho = sample_sum_or_fin(part, fin, P_RR, stride, s, nct, sh);
+  const double rn2 = sample_sum_or_fin(part, fin, P_RN, stride, s, nct, sh);
   const double bn2 = (it == 0) ? rn2 : sc[s].bnorm2;
   const bool finite = (rn2 <= 1.0e300) && (rho == rho);
   if (!finite || rn2 <= rtol2 * bn2 || it >= maxit) {
@@ -714,8 +744,7 @@ __global__ void __launch_bounds__(TPB) k_bicg_p(int B, int N, int it, int maxit,
     // step; Newton's own test decides); a non-finite one fails.
     if (threadIdx.x == 0 && ct == 0) {
       lin_active[s] = 0;
-      iters[s] = (finite && rn2 <= rtol2 * bn2) ? it : -1;
-      if (!finite) status[s] = 3;
+      iters[s] = !finite ? -2 : ((rn2 <= rtol2 * bn2) ? it : -1);
       atomicAdd(lin_total, (unsigned long long)it);
     }
     return;
@@ -741,7 +770,8 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_bicg_s(int B, int N, const typename VT<T>::v2* __restrict__ r,
                                                 const typename VT<T>::v2* __restrict__ v,
                                                 typename VT<T>::v2* __restrict__ sv, const double* __restrict__ part,
-                                                LinScal* __restrict__ sc, const int* __restrict__ lin_active) {
+                                                LinScal* __restrict__ sc, const int* __restrict__ lin_active,
+                                                const double* __restrict__ fin) {
   typedef typename VT<T>::v2 V2;
   __shared__ double sh[40];
   const int nct = N / TPB;
@@ -750,8 +780,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_s(int B, int N, const typename VT<
   if (!lin_active[s]) return;
   const int ct = (int)((e - (int64_t)s * N) / TPB);
   const int64_t stride = (int64_t)B * nct;
-  const double rho = sample_sum(part + P_RR * stride + (int64_t)s * nct, nct, sh);
-  const double rv = sample_sum(part + P_RV * stride + (int64_t)s * nct, nct, sh);
+  const double rho = sample_sum_or_fin(part, fin, P_RR, stride, s, nct, sh);
+  const double rv = sample_sum_or_fin(part, fin, P_RV, stride, s, nct, sh);
   const double alpha = rho / rv;
   if (threadIdx.x == 0 && ct == 0) {
     sc[s].rho = rho;
@@ -772,7 +802,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
                                                      const typename VT<T>::v2* __restrict__ t,
                                                      const typename VT<T>::v2* __restrict__ rh,
                                                      typename VT<T>::v2* __restrict__ r, double* __restrict__ part,
-                                                     LinScal* __restrict__ sc, const int* __restrict__ lin_active) {
+                                                     LinScal* __restrict__ sc, const int* __restrict__ lin_active,
+                                                     const double* __restrict__ fin) {
   typedef typename VT<T>::v2 V2;
   __shared__ double sh[40];
   const int nct = N / TPB;
@@ -781,8 +812,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
   if (!lin_active[s]) return;
   const int ct = (int)((e - (int64_t)s * N) / TPB);
   const int64_t stride = (int64_t)B * nct;
-  const double ts = sample_sum(part + P_TS * stride + (int64_t)s * nct, nct, sh);
-  const double tt = sample_sum(part + P_TT * stride + (int64_t)s * nct, nct, sh);
+  const double ts = sample_sum_or_fin(part, fin, P_TS, stride, s, nct, sh);
+  const double tt = sample_sum_or_fin(part, fin, P_TT, stride, s, nct, sh);
   const double omega = (tt > 0.0) ? ts / tt : 0.0;
   const double alpha = sc[s].alpha;
   if (threadIdx.x == 0 && ct == 0) sc[s].omega = omega;
@@ -798,6 +829,17 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
     part[P_RR * stride + pi] = d1;
     part[P_RN * stride + pi] = d2;
   }
+}
+
+// Samples whose BiCGStab did not converge (or broke down) in this Newton
+// iteration get a second linear solve with the fallback preconditioner.
+__global__ void k_mark_retry(int B, const int* __restrict__ newton_active, const int* __restrict__ iters,
+                             int* __restrict__ lin_active, int* __restrict__ n_retry) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B) return;
+  const int r = newton_active[s] && iters[s] < 0;
+  lin_active[s] = r;
+  if (r) atomicAdd(n_retry, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -832,26 +874,61 @@ __global__ void k_newton_res_check(int B, int nct, double atol, int maxit, const
   lin_active[s] = act;
 }
 
-// x += dx (FP64 state), per-CTA max of the scaled update.
+// Per-CTA maxima of the Newton step: max(|dp| / p_ref, |dc|) (the update
+// test) and max |dc| (the step limiter).
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_newton_update(int B, int N, double inv_pref, double2* __restrict__ x,
-                                                       const typename VT<T>::v2* __restrict__ dx,
-                                                       double* __restrict__ dmax_part,
-                                                       const int* __restrict__ newton_active) {
+__global__ void __launch_bounds__(TPB) k_newton_step_max(int B, int N, double inv_pref,
+                                                         const typename VT<T>::v2* __restrict__ dx,
+                                                         double* __restrict__ dmax_part, double* __restrict__ dc_part,
+                                                         const int* __restrict__ newton_active) {
   __shared__ double sh[40];
   const int nct = N / TPB;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int s = (int)(e / N);
   if (!newton_active[s]) return;
   const auto d = dx[e];
-  double2 xx = x[e];
-  xx.x += (double)d.x;
-  xx.y += (double)d.y;
-  x[e] = xx;
-  double loc = fmax(fabs((double)d.x) * inv_pref, fabs((double)d.y));
+  double dc = fabs((double)d.y);
+  double loc = fmax(fabs((double)d.x) * inv_pref, dc);
   if (!(loc <= 1.0e300)) loc = INFINITY;
+  if (!(dc <= 1.0e300)) dc = INFINITY;
   const double m = block_reduce<true>(loc, sh);
-  if (threadIdx.x == 0) dmax_part[(int64_t)s * nct + (e - (int64_t)s * N) / TPB] = m;
+  const double mc = block_reduce<true>(dc, sh);
+  if (threadIdx.x == 0) {
+    const int64_t i = (int64_t)s * nct + (e - (int64_t)s * N) / TPB;
+    dmax_part[i] = m;
+    dc_part[i] = mc;
+  }
+}
+
+// Per sample: theta = min(1, dc_limit / max |dc|) (a step that would change a
+// mass fraction by more than dc_limit is shortened; dc_limit <= 0: theta = 1).
+__global__ void k_newton_theta(int B, int nct, double dc_limit, const double* __restrict__ dc_part,
+                               const int* __restrict__ newton_active, double* __restrict__ theta) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= B || !newton_active[s]) return;
+  double th = 1.0;
+  if (dc_limit > 0.0) {
+    const double mc = sample_max(dc_part + (int64_t)s * nct, nct);
+    if (mc > dc_limit) th = dc_limit / mc;
+  }
+  theta[s] = th;
+}
+
+// a9: x += theta dx.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_newton_update(int B, int N, double2* __restrict__ x,
+                                                       const typename VT<T>::v2* __restrict__ dx,
+                                                       const double* __restrict__ theta,
+                                                       const int* __restrict__ newton_active) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int s = (int)(e / N);
+  if (!newton_active[s]) return;
+  const double th = theta[s];
+  const auto d = dx[e];
+  double2 xx = x[e];
+  xx.x = fma(th, (double)d.x, xx.x);
+  xx.y = fma(th, (double)d.y, xx.y);
+  x[e] = xx;
 }
 
 __global__ void k_newton_dx_check(int B, int nct, double dxtol, const double* __restrict__ dmax_part,

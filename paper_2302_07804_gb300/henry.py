@@ -37,8 +37,10 @@ class HenryConfig(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("newton_atol", "newton_dxtol", "lin_rtol")] + \
                [(n, ctypes.c_int32) for n in ("newton_maxit", "lin_maxit", "nu1", "nu2")] + \
                [("workspace_bytes", ctypes.c_double), ("newton_predictor", ctypes.c_double),
+                ("newton_dc_limit", ctypes.c_double),
                 ("fused_small_grids", ctypes.c_int32), ("coef_model", ctypes.c_int32), ("kl_terms", ctypes.c_int32)] + \
-               [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")]
+               [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")] + \
+               [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):

@@ -106,3 +106,21 @@ def test_two_layer_paper_variant_matches_oracle(hl):
     assert ok.all()
     _qoi_check(qf.cpu().numpy(), ref)
     s.close()
+
+
+def test_kl_hard_samples_converge_with_fallback(hl):
+    """Inputs with strong permeability/porosity contrast for which one
+    V-cycle preconditioner loses BiCGStab convergence (the same happens in
+    the oracle's textbook V-cycle): the fallback V-cycle on the Jacobian
+    without density derivatives and the Newton step limit let every sample
+    converge, to the oracle's solution."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "kl_hard_inputs.txt")
+    th = np.loadtxt(path)
+    s = hl.Solver(coef_model=hl.HENRY_MODEL_KL)
+    qf, _, st, _ = s.level_batch_solve(0, _to_dev(th))
+    assert int(st.abs().sum()) == 0
+    ref, ok = ohenry.solve_scenarios(PRM, 0, th, model="kl")
+    assert ok.all()
+    _qoi_check(qf.cpu().numpy(), ref)
+    s.close()
