@@ -59,19 +59,26 @@ ALU_PEAK_TFLOPS = {"f64": 152 * 2 * 2 * 2.07e9 / 1e12, "f32": 152 * 128 * 2 * 2.
 SWEEP_COUNTERS = os.path.join(ROOT, "profiles", "k_sweep_counters.json")
 
 
+def smoother_source_sha256():
+    """Hash of the smoother's source (sweep_cell and k_sweep, between the
+    'smoother source begin/end' markers of henry_kernels.cuh)."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2302_07804_gb300", "csrc", "henry_kernels.cuh")).read()
+    a = src.index("// ---- smoother source begin")
+    b = src.index("// ---- smoother source end")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()
+
+
 def sweep_traffic(alg_bytes_per_launch, precision):
     """DRAM traffic of an average smoother launch of the bench, scaled from
     the committed ncu capture of a fine-level sweep (traffic / algorithmic
     bytes, which is per swept cell and so scales with the launch's cells);
     None when the capture is missing or the smoother source changed since."""
-    import hashlib
     try:
         with open(SWEEP_COUNTERS) as f:
             c = json.load(f)
-        src = os.path.join(ROOT, "paper_2302_07804_gb300", "csrc", "henry_kernels.cuh")
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         rec = c.get(precision)
-        if not rec or rec.get("henry_kernels_cuh_sha256") != sha:
+        if not rec or rec.get("smoother_source_sha256") != smoother_source_sha256():
             return None
         return alg_bytes_per_launch * rec["traffic_bytes"] / rec["alg_bytes"]
     except Exception:
@@ -235,82 +242,81 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ GPU arm
 class Workload:
-    """The MLMC pass: one handle and one CUDA stream per level, the levels run
-    concurrently from host threads (each level's solve synchronises only its
-    own stream), joined on the main stream."""
+    """The MLMC pass through the public API: one henry_batch_solve_mixed call
+    over all levels (the library runs the levels concurrently, one child
+    handle, CUDA stream and host thread each), then one mlmc_accumulate per
+    level on the caller's stream.  `sequential=True` runs the levels one after
+    another through per-level handles instead (for per-kernel timing, where
+    levels must not overlap)."""
 
     def __init__(self, henry, torch, dev, alloc, precision, xis, with_coarse=True, **solver_kw):
-        import threading
-        self.h, self.t, self.dev, self.alloc = henry, torch, dev, alloc
+        import numpy as np
+        self.h, self.t, self.dev, self.alloc = henry, torch, dev, list(alloc)
         self.L = len(alloc)
         self.with_coarse = with_coarse
-        self.solvers = [henry.Solver(precision=precision, **solver_kw) for _ in range(self.L)]
-        self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.L)]
-        self.outs = [(torch.empty((m, 2), dtype=torch.float64, device=dev),
-                      torch.empty((m, 2), dtype=torch.float64, device=dev) if l > 0 else None,
-                      torch.empty((m,), dtype=torch.int32, device=dev)) for l, m in enumerate(alloc)]
+        self.precision, self.solver_kw = precision, solver_kw
+        self.solver = henry.Solver(precision=precision, **solver_kw)
+        self.solvers = None  # per-level handles of the sequential mode
+        self.levels = np.concatenate([np.full(m, l, dtype=np.int32) for l, m in enumerate(alloc)])
+        self.off = [0] + list(np.cumsum(alloc))
+        n = int(self.off[-1])
+        self.n = n
+        self.qf = torch.empty((n, 2), dtype=torch.float64, device=dev)
+        self.qc = torch.empty((n, 2), dtype=torch.float64, device=dev) if with_coarse else None
+        self.st = torch.empty((n,), dtype=torch.int32, device=dev)
+        self.outs = [self._slice(l) for l in range(self.L)]
         self.sums = torch.zeros((self.L, 2, 2, 3), dtype=torch.float64, device=dev)
-        self.xis = xis
-        self.fails = [0] * self.L
-        self.errors = []
-        self.threading = threading
-        # order threads by work: finest level first
-        self.order = sorted(range(self.L), key=lambda l: -alloc[l] * (8 ** l))
+        self.xis = [torch.cat(list(x)).contiguous() for x in xis]  # per step, samples in level order
+        self.fails = 0
 
-    def _level(self, l, xi, host=None):
-        torch, henry = self.t, self.h
-        try:
-            torch.cuda.set_device(self.dev)
-            s = self.streams[l]
-            with torch.cuda.stream(s):
-                if host is not None:
-                    host["xi_dev"][l].copy_(host["xi"][l], non_blocking=True)
-                    xi = host["xi_dev"][l]
-                wc = self.with_coarse and l > 0
-                qf, qc, st, stats = self.solvers[l].level_batch_solve(l, xi, with_coarse=wc, stream=s,
-                                                                      allow_failures=True,
-                                                                      out=self.outs[l] if wc or l == 0 else
-                                                                      (self.outs[l][0], None, self.outs[l][2]))
-                self.fails[l] += int(stats["failed_samples"])
-                henry.mlmc_accumulate(l, qf, qc, st, self.sums[l], stream=s)
-                if host is not None:
-                    host["qf"][l].copy_(qf, non_blocking=True)
-                    if qc is not None:
-                        host["qc"][l].copy_(qc, non_blocking=True)
-                    host["st"][l].copy_(st, non_blocking=True)
-        except Exception as exc:  # surfaced by run()
-            self.errors.append(exc)
+    def _slice(self, l):
+        a, b = self.off[l], self.off[l + 1]
+        return (self.qf[a:b], self.qc[a:b] if (self.with_coarse and l > 0) else None, self.st[a:b])
 
     def run(self, k=None, host=None, sequential=False):
-        torch = self.t
-        main = torch.cuda.current_stream(self.dev)
-        ev = torch.cuda.Event()
-        ev.record(main)
-        for s in self.streams:
-            s.wait_event(ev)
-        if sequential:  # for per-kernel timing: no overlap between levels
-            for l in self.order:
-                self._level(l, None if k is None else self.xis[k][l], host)
-                self.streams[l].synchronize()
+        torch, henry = self.t, self.h
+        stream = torch.cuda.current_stream(self.dev)
+        if host is not None:
+            host["xi_dev"].copy_(host["xi"], non_blocking=True)
+            xi = host["xi_dev"]
         else:
-            ths = [self.threading.Thread(target=self._level, args=(l, None if k is None else self.xis[k][l], host))
-                   for l in self.order]
-            for th in ths:
-                th.start()
-            for th in ths:
-                th.join()
-        if self.errors:
-            raise self.errors[0]
-        for s in self.streams:
-            main.wait_stream(s)
+            xi = self.xis[k]
+        if sequential:
+            self._run_sequential(xi, stream)
+        else:
+            _, _, _, stats = self.solver.batch_solve_mixed(self.levels, xi, with_coarse=self.with_coarse,
+                                                           stream=stream, allow_failures=True,
+                                                           out=(self.qf, self.qc, self.st))
+            self.fails += int(stats["failed_samples"])
+        for l in range(self.L):
+            qf, qc, st = self.outs[l]
+            henry.mlmc_accumulate(l, qf, qc, st, self.sums[l], stream=stream)
+        if host is not None:
+            host["qf"].copy_(self.qf, non_blocking=True)
+            if self.qc is not None:
+                host["qc"].copy_(self.qc, non_blocking=True)
+            host["st"].copy_(self.st, non_blocking=True)
+
+    def _level_solvers(self):
+        if self.solvers is None:
+            self.solvers = [self.h.Solver(precision=self.precision, **self.solver_kw) for _ in range(self.L)]
+        return self.solvers
+
+    def _run_sequential(self, xi, stream):
+        for l in range(self.L):
+            a, b = self.off[l], self.off[l + 1]
+            wc = self.with_coarse and l > 0
+            _, _, _, stats = self._level_solvers()[l].level_batch_solve(l, xi[a:b], with_coarse=wc, stream=stream,
+                                                                        allow_failures=True, out=self.outs[l])
+            self.fails += int(stats["failed_samples"])
 
     def profile(self, on):
-        for s in self.solvers:
+        for s in self._level_solvers():
             s.profile(on)
 
     def profile_read(self):
         tot = None
-        for s in self.solvers:
+        for s in self._level_solvers():
             p = s.profile_read()
             if tot is None:
                 tot = {k: list(v) for k, v in p.items()}
@@ -321,7 +327,8 @@ class Workload:
         return tot
 
     def close(self):
-        for s in self.solvers:
+        self.solver.close()
+        for s in self.solvers or []:
             s.close()
 
 
@@ -368,8 +375,8 @@ def run_uneven(args):
     sec = e0.elapsed_time(e1) / 1e3
     line = {"workload": "uneven-4096-levels0-5" + ("-kl-mixed" if kl else "-fp64"), "metric": METRIC,
             "value": cs / sec, "unit": "cell-steps/s", "seconds": sec, "counts": counts, "cell_steps": cs,
-            "failed_samples": sum(W.fails), "clocks": clk.summary(),
-            "schedule": "levels concurrent, one stream + handle each"}
+            "failed_samples": W.fails, "clocks": clk.summary(),
+            "schedule": "one henry_batch_solve_mixed call: levels concurrent, one stream + child handle each"}
     if kl:
         q32 = [W.outs[l][0].clone() for l in range(len(counts))]
         W64 = Workload(henry, torch, dev, counts, henry.HENRY_FP64, [xis], with_coarse=False, **kw)
@@ -518,14 +525,14 @@ def main():
     value = total_cells / elapsed_max
 
     # ---- e2e through the public API with host buffers (pinned), copies inside the timed region
-    host = {"xi": None, "xi_dev": [torch.empty((m, 3), dtype=torch.float64, device=dev) for m in alloc],
-            "qf": [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc],
-            "qc": [torch.empty((m, 2), dtype=torch.float64).pin_memory() for m in alloc],
-            "st": [torch.empty((m,), dtype=torch.int32).pin_memory() for m in alloc]}
-    xi_host = [[x.cpu().pin_memory() for x in xis[k]] for k in range(args.warmup, nsteps_all)]
+    host = {"xi": None, "xi_dev": torch.empty((W.n, 3), dtype=torch.float64, device=dev),
+            "qf": torch.empty((W.n, 2), dtype=torch.float64).pin_memory(),
+            "qc": torch.empty((W.n, 2), dtype=torch.float64).pin_memory(),
+            "st": torch.empty((W.n,), dtype=torch.int32).pin_memory()}
+    xi_host = [W.xis[k].cpu().pin_memory() for k in range(args.warmup, nsteps_all)]
     sums_host = torch.empty(W.sums.shape, dtype=torch.float64).pin_memory()
-    h2d = sum(m * 3 * 8 for m in alloc)
-    d2h = sum(m * 2 * 8 * (2 if l > 0 else 1) + m * 4 for l, m in enumerate(alloc)) + W.sums.numel() * 8
+    h2d = W.n * 3 * 8
+    d2h = W.n * (2 * 8 * 2 + 4) + W.sums.numel() * 8
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -547,9 +554,10 @@ def main():
                        "m_per_level": alloc, "coarse_partners": True, "cell_steps_per_step": cells_per_step,
                        "eps": EPS, "var_budget": 0.5 * EPS * EPS, "pilot": list(PILOT),
                        "V_pilot": V, "seed": inputs.SEED, "parallelism": "replicas" if world > 1 else "single",
-                       "levels_concurrent": "one stream and host thread per level",
+                       "levels_concurrent": "one henry_batch_solve_mixed call per step (one stream, child "
+                                            "handle and host thread per level)",
                        "l2": "working set > L2 (level-0 batch alone is GBs); no flush needed",
-                       "failed_samples": sum(W.fails)},
+                       "failed_samples": W.fails},
             "e2e": {"value": e2e, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary()}
 

@@ -170,6 +170,25 @@ int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const d
                             double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
                             henry_stats* stats_host, void* stream);
 
+/* a2-a11 over an uneven batch (samples at several MLMC levels in one call,
+ * the situation of an MLMC pass, Sec. 3: each level l needs m_l samples of
+ * Y_l, Eq. (A)).  Sample i is solved at level levels_host[i] (host array,
+ * 0 <= level <= max_level, any order) with inputs xi_dev[i][n_xi]; its QoIs go
+ * to qoi_fine_dev[i][2] and, when with_coarse != 0, those of its coarse partner
+ * (level - 1, same xi) to qoi_coarse_dev[i][2] (zeros for level-0 samples).
+ * status_dev[i] as in henry_level_batch_solve.  The levels run concurrently:
+ * each on its own child handle (created on first use, same configuration,
+ * its own workspace), CUDA stream and host thread, forked from `stream` by an
+ * event; samples not already in level order are gathered into level order
+ * and their results scattered back.  Results are bit-identical to
+ * henry_level_batch_solve on the same samples.  stats_host (nullable) sums
+ * over levels.  Synchronises `stream`.  Errors: EINVAL (NULL pointer, n <= 0,
+ * a level out of range), ENOMEM, ECUDA, ENOCONV as in henry_level_batch_solve
+ * (the first failing level's message for the others). */
+int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, int with_coarse,
+                            const double* xi_dev, double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
+                            henry_stats* stats_host, void* stream);
+
 /* a12. Merge one batch of level-`level` samples into running MLMC sums.
  * Y = qoi_fine - qoi_coarse (qoi_coarse_dev NULL: Y = qoi_fine, level 0), the
  * level term of the telescoping sum Eq. (EgL) / Def. (Yell).  Samples with

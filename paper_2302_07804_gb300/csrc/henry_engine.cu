@@ -23,6 +23,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "henry.h"
@@ -66,7 +67,7 @@ struct Level {
   double h;
   double2 *x, *xo;  // state (fine: Newton iterate; coarse: restricted) and old state
   double2* cc;      // per-cell (phi, K / mu) of the field models (else null)
-  double4* fc;      // per-cell east/north face harmonic means of the field models (else null)
+  double4_32a* fc;      // per-cell east/north face harmonic means of the field models (else null)
   void* J;          // 6 planes of B4
   void *mgx, *mgb;  // multigrid vectors (coarse levels)
   int64_t plane;
@@ -124,7 +125,7 @@ struct Group {
       l.fc = nullptr;
       if (fields) {
         l.cc = c.take<double2>(sizeof(double2) * l.plane);
-        l.fc = c.take<double4>(sizeof(double4) * l.plane);
+        l.fc = c.take<double4_32a>(sizeof(double4_32a) * l.plane);
       }
       if (light_ws) {
         if (L.empty()) l.xo = c.take<double2>(sizeof(double2) * l.plane);
@@ -215,6 +216,13 @@ struct henry_handle {
   unsigned long long* host_totals = nullptr;
   Prof prof;
   int nact = 0;  // samples iterating in the current Newton / Krylov iteration (for byte counts)
+  // henry_batch_solve_mixed: one child handle, stream and host thread per
+  // level, plus a buffer for batches whose samples are not sorted by level
+  std::map<int, henry_handle*> kids;
+  std::map<int, cudaStream_t> kid_streams;
+  cudaEvent_t ev_fork = nullptr;
+  char* perm_mem = nullptr;
+  int perm_cap = 0;
 };
 
 namespace {
@@ -1034,6 +1042,10 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
 void henry_destroy(henry_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (auto& kv : h->kids) henry_destroy(kv.second);
+  for (auto& kv : h->kid_streams) cudaStreamDestroy(kv.second);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->perm_mem) cudaFree(h->perm_mem);
   for (auto& p : h->prof.pend) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -1058,6 +1070,149 @@ void henry_destroy(henry_handle* h) {
 
 const char* henry_last_error(void) { return g_err.c_str(); }
 
+int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, int with_coarse,
+                            const double* xi_dev, double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
+                            henry_stats* stats_host, void* stream) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!levels_host || !xi_dev || !qoi_fine_dev || !status_dev) return set_err(HENRY_EINVAL, "NULL pointer");
+  if (with_coarse && !qoi_coarse_dev) return set_err(HENRY_EINVAL, "qoi_coarse_dev is NULL");
+  const int NL = h->cfg.max_level + 1;
+  std::vector<int> cnt(NL, 0), first(NL, 0);
+  for (int i = 0; i < n; ++i) {
+    if (!valid_level(h, levels_host[i]))
+      return set_err(HENRY_EINVAL, "levels_host[%d] = %d outside [0, %d]", i, levels_host[i], h->cfg.max_level);
+    ++cnt[levels_host[i]];
+  }
+  for (int l = 1; l < NL; ++l) first[l] = first[l - 1] + cnt[l - 1];
+  // perm[j]: original index of the j-th sample in level order (stable)
+  std::vector<int> perm(n), pos(first);
+  bool sorted = true;
+  for (int i = 0; i < n; ++i) {
+    const int j = pos[levels_host[i]]++;
+    perm[j] = i;
+    sorted = sorted && j == i;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nin = n_inputs(h->cfg);
+  const double* xs = xi_dev;
+  double* qf = qoi_fine_dev;
+  double* qc = qoi_coarse_dev;
+  int32_t* ss = status_dev;
+  int* perm_dev = nullptr;
+  if (!sorted) {  // gather into level order; results are scattered back below
+    auto carve = [&](int cap, char* base, int** pd, double** x, double** f, double** c, int32_t** sd) {
+      size_t o = 0;
+      auto take = [&](size_t b) {
+        char* p = base ? base + o : nullptr;
+        o += (b + 255) & ~(size_t)255;
+        return p;
+      };
+      *pd = (int*)take(sizeof(int) * cap);
+      *x = (double*)take(sizeof(double) * cap * nin);
+      *f = (double*)take(sizeof(double) * cap * 2);
+      *c = (double*)take(sizeof(double) * cap * 2);
+      *sd = (int32_t*)take(sizeof(int32_t) * cap);
+      return o;
+    };
+    int* pd;
+    double *x, *f, *c;
+    int32_t* sd;
+    if (h->perm_cap < n) {
+      if (h->perm_mem) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(h->perm_mem));
+        h->perm_mem = nullptr;
+        h->perm_cap = 0;
+      }
+      const size_t bytes = carve(n, nullptr, &pd, &x, &f, &c, &sd);
+      if (cudaMalloc(&h->perm_mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        h->perm_mem = nullptr;
+        return set_err(HENRY_ENOMEM, "cudaMalloc of %zu bytes for the level permutation failed", bytes);
+      }
+      h->perm_cap = n;
+    }
+    carve(h->perm_cap, h->perm_mem, &pd, &x, &f, &c, &sd);
+    perm_dev = pd;
+    CK(cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    k_permute_rows<double, false><<<nblk((int64_t)n * nin), TPB, 0, st>>>(n, nin, perm_dev, xi_dev, x);
+    CKL();
+    xs = x;
+    qf = f;
+    qc = c;
+    ss = sd;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (!h->ev_fork) CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventRecord(h->ev_fork, st));
+  std::vector<int> act;
+  for (int l = NL - 1; l >= 0; --l) {  // finest (longest) level first
+    if (!cnt[l]) continue;
+    if (!h->kids.count(l)) {
+      henry_handle* k = nullptr;
+      const int rc = henry_create(&h->cfg, &k);
+      if (rc) return rc;
+      h->kids[l] = k;
+      cudaStream_t ls = nullptr;
+      CK(cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking));
+      h->kid_streams[l] = ls;
+    }
+    henry_handle* k = h->kids[l];
+    if (k->prof.on != h->prof.on) {
+      const int rc = henry_profile(k, h->prof.on ? 1 : 0);
+      if (rc) return rc;
+    }
+    CK(cudaStreamWaitEvent(h->kid_streams[l], h->ev_fork, 0));
+    act.push_back(l);
+  }
+  std::vector<int> rcs(NL, HENRY_OK);
+  std::vector<std::string> msg(NL);
+  std::vector<henry_stats> sts(NL);
+  std::vector<std::thread> ths;
+  for (int l : act) {
+    ths.emplace_back([&, l] {
+      cudaSetDevice(dev);
+      std::memset(&sts[l], 0, sizeof sts[l]);
+      const int wc = (with_coarse && l > 0) ? 1 : 0;
+      const int64_t o = first[l];
+      rcs[l] = henry_level_batch_solve(h->kids[l], l, wc, xs + o * nin, cnt[l], qf + o * 2, wc ? qc + o * 2 : nullptr,
+                                       ss + o, &sts[l], h->kid_streams[l]);
+      if (rcs[l] != HENRY_OK && rcs[l] != HENRY_ENOCONV) msg[l] = henry_last_error();
+    });
+  }
+  for (auto& t : ths) t.join();
+  // every level solve synchronised its own stream, so its results are in memory
+  for (int l : act)
+    if (rcs[l] != HENRY_OK && rcs[l] != HENRY_ENOCONV) return set_err(rcs[l], "level %d: %s", l, msg[l].c_str());
+  if (with_coarse && cnt[0]) CK(cudaMemsetAsync(qc + (int64_t)first[0] * 2, 0, sizeof(double) * 2 * cnt[0], st));
+  if (!sorted) {
+    k_permute_rows<double, true><<<nblk((int64_t)n * 2), TPB, 0, st>>>(n, 2, perm_dev, qf, qoi_fine_dev);
+    CKL();
+    if (with_coarse) {
+      k_permute_rows<double, true><<<nblk((int64_t)n * 2), TPB, 0, st>>>(n, 2, perm_dev, qc, qoi_coarse_dev);
+      CKL();
+    }
+    k_permute_rows<int32_t, true><<<nblk(n), TPB, 0, st>>>(n, 1, perm_dev, ss, status_dev);
+    CKL();
+  }
+  CK(cudaStreamSynchronize(st));
+  henry_stats tot;
+  std::memset(&tot, 0, sizeof tot);
+  for (int l : act) {
+    tot.newton_iters += sts[l].newton_iters;
+    tot.linear_iters += sts[l].linear_iters;
+    tot.newton_solves += sts[l].newton_solves;
+    tot.failed_samples += sts[l].failed_samples;
+    tot.cell_steps += sts[l].cell_steps;
+  }
+  if (stats_host) *stats_host = tot;
+  if (tot.failed_samples)
+    return set_err(HENRY_ENOCONV, "%lld of %d samples did not converge", (long long)tot.failed_samples, n);
+  return HENRY_OK;
+}
+
 int henry_profile(henry_handle* h, int enable) {
   if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
   Prof& P = h->prof;
@@ -1074,6 +1229,10 @@ int henry_profile(henry_handle* h, int enable) {
     }
   }
   P.on = enable != 0;
+  for (auto& kv : h->kids) {
+    const int rc = henry_profile(kv.second, enable);
+    if (rc) return rc;
+  }
   return HENRY_OK;
 }
 
@@ -1086,10 +1245,22 @@ int henry_profile_read(henry_handle* h, int kclass, double* total_ms, int64_t* l
     CK(cudaDeviceSynchronize());
     prof_drain(h);
   }
-  if (total_ms) *total_ms = P.ms[kclass];
-  if (launches) *launches = P.launches[kclass];
-  if (alg_bytes) *alg_bytes = P.bytes[kclass];
-  if (alg_flops) *alg_flops = P.flops[kclass];
+  double ms = P.ms[kclass], by = P.bytes[kclass], fl = P.flops[kclass];
+  int64_t nl = P.launches[kclass];
+  for (auto& kv : h->kids) {  // the per-level handles of henry_batch_solve_mixed
+    double a, b, c;
+    int64_t d;
+    const int rc = henry_profile_read(kv.second, kclass, &a, &d, &b, &c);
+    if (rc) return rc;
+    ms += a;
+    nl += d;
+    by += b;
+    fl += c;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = nl;
+  if (alg_bytes) *alg_bytes = by;
+  if (alg_flops) *alg_flops = fl;
   return HENRY_OK;
 }
 

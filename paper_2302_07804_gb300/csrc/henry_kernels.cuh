@@ -200,7 +200,7 @@ template <typename T, typename S, bool FIELDS = false, bool DROP = false>
 __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, int nx, int ny, double h, double inv_h,
                                               double vt_s, double inv_s, const double2* xs, const double2* xos,
                                               int st, int ix, int iy, CellSys<T, S>& o,
-                                              const double2* cc = nullptr, const double4* fc = nullptr) {
+                                              const double2* cc = nullptr, const double4_32a* fc = nullptr) {
   S kmu, PD, phi;
   if (FIELDS) {
     const double2 c = cc[st];
@@ -235,7 +235,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     const int sn = st_of(jx, jy, nx);
     S kmu_f = kmu, PD_f = PD;
     if (FIELDS) {  // the face's harmonic means, stored with the cell west of / below the face
-      const double4 f = fc[(k == 0 || k == 2) ? sn : st];
+      const double4_32a f = fc[(k == 0 || k == 2) ? sn : st];
       kmu_f = (S)(((k < 2) ? f.x : f.z) * inv_s);
       PD_f = (S)(((k < 2) ? f.y : f.w) * inv_s);
     }
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
                                                   const int* __restrict__ active, double2* __restrict__ F,
                                                   typename VT<T>::b4* __restrict__ J, int64_t plane,
                                                   double* __restrict__ rmax_part, const double2* __restrict__ cc = nullptr,
-                                                  const double4* __restrict__ fc = nullptr) {
+                                                  const double4_32a* __restrict__ fc = nullptr) {
   typedef typename std::conditional<FINE, double, T>::type S;
   __shared__ double sh[40];
   const int N = nx * ny;
@@ -467,6 +467,7 @@ __global__ void k_coarse_solve(int B, const T* __restrict__ Ainv, const typename
   x[2 * (int64_t)s + 1] = mk2<V2>(o[2], o[3]);
 }
 
+// ---- smoother source begin (the measured sweep-traffic record is keyed to the hash of this region)
 // a7: one half-sweep of red-black point-block Gauss-Seidel over colour `col`:
 //   x_P = C_P^{-1} (b_P - sum_nb A_nb x_nb).
 // MODE 0: x = 0 before the sweep (first pre-smoothing sweep: x_P = C_P^{-1} b_P).
@@ -526,6 +527,7 @@ __global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, c
   x[base + i] = sweep_cell<T, MODE>(nx, ny, ix, iy, i, J + base, plane, b + base, x + base,
                                     MODE == 2 ? xc + (int64_t)s * (N >> 2) : nullptr);
 }
+// ---- smoother source end
 
 // Residual r_P = b_P - (A x)_P of one cell (sample-relative arrays).
 template <typename T>

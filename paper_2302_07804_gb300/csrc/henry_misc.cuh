@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TPB) k_restrict_cc(int B, int ncx, int ncy, co
 // Face coefficients: harmonic means 2 a b / (a + b) of K / mu and of phi Dm on
 // the east (.x, .y) and north (.z, .w) face of every cell, 0 on the boundary.
 __global__ void __launch_bounds__(TPB) k_face_coefs(int B, int nx, int ny, double Dm, const double2* __restrict__ cc,
-                                                    double4* __restrict__ fc) {
+                                                    double4_32a* __restrict__ fc) {
   const int N = nx * ny;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   if (e >= (int64_t)B * N) return;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TPB) k_face_coefs(int B, int nx, int ny, doubl
   xy_of(st, nx, ix, iy);
   const double2* c = cc + (int64_t)s * N;
   const double2 P = c[st];
-  double4 f;
+  double4_32a f;
   f.x = f.y = f.z = f.w = 0.0;
   auto harm = [](double a, double b) { return 2.0 * a * b / (a + b); };
   if (ix + 1 < nx) {
@@ -273,6 +273,25 @@ __global__ void __launch_bounds__(TPB) k_blocks_out(int B, int nx, int ny, const
     o[2] = (double)b.a10;
     o[3] = (double)b.a11;
   }
+}
+
+// Row permutation of a [n][w] array (uneven mixed-level batches): gather
+// dst[i] = src[perm[i]] or scatter dst[perm[i]] = src[i].
+template <typename E, bool SCATTER>
+__global__ void k_permute_rows(int n, int w, const int* __restrict__ perm, const E* __restrict__ src,
+                               E* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * w) return;
+  const int i = (int)(t / w), k = (int)(t % w);
+  const int64_t j = perm[i];
+  if (SCATTER) dst[j * w + k] = src[t];
+  else dst[t] = src[j * w + k];
+}
+// Zero the rows perm[i], i in [0, n), of a [*][w] array.
+__global__ void k_zero_rows(int n, int w, const int* __restrict__ perm, double* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * w) return;
+  dst[(int64_t)perm[t / w] * w + t % w] = 0.0;
 }
 
 __global__ void __launch_bounds__(TPB) k_scale_d2(int64_t n, double a, double2* __restrict__ x) {

@@ -24,7 +24,7 @@ N_XI = 3
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
-           "henry_profile_read", "henry_level_batch_solve_static")
+           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused")
 
@@ -78,6 +78,7 @@ def lib():
         L.henry_last_error.restype = ctypes.c_char_p
         L.henry_sample_xi.argtypes = [U64, I, U64, I, P, P]
         L.henry_level_batch_solve.argtypes = [P, I, I, P, I, P, P, P, ctypes.POINTER(HenryStats), P]
+        L.henry_batch_solve_mixed.argtypes = [P, P, I, I, P, P, P, P, ctypes.POINTER(HenryStats), P]
         L.mlmc_accumulate.argtypes = [I, I, I, P, P, P, P, P]
         L.mlmc_allocate.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(D), D, ctypes.POINTER(I64)]
         L.henry_assemble.argtypes = [P, I, P, I, P, P, P, P, P]
@@ -230,6 +231,28 @@ class Solver:
         stats = HenryStats()
         rc = lib().henry_level_batch_solve(self._h, level, 1 if with_coarse else 0, _ptr(xi), n, _ptr(qf), _ptr(qc),
                                            _ptr(st), ctypes.byref(stats), _stream(stream))
+        _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
+        return qf, qc, st, stats.as_dict()
+
+    def batch_solve_mixed(self, levels, xi, with_coarse=False, stream=None, allow_failures=False, out=None):
+        """Uneven batch: sample i at level levels[i] (henry_batch_solve_mixed).
+        Returns (qoi_fine[n][2], qoi_coarse[n][2] or None, status[n] int32, stats dict)."""
+        import numpy as np
+        lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+        n = xi.shape[0]
+        if lv.shape != (n,):
+            raise ValueError("levels must hold one level per row of xi")
+        _dev_f64(xi, (n, self.n_xi))
+        if out is None:
+            qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
+            qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
+            st = torch.empty((n,), dtype=torch.int32, device=xi.device)
+        else:
+            qf, qc, st = out
+        stats = HenryStats()
+        rc = lib().henry_batch_solve_mixed(self._h, lv.ctypes.data_as(ctypes.c_void_p), n, 1 if with_coarse else 0,
+                                           _ptr(xi), _ptr(qf), _ptr(qc), _ptr(st), ctypes.byref(stats),
+                                           _stream(stream))
         _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
         return qf, qc, st, stats.as_dict()
 

@@ -79,4 +79,12 @@ def test_null_and_range_arguments_return_einval(L):
     assert L.henry_sample_xi(1, 0, 0, 0, P(16), None) == henry.HENRY_EINVAL
     assert L.mlmc_accumulate(0, 0, 2, P(16), None, None, P(16), None) == henry.HENRY_EINVAL
     assert L.henry_assemble(s._h, -1, P(16), 1, P(16), P(16), P(16), None, None) == henry.HENRY_EINVAL
+    lv = (ctypes.c_int32 * 3)(0, 1, 9)
+    mixed = L.henry_batch_solve_mixed
+    assert mixed(s._h, lv, 3, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert b"levels_host[2]" in L.henry_last_error()
+    assert mixed(s._h, lv, 0, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert mixed(s._h, lv, 2, 1, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert mixed(s._h, None, 2, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
+    assert mixed(None, lv, 2, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
     s.close()
