@@ -605,6 +605,16 @@ def main():
                            "alloc": r["alloc"], "cell_steps": r["cell_steps"]}
             s2.close()
         line["mlmc_time_to_rmse_1e-3"] = times
+        # ---- rates of the complexity theorem and the bias test, from the timed run's own sums (c at the point)
+        S = W.sums.cpu()
+        mY = [float(S[l, 0, 1, 1]) for l in range(W.L)]
+        vY = [float(S[l, 0, 1, 2]) / max(float(S[l, 0, 1, 0]) - 1.0, 1.0) for l in range(W.L)]
+        a, b, g = henry.mlmc_rates(mY, vY, s_model, first_level=1)
+        bias, ok = henry.mlmc_bias_test(mY, max(a, 0.5), EPS)
+        line["mlmc_rates"] = {"alpha": a, "beta": b, "gamma_d": g, "bias_est": bias, "bias_ok": ok,
+                              "mean_Y": mY, "V_Y": vY, "samples": [float(S[l, 0, 1, 0]) for l in range(W.L)],
+                              "fit": "least squares over levels 1..3 (mlmc_rates); bias |E Y_L|/(2^alpha-1) "
+                                     "vs eps/sqrt(2)"}
         # ---- CPU oracle on the host cores (bounded sample)
         try:
             v, cores, desc, wall = oracle_sample()

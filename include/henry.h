@@ -206,6 +206,27 @@ int mlmc_accumulate(int level, int n, int n_qoi, const double* qoi_fine_dev, con
  * Levels with V_l = 0 get m_l = 0.  Host only, synchronous. */
 int mlmc_allocate(int n_levels, const double* V_host, const double* s_host, double var_budget, int64_t* m_out_host);
 
+/* Rates of Theorem (costMLMC), estimated from per-level statistics as the
+ * paper does from its preliminary runs (Sec. 3; the slopes of Fig.
+ * weak_strong): least-squares slopes over levels first_level .. n_levels - 1
+ * of log2 |mean_Y_l| (alpha = -slope, weak rate of Eq. weak_error_model),
+ * log2 V_l (beta = -slope, Eq. strong_error_model) and log2 s_l (gamma_d =
+ * d gamma = +slope, cost growth).  Host arrays indexed by level; any output
+ * pointer may be NULL (that rate is skipped, its input may then be NULL).
+ * Errors: EINVAL with fewer than two levels, or a zero / non-finite value
+ * (negative V_l or s_l).  Host only, synchronous. */
+int mlmc_rates(int n_levels, int first_level, const double* mean_Y_host, const double* V_host,
+               const double* s_host, double* alpha, double* beta, double* gamma_d);
+
+/* Bias test for adding levels (Eq. MSE asks (E[g_L - g])^2 <= eps^2 / 2):
+ * with the weak error model |E[g_l - g]| ~ c 2^-alpha l the remaining bias is
+ * the geometric tail E[Y_L] / (2^alpha - 1), so *bias_est = |mean_Y[L]| /
+ * (2^alpha - 1), L = n_levels - 1, and *converged = (bias_est <= eps /
+ * sqrt 2).  Either output may be NULL.  Errors: EINVAL (n_levels < 2, alpha
+ * or eps <= 0, non-finite mean).  Host only, synchronous. */
+int mlmc_bias_test(int n_levels, const double* mean_Y_host, double alpha, double eps, double* bias_est,
+                   int32_t* converged);
+
 /* ---- Per-step entry points: one step of the solve on given states, for
  * checking each step on its own.  Each evaluates the coefficients of
  * xi_dev[n][3] at `level` and takes the current and previous-time-step states

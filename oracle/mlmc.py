@@ -62,3 +62,25 @@ def allocate(V, s, var_budget):
 def total_cost(V, s, var_budget):
     """S = var_budget^-1 (sum_l sqrt(V_l s_l))^2."""
     return (sum(math.sqrt(float(v) * float(c)) for v, c in zip(V, s))) ** 2 / var_budget
+
+
+def rates(mean_Y, V, s, first_level=1):
+    """Rates of Theorem (costMLMC) from per-level statistics: the least-squares
+    slopes (numpy polyfit, degree 1) of log2 |E[Y_l]| (alpha = -slope, the weak
+    error model), log2 V_l (beta = -slope, the variance model) and log2 s_l
+    (gamma_d = d gamma = +slope, the cost model) over l = first_level .. L."""
+    lev = np.arange(first_level, len(V))
+
+    def slope(y):
+        return np.polyfit(lev, np.log2(np.asarray(y, dtype=np.float64)[first_level:]), 1)[0]
+
+    return -slope(np.abs(mean_Y)), -slope(V), slope(s)
+
+
+def bias_test(mean_Y, alpha, eps):
+    """Remaining bias of a level-L estimator under the weak error model
+    |E[g_l - g]| = c 2^(-alpha l): E[g - g_L] = sum_{l > L} E[Y_l] = E[Y_L] / (2^alpha - 1)
+    (geometric series); Eq. (MSE) asks its square to stay below eps^2 / 2.
+    Returns (estimate, passed)."""
+    b = abs(float(mean_Y[-1])) / (2.0 ** alpha - 1.0)
+    return b, b <= eps / math.sqrt(2.0)

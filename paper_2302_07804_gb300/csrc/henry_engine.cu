@@ -1338,6 +1338,64 @@ int mlmc_allocate(int n_levels, const double* V, const double* s, double var_bud
   return HENRY_OK;
 }
 
+// Least-squares slope of y_l against l over the given levels (closed form
+// of the 2-parameter linear regression).
+static double ls_slope(int n, const double* l, const double* y) {
+  double ml = 0.0, my = 0.0;
+  for (int i = 0; i < n; ++i) {
+    ml += l[i];
+    my += y[i];
+  }
+  ml /= n;
+  my /= n;
+  double sxy = 0.0, sxx = 0.0;
+  for (int i = 0; i < n; ++i) {
+    sxy += (l[i] - ml) * (y[i] - my);
+    sxx += (l[i] - ml) * (l[i] - ml);
+  }
+  return sxy / sxx;
+}
+
+int mlmc_rates(int n_levels, int first_level, const double* mean_Y, const double* V, const double* s,
+               double* alpha, double* beta, double* gamma_d) {
+  if (n_levels <= 0 || first_level < 0 || n_levels - first_level < 2)
+    return set_err(HENRY_EINVAL, "need at least two levels from first_level (n_levels %d, first_level %d)",
+                   n_levels, first_level);
+  const int n = n_levels - first_level;
+  std::vector<double> l(n), y(n);
+  for (int i = 0; i < n; ++i) l[i] = first_level + i;
+  struct {
+    const double* a;
+    double* out;
+    double sign;
+    bool absval;
+  } fits[3] = {{mean_Y, alpha, -1.0, true}, {V, beta, -1.0, false}, {s, gamma_d, 1.0, false}};
+  for (auto& f : fits) {
+    if (!f.out) continue;
+    if (!f.a) return set_err(HENRY_EINVAL, "input array for a requested rate is NULL");
+    for (int i = 0; i < n; ++i) {
+      const double v = f.absval ? std::fabs(f.a[first_level + i]) : f.a[first_level + i];
+      if (!(v > 0.0) || !std::isfinite(v))
+        return set_err(HENRY_EINVAL, "level %d: value %g must be finite and nonzero (positive)", first_level + i,
+                       f.a[first_level + i]);
+      y[i] = std::log2(v);
+    }
+    *f.out = f.sign * ls_slope(n, l.data(), y.data());
+  }
+  return HENRY_OK;
+}
+
+int mlmc_bias_test(int n_levels, const double* mean_Y, double alpha, double eps, double* bias_est,
+                   int32_t* converged) {
+  if (n_levels < 2 || !mean_Y) return set_err(HENRY_EINVAL, "need at least two levels");
+  if (!(alpha > 0.0) || !(eps > 0.0)) return set_err(HENRY_EINVAL, "alpha and eps must be positive");
+  const double b = std::fabs(mean_Y[n_levels - 1]) / (std::exp2(alpha) - 1.0);
+  if (!std::isfinite(b)) return set_err(HENRY_EINVAL, "mean_Y[%d] is not finite", n_levels - 1);
+  if (bias_est) *bias_est = b;
+  if (converged) *converged = b <= eps / std::sqrt(2.0) ? 1 : 0;
+  return HENRY_OK;
+}
+
 #define STEP_DISPATCH(which, in, out, out2, iters)                                                              \
   (h->cfg.precision == HENRY_MIXED                                                                             \
        ? step_entry<float>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,        \

@@ -24,7 +24,7 @@ N_XI = 3
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
-           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed")
+           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused")
 
@@ -81,6 +81,9 @@ def lib():
         L.henry_batch_solve_mixed.argtypes = [P, P, I, I, P, P, P, P, ctypes.POINTER(HenryStats), P]
         L.mlmc_accumulate.argtypes = [I, I, I, P, P, P, P, P]
         L.mlmc_allocate.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(D), D, ctypes.POINTER(I64)]
+        L.mlmc_rates.argtypes = [I, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                 ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.mlmc_bias_test.argtypes = [I, ctypes.POINTER(D), D, D, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int32)]
         L.henry_assemble.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
@@ -159,6 +162,27 @@ def mlmc_allocate(V, s, var_budget):
     out = (ctypes.c_int64 * L)()
     _check(lib().mlmc_allocate(L, Va, sa, float(var_budget), out))
     return [int(v) for v in out]
+
+
+def mlmc_rates(mean_Y=None, V=None, s=None, first_level=1):
+    """(alpha, beta, gamma_d) of Theorem (costMLMC) from per-level statistics
+    (host; mlmc_rates).  A rate whose input is None is returned as None."""
+    ins = [mean_Y, V, s]
+    n = len(next(a for a in ins if a is not None))
+    arrs = [None if a is None else (ctypes.c_double * n)(*[float(v) for v in a]) for a in ins]
+    outs = [ctypes.c_double() for _ in ins]
+    refs = [None if a is None else ctypes.byref(o) for a, o in zip(ins, outs)]
+    _check(lib().mlmc_rates(n, first_level, *arrs, *refs))
+    return tuple(None if a is None else o.value for a, o in zip(ins, outs))
+
+
+def mlmc_bias_test(mean_Y, alpha, eps):
+    """(bias estimate |mean_Y[L]| / (2^alpha - 1), bias <= eps / sqrt 2) (host; mlmc_bias_test)."""
+    n = len(mean_Y)
+    arr = (ctypes.c_double * n)(*[float(v) for v in mean_Y])
+    b, ok = ctypes.c_double(), ctypes.c_int32()
+    _check(lib().mlmc_bias_test(n, arr, float(alpha), float(eps), ctypes.byref(b), ctypes.byref(ok)))
+    return b.value, bool(ok.value)
 
 
 def level_batch_solve_static(cfg, level, xi, with_coarse=False, stream=None, allow_failures=False):

@@ -108,7 +108,8 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
     from . import inputs
     seed = inputs.SEED if seed is None else seed
     dev = torch.device("cuda", torch.cuda.current_device())
-    levels = state or [LevelState(l, dev) for l in range(max_level + 1)]
+    levels = list(state) if state else []
+    levels += [LevelState(l, dev) for l in range(len(levels), max_level + 1)]
     t0 = time.perf_counter()
     for l in range(max_level + 1):
         need = max(0, pilot[l] - levels[l].n_used)
@@ -147,4 +148,37 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
     return {"estimate": est, "variance": var_est, "rmse_stat": math.sqrt(var_est), "eps": eps,
             "var_budget": budget, "alloc": alloc, "wall_seconds": wall,
             "cell_steps": sum(p["cell_steps"] for p in per), "levels": per,
-            "checkpoint": json.dumps([st.to_json() for st in levels])}
+            "checkpoint": json.dumps([st.to_json() for st in levels]), "state": levels}
+
+
+def run_mlmc_adaptive(solver, eps=1e-3, L_start=2, L_max=None, pilot=(1000, 200, 50, 20, 10, 10, 10, 10, 10),
+                      seed=None, qoi=1, cost="model", alpha_min=0.5, log=None):
+    """MLMC with the finest level chosen by the bias test (Sec. 3: Eq. (MSE)
+    splits eps^2 into eps^2 / 2 for the variance and eps^2 / 2 for the
+    squared bias).  Levels 0 .. L_start are allocated as in run_mlmc; the weak
+    rate alpha is fitted over levels 1 .. L (mlmc_rates, at least alpha_min),
+    and level L + 1 is added while the bias test fails and L < L_max.  The
+    result of the last run_mlmc pass carries L, the rates and the bias test."""
+    L_max = solver.cfg.max_level if L_max is None else L_max
+    if L_start < 2 or L_start > L_max:
+        raise ValueError("need 2 <= L_start <= L_max to fit the weak rate over levels 1 .. L")
+    t0 = time.perf_counter()
+    state = None
+    L = L_start
+    while True:
+        res = run_mlmc(solver, eps, max_level=L, pilot=pilot, seed=seed, qoi=qoi, cost=cost, state=state, log=log)
+        state = res["state"]
+        means = [p["mean_Y"] for p in res["levels"]]
+        var = [p["var_Y"] for p in res["levels"]]
+        s = [level_cost_model(solver.cfg, l) for l in range(L + 1)]
+        alpha, beta, gamma_d = henry.mlmc_rates(means, var, s, first_level=1)
+        alpha_used = max(alpha, alpha_min)
+        bias, ok = henry.mlmc_bias_test(means, alpha_used, eps)
+        if log:
+            log("L=%d alpha=%.3f beta=%.3f gamma_d=%.3f bias=%.3g ok=%s" % (L, alpha, beta, gamma_d, bias, ok))
+        res.update({"L": L, "alpha": alpha, "alpha_used": alpha_used, "beta": beta, "gamma_d": gamma_d,
+                    "bias_est": bias, "bias_ok": ok, "wall_seconds": time.perf_counter() - t0,
+                    "cell_steps": sum(st.cell_steps for st in state)})
+        if ok or L >= L_max:
+            return res
+        L += 1

@@ -88,3 +88,38 @@ def test_null_and_range_arguments_return_einval(L):
     assert mixed(s._h, None, 2, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
     assert mixed(None, lv, 2, 0, P(16), P(16), None, P(16), None, None) == henry.HENRY_EINVAL
     s.close()
+
+
+def test_mlmc_rates_and_bias_test_match_oracle(L):
+    import numpy as np
+    from oracle import mlmc as omlmc
+    from paper_2302_07804_gb300 import henry
+    rows = golden_rows("paper_table_M_ell.txt")
+    s = [float(v) for v in rows[0][1:]]
+    V = [float(v) for v in rows[1][1:]]
+    gen = np.random.default_rng(5)
+    means = list(0.02 * 2.0 ** -np.arange(6) * np.exp(0.3 * gen.standard_normal(6)))
+    for first in (0, 1, 2):
+        got = henry.mlmc_rates(means, V, s, first_level=first)
+        ref = omlmc.rates(means, V, s, first_level=first)
+        np.testing.assert_allclose(got, ref, rtol=1e-12)
+    a, b, g = henry.mlmc_rates(None, V, None)
+    assert a is None and g is None and b == pytest.approx(omlmc.rates(means, V, s)[1], rel=1e-12)
+    for alpha, eps in ((1.0, 1e-3), (0.7, 1e-2), (2.0, 1e-5)):
+        b, ok = henry.mlmc_bias_test(means, alpha, eps)
+        rb, rok = omlmc.bias_test(means, alpha, eps)
+        assert b == pytest.approx(rb, rel=1e-14) and ok == rok
+
+
+def test_mlmc_rates_reject_bad_input(L):
+    from paper_2302_07804_gb300 import henry
+    for args in (([1.0], [1.0], [1.0], 0), ([1.0, 0.5], [1.0, 0.5], [1.0, 2.0], 1),
+                 ([1.0, 0.0, 0.1], [1.0, 0.5, 0.2], [1.0, 2.0, 4.0], 0),
+                 ([1.0, 0.5, 0.1], [1.0, -0.5, 0.2], [1.0, 2.0, 4.0], 0)):
+        with pytest.raises(henry.HenryError) as e:
+            henry.mlmc_rates(*args[:3], first_level=args[3])
+        assert e.value.code == henry.HENRY_EINVAL
+    for args in (([1.0], 1.0, 1e-3), ([1.0, 0.5], 0.0, 1e-3), ([1.0, 0.5], 1.0, 0.0),
+                 ([1.0, float("nan")], 1.0, 1e-3)):
+        with pytest.raises(henry.HenryError):
+            henry.mlmc_bias_test(*args)

@@ -1,0 +1,40 @@
+"""The MLMC driver on the GPU: the adaptive choice of the finest level by the
+bias test, with the rates fitted by the library checked against the oracle's
+fit of the same per-level statistics."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlmc as omlmc
+
+
+@pytest.fixture(scope="module")
+def hl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_07804_gb300 import build, henry
+    build.build()
+    return henry
+
+
+def test_adaptive_mlmc_bias_test_and_rates(hl):
+    from paper_2302_07804_gb300 import mlmc
+    s = hl.Solver()
+    eps = 5e-3
+    r = mlmc.run_mlmc_adaptive(s, eps=eps, L_start=2, L_max=3, pilot=(200, 50, 20, 10))
+    means = [p["mean_Y"] for p in r["levels"]]
+    var = [p["var_Y"] for p in r["levels"]]
+    assert r["L"] in (2, 3) and len(means) == r["L"] + 1
+    assert r["bias_ok"] or r["L"] == 3
+    cost = [mlmc.level_cost_model(s.cfg, l) for l in range(r["L"] + 1)]
+    a, b, g = omlmc.rates(means, var, cost, first_level=1)
+    assert r["alpha"] == pytest.approx(a, rel=1e-10)
+    assert r["beta"] == pytest.approx(b, rel=1e-10)
+    assert r["gamma_d"] == pytest.approx(g, rel=1e-10)
+    bias, ok = omlmc.bias_test(means, max(a, 0.5), eps)
+    assert r["bias_est"] == pytest.approx(bias, rel=1e-10) and r["bias_ok"] == ok
+    assert r["estimate"] == pytest.approx(sum(means), rel=1e-13)
+    assert r["variance"] <= 1.5 * 0.5 * eps * eps
+    assert all(p["failed"] == 0 for p in r["levels"])
+    s.close()

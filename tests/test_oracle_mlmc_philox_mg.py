@@ -205,3 +205,39 @@ def test_vcycle_iteration_converges_and_bicgstab_matches_direct(level):
     xd = spla.spsolve((J / s).tocsc(), b.ravel()).reshape(b.shape)
     assert np.linalg.norm(b - mg.apply(A, xk)) <= 1e-10 * r0
     np.testing.assert_allclose(xk, xd, rtol=0, atol=1e-7 * np.abs(xd).max())
+
+
+def test_rates_recover_exact_geometric_sequences():
+    """Theorem (costMLMC) rates from per-level statistics: exact power laws
+    give exact slopes; level 0 (Y_0 = g_0, not a difference) lies off the
+    line and must be excluded by first_level; two levels give the log2 ratio."""
+    lev = np.arange(6)
+    mean = 0.3 * 2.0 ** (-1.0 * lev) * (-1.0) ** lev
+    mean[0] = 0.47                      # E[g_0]: not on the weak-error line
+    V = 7e-4 * 2.0 ** (-2.0 * lev)
+    V[0] = 0.03
+    s = 1.5 * 8.0 ** lev
+    a, b, g = mlmc.rates(mean, V, s, first_level=1)
+    assert a == pytest.approx(1.0, rel=1e-12)
+    assert b == pytest.approx(2.0, rel=1e-12)
+    assert g == pytest.approx(3.0, rel=1e-12)
+    a0, b0, _ = mlmc.rates(mean, V, s, first_level=0)
+    assert abs(a0 - 1.0) > 0.05 and abs(b0 - 2.0) > 0.05
+    a2, b2, g2 = mlmc.rates([9.0, 0.2, 0.05], [9.0, 0.1, 0.02], [1.0, 3.0, 20.0], first_level=1)
+    assert a2 == pytest.approx(math.log2(0.2 / 0.05), rel=1e-12)
+    assert b2 == pytest.approx(math.log2(0.1 / 0.02), rel=1e-12)
+    assert g2 == pytest.approx(math.log2(20.0 / 3.0), rel=1e-12)
+
+
+def test_bias_test_is_the_geometric_tail():
+    """With E[Y_l] = c 2^(-alpha l) exactly, the bias of the level-L estimator
+    is sum_{l > L} E[Y_l]; the test's estimate must equal that sum."""
+    c, L = 0.01, 4
+    for alpha in (0.5, 1.0, 2.0):
+        means = [c * 2.0 ** (-alpha * l) for l in range(L + 1)]
+        tail = sum(c * 2.0 ** (-alpha * l) for l in range(L + 1, 400))
+        b, ok = mlmc.bias_test(means, alpha, 1.0)
+        assert b == pytest.approx(tail, rel=1e-12)
+        assert ok
+        assert mlmc.bias_test(means, alpha, math.sqrt(2.0) * tail * 0.999)[1] is False
+        assert mlmc.bias_test(means, alpha, math.sqrt(2.0) * tail * 1.001)[1] is True
