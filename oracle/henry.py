@@ -55,6 +55,7 @@ data by given functions; the manufactured-solution convergence test uses
 this, the Henry solve never does.
 """
 from dataclasses import dataclass, field, replace
+import cmath
 import math
 
 import numpy as np
@@ -124,15 +125,26 @@ class Coeffs:
     qin: float
 
 
+def _exp(v):
+    """exp of a real (libm) or complex (cmath) scalar: the coefficient models
+    also accept complex inputs, for complex-step derivatives in the adjoint
+    checks; real inputs take the same path as before."""
+    return cmath.exp(v) if isinstance(v, complex) else math.exp(float(v))
+
+
+def _scalar(v):
+    return complex(v) if np.iscomplexobj(v) else float(v)
+
+
 def coefficients(prm: Params, grid: Grid, xi) -> Coeffs:
     """Three-parameter random model of the solved configuration:
     phi = phi_mean (1 + phi_amp xi1), K = K_mean exp(logK_amp xi2),
     q_in = qin_mean (1 + qin_amp xi3), xi_i iid U[-1, 1] (the paper's model of
     Sec. 4 is a two-layer porosity field with Kozeny-Carman K; the configuration
     replaces it by these independent factors)."""
-    xi1, xi2, xi3 = float(xi[0]), float(xi[1]), float(xi[2])
+    xi1, xi2, xi3 = _scalar(xi[0]), _scalar(xi[1]), _scalar(xi[2])
     phi = prm.phi_mean * (1.0 + prm.phi_amp * xi1)
-    K = prm.K_mean * math.exp(prm.logK_amp * xi2)
+    K = prm.K_mean * _exp(prm.logK_amp * xi2)
     qin = prm.qin_mean * (1.0 + prm.qin_amp * xi3)
     shape = (grid.ny, grid.nx)
     return Coeffs(phi=np.full(shape, phi), K=np.full(shape, K), qin=qin)
@@ -212,7 +224,8 @@ def residual(prm, grid, coef, p, c, p_old, c_old, src=None, bc=None):
     rhof = 0.5 * (rho[:, :-1] + rho[:, 1:])
     q = -(Kf / prm.mu) * (p[:, 1:] - p[:, :-1]) / h
     F = rhof * q * h
-    cup = np.where(F >= 0.0, c[:, :-1], c[:, 1:])
+    # upwind switches compare real parts (complex inputs: complex-step derivatives)
+    cup = np.where(np.real(F) >= 0.0, c[:, :-1], c[:, 1:])
     G = F * cup - rhof * PDf * (c[:, 1:] - c[:, :-1])
     Rm[:, :-1] += F
     Rm[:, 1:] -= F
@@ -225,7 +238,7 @@ def residual(prm, grid, coef, p, c, p_old, c_old, src=None, bc=None):
     rhof = 0.5 * (rho[:-1, :] + rho[1:, :])
     q = -(Kf / prm.mu) * ((p[1:, :] - p[:-1, :]) / h + rhof * prm.g)
     F = rhof * q * h
-    cup = np.where(F >= 0.0, c[:-1, :], c[1:, :])
+    cup = np.where(np.real(F) >= 0.0, c[:-1, :], c[1:, :])
     G = F * cup - rhof * PDf * (c[1:, :] - c[:-1, :])
     Rm[:-1, :] += F
     Rm[1:, :] -= F
@@ -244,7 +257,7 @@ def residual(prm, grid, coef, p, c, p_old, c_old, src=None, bc=None):
     rhob = 0.5 * (rho[:, 0] + prm.rho0 + drho * cl)
     Rm[:, 0] += Fl
     # advective salt: inflow carries the boundary value, outflow the cell value
-    cupl = np.where(Fl >= 0.0, c[:, 0], cl)
+    cupl = np.where(np.real(Fl) >= 0.0, c[:, 0], cl)
     Rs[:, 0] += Fl * cupl - rhob * PD[:, 0] * (cl - c[:, 0]) / (0.5 * h) * h
 
     # seaside x = Lx
@@ -253,7 +266,7 @@ def residual(prm, grid, coef, p, c, p_old, c_old, src=None, bc=None):
     rhob = 0.5 * (rho[:, -1] + prm.rho0 + drho * cr)
     q = -(K[:, -1] / prm.mu) * (pr - p[:, -1]) / (0.5 * h)
     Fr = rhob * q * h
-    cupr = np.where(Fr >= 0.0, c[:, -1], cr)
+    cupr = np.where(np.real(Fr) >= 0.0, c[:, -1], cr)
     Rm[:, -1] += Fr
     Rs[:, -1] += Fr * cupr - rhob * PD[:, -1] * (cr - c[:, -1]) / (0.5 * h) * h
 
@@ -427,10 +440,10 @@ def qoi(prm, grid, coef, p, c):
     metre of depth) and c at (1.5, 0.25), the mean of the four cells meeting at
     that vertex (the configuration's point; the paper's points are Eq. 12points)."""
     rho = prm.rho0 + (prm.rho1 - prm.rho0) * c
-    mass = float(np.sum(coef.phi * rho * c) * grid.h * grid.h)
+    mass = _scalar(np.sum(coef.phi * rho * c) * grid.h * grid.h)
     ix = int(round(1.5 / grid.h))
     iy = int(round(0.25 / grid.h))
-    cpt = float(0.25 * (c[iy - 1, ix - 1] + c[iy - 1, ix] + c[iy, ix - 1] + c[iy, ix]))
+    cpt = _scalar(0.25 * (c[iy - 1, ix - 1] + c[iy - 1, ix] + c[iy, ix - 1] + c[iy, ix]))
     return mass, cpt
 
 

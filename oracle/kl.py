@@ -124,7 +124,7 @@ def coefficients_kl(prm, grid, inp, basis=None, sigma_logK=0.5, sigma_phi=0.1, p
     from .henry import Coeffs
     basis = basis or default_basis(prm.Lx, prm.Ly)
     n = len(basis.pairs)
-    inp = np.asarray(inp, dtype=np.float64)
+    inp = np.asarray(inp, dtype=complex if np.iscomplexobj(inp) else np.float64)
     xc = (np.arange(grid.nx) + 0.5) * grid.h
     yc = (np.arange(grid.ny) + 0.5) * grid.h
     M = basis.modes(xc, yc)
@@ -132,6 +132,10 @@ def coefficients_kl(prm, grid, inp, basis=None, sigma_logK=0.5, sigma_phi=0.1, p
     gK = np.tensordot(sl * inp[:n], M, axes=1)
     gphi = np.tensordot(sl * inp[n:2 * n], M, axes=1)
     K = prm.K_mean * np.exp(sigma_logK * gK)
-    phi = np.clip(prm.phi_mean + sigma_phi * gphi, phi_lo, phi_hi)
+    phi = prm.phi_mean + sigma_phi * gphi
+    if np.iscomplexobj(phi):  # complex-step derivatives: clip on the real part (derivative 0 when clipped)
+        phi = np.where(phi.real < phi_lo, phi_lo, np.where(phi.real > phi_hi, phi_hi, phi))
+    else:
+        phi = np.clip(phi, phi_lo, phi_hi)
     qin = prm.qin_mean * (1.0 + prm.qin_amp * inp[2 * n])
     return Coeffs(phi=phi, K=K, qin=qin)
