@@ -124,6 +124,8 @@ typedef struct {
                         Jacobian without density derivatives; 0 keeps the failed iterate */
   int32_t finalize_nct; /* BiCGStab dot products of samples with >= this many 256-cell blocks are reduced
                            once per sample by a separate kernel (default 512; 0: never); same values */
+  double adj_rtol;   /* henry_adjoint: relative residual of each adjoint solve J^T lam = rhs (default 1e-10) */
+  int32_t adj_maxit; /* henry_adjoint: BiCGStab iteration cap of each adjoint solve (default 200) */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -188,6 +190,27 @@ int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const d
 int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, int with_coarse,
                             const double* xi_dev, double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev,
                             henry_stats* stats_host, void* stream);
+
+/* Discrete adjoint (dQ/dtheta of the implicit-Euler solve of Sec. 2.3; the
+ * gradients the paper's future work on parameter identification needs,
+ * Sec. 5).  For each of the n samples, inputs xi_dev[n][n_xi] as in
+ * henry_level_batch_solve and weights qoi_weights_dev[n][2], Q = w0 salt mass +
+ * w1 c(1.5, 0.25) at T; writes grad_dev[n][n_xi] = dQ/dxi (three-parameter
+ * and two-layer models: d/d(xi1, xi2, xi3); KL: d/d(theta_K[terms],
+ * theta_phi[terms], xi3)), qoi_dev[n][2] (the forward QoIs, the same values as
+ * henry_level_batch_solve) and status_dev[n] (HENRY_SAMPLE_*; 2: an adjoint
+ * solve did not converge).  Always computed in FP64, whatever `precision`.
+ * The forward keeps the state pair every checkpoint_every steps (>= 1; values
+ * above the step count keep every state) and recomputes each segment's states
+ * in the backward sweep; each step's adjoint system J_m^T lam_m = rhs is solved
+ * by BiCGStab preconditioned by the V-cycle of the transposed hierarchy, to
+ * adj_rtol.  Device workspace: the level's FP64 group plus (2 ceil(steps /
+ * checkpoint_every) + checkpoint_every + 1) x 16 B + 64 B per cell and sample,
+ * within workspace_bytes (larger batches are chunked).  Synchronises `stream`.
+ * Errors: EINVAL (NULL pointer, n <= 0, level out of range, checkpoint_every <=
+ * 0), ENOMEM, ECUDA, ENOCONV (>= 1 sample failed; see status_dev). */
+int henry_adjoint(henry_handle* h, int level, const double* xi_dev, int n, const double* qoi_weights_dev,
+                  double* grad_dev, double* qoi_dev, int checkpoint_every, int32_t* status_dev, void* stream);
 
 /* a12. Merge one batch of level-`level` samples into running MLMC sums.
  * Y = qoi_fine - qoi_coarse (qoi_coarse_dev NULL: Y = qoi_fine, level 0), the

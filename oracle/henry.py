@@ -163,7 +163,7 @@ def coefficients_two_layer(prm: Params, grid: Grid, xi) -> Coeffs:
     y in [-1, 0]: y_paper = y - Ly here), K = K(phi) by Kozeny-Carman, and the
     recharge q_in = qin_mean (1 + qin_amp xi3) (Sec. 4; xi2 appears twice and
     xi3 only in the recharge, as printed)."""
-    xi1, xi2, xi3 = float(xi[0]), float(xi[1]), float(xi[2])
+    xi1, xi2, xi3 = _scalar(xi[0]), _scalar(xi[1]), _scalar(xi[2])
     x = (np.arange(grid.nx) + 0.5) * grid.h
     yp = (np.arange(grid.ny) + 0.5) * grid.h - prm.Ly
     X, Y = np.meshgrid(x, yp)

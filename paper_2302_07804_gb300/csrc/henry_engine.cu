@@ -31,6 +31,7 @@
 #include "henry_misc.cuh"
 #include "henry_cta.cuh"
 #include "henry_kl.cuh"
+#include "henry_adjoint.cuh"
 
 using namespace hk;
 
@@ -223,6 +224,9 @@ struct henry_handle {
   cudaEvent_t ev_fork = nullptr;
   char* perm_mem = nullptr;
   int perm_cap = 0;
+  // henry_adjoint: checkpoints, one segment of states, right-hand side and sensitivity sums
+  char* adj_mem = nullptr;
+  size_t adj_bytes = 0;
 };
 
 namespace {
@@ -617,9 +621,11 @@ int read_counter(henry_handle* H, const int* dev, cudaStream_t st, int* out) {
 }
 
 // BiCGStab on the fine level for the samples with lin_active set; right-hand
-// side -F; solution in G.dx.
+// side -F; solution in G.dx.  rtol / maxit > 0 override the configuration's
+// lin_rtol / lin_maxit.
 template <typename T>
-int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const void* Jpre0 = nullptr) {
+int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const void* Jpre0 = nullptr,
+                 double rtol = -1.0, int maxit = -1) {
   typedef typename VT<T>::v2 V2;
   typedef typename VT<T>::b4 B4;
   Level& L = G.lv[0];
@@ -639,11 +645,13 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
            [&] { k_finalize<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, G.part, a, b, fin); });
   };
   finalize(P_RR, P_RN);
-  const double rtol2 = H->cfg.lin_rtol * H->cfg.lin_rtol;
-  for (int it = 0; it <= H->cfg.lin_maxit; ++it) {
+  const double rt = rtol > 0.0 ? rtol : H->cfg.lin_rtol;
+  const int mi = maxit > 0 ? maxit : H->cfg.lin_maxit;
+  const double rtol2 = rt * rt;
+  for (int it = 0; it <= mi; ++it) {
     CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
     launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (it == 0 ? 2 : 4) * v2, [&] {
-      k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, H->cfg.lin_maxit, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
+      k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, mi, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active,
                                       G.iters, G.status, G.counter + 1, G.totals + 1, fin);
     });
     CKL();
@@ -708,9 +716,12 @@ int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, doub
   return linear_solve<T>(H, G, B, st, G.Jp);
 }
 
-// Full scenario solves of B samples whose coefficients and status are set.
+// One implicit-Euler step (Sec. 2.3) of the B samples of a group: the
+// state x^n in lv[0].x (and x^{n-1} in lv[0].xo, for the predictor) becomes
+// x^{n+1}, with Newton iterations as described at the top of this file.
+// `step` is the step's index (the predictor is used from step 1 on).
 template <typename T>
-int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t st) {
+int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st) {
   typedef typename VT<T>::b4 B4;
   typedef typename VT<T>::v2 V2;
   const henry_config& c = H->cfg;
@@ -723,69 +734,81 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   const double inv_pref = 1.0 / (c.rho0 * c.g * c.Ly);
   double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
+  H->nact = B;
+  launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
+    if (step > 0 && c.newton_predictor > 0.0)
+      k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
+    else
+      k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
+  });
+  CKL();
+  int rc = restrict_states<T>(H, G, B, true, G.newton_active, st);
+  if (rc) return rc;
+  for (int it = 0; it <= c.newton_maxit; ++it) {
+    CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
+    launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
+      if (L.cc)
+        k_assemble<T, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                             lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                             G.newton_active, G.F, (B4*)L.J, L.plane, pmax, L.cc,
+                                                             L.fc);
+      else
+        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                       lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
+    });
+    launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
+      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+                                                       G.newton_active, G.lin_active, G.newton_it, G.status,
+                                                       G.counter, G.totals);
+    });
+    CKL();
+    int n_act = 0;
+    rc = read_counter(H, G.counter, st, &n_act);
+    if (rc) return rc;
+    if (n_act == 0) break;
+    H->nact = n_act;
+    if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
+      rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
+      if (rc) return rc;
+    }
+    rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
+    if (rc) return rc;
+    rc = linear_solve<T>(H, G, B, st);
+    if (rc) return rc;
+    if (G.Jp && c.lin_retry) {  // fallback preconditioner for the samples whose solve failed
+      rc = retry_linear_solve<T>(H, G, B, inv_tau, inv_s, st);
+      if (rc) return rc;
+    }
+    H->nact = n_act;
+    launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
+      double* pdc = G.part + P_DC * (int64_t)B * G.nct;
+      k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
+      k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
+      k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
+      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
+    });
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// Full scenario solves of B samples whose coefficients and status are set.
+template <typename T>
+int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  Level& L = G.lv[0];
+  const int64_t n0 = (int64_t)B * L.N;
   CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
   H->nact = B;
   launch(H, st, HENRY_K_QOI, (double)n0 * 16,
          [&] { k_init_state<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0 * c.g, c.Ly, L.x); });
   CKL();
   for (int step = 0; step < lg.steps; ++step) {
-    H->nact = B;
-    launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
-      if (step > 0 && c.newton_predictor > 0.0)
-        k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
-      else
-        k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
-      k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
-    });
-    CKL();
-    int rc = restrict_states<T>(H, G, B, true, G.newton_active, st);
+    const int rc = implicit_step<T>(H, G, B, step, st);
     if (rc) return rc;
-    for (int it = 0; it <= c.newton_maxit; ++it) {
-      CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
-      launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
-        if (L.cc)
-          k_assemble<T, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                               lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                               G.newton_active, G.F, (B4*)L.J, L.plane, pmax, L.cc,
-                                                               L.fc);
-        else
-          k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                         lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                         G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
-      });
-      launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
-        k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
-                                                         G.newton_active, G.lin_active, G.newton_it, G.status,
-                                                         G.counter, G.totals);
-      });
-      CKL();
-      int n_act = 0;
-      rc = read_counter(H, G.counter, st, &n_act);
-      if (rc) return rc;
-      if (n_act == 0) break;
-      H->nact = n_act;
-      if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
-        rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
-        if (rc) return rc;
-      }
-      rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
-      if (rc) return rc;
-      rc = linear_solve<T>(H, G, B, st);
-      if (rc) return rc;
-      if (G.Jp && c.lin_retry) {  // fallback preconditioner for the samples whose solve failed
-        rc = retry_linear_solve<T>(H, G, B, inv_tau, inv_s, st);
-        if (rc) return rc;
-      }
-      H->nact = n_act;
-      launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
-        double* pdc = G.part + P_DC * (int64_t)B * G.nct;
-        k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
-        k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
-        k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
-        k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
-      });
-      CKL();
-    }
   }
   launch(H, st, HENRY_K_QOI, (double)n0 * 16, [&] {
     k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc);
@@ -917,6 +940,191 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
 }
 
 bool valid_level(henry_handle* h, int level) { return h && level >= 0 && level <= h->cfg.max_level; }
+// ---------------------------------------------------------------------------
+// Discrete adjoint (henry_adjoint).  The forward solve keeps the state pair
+// (x_n, x_{n-1}) every `ckpt` steps and the states of the last segment; the
+// backward sweep visits the segments from the last, recomputes each
+// segment's states from its checkpoint pair (the same kernels and inputs, so
+// the same states), and for every step from the last to the first assembles
+// the Jacobian at (x_m, x_{m-1}), builds the coarse operators, transposes the
+// whole multigrid hierarchy in place, solves J_m^T lam_m = rhs with the same
+// BiCGStab and V-cycle, and accumulates the sensitivities (henry_adjoint.cuh).
+size_t adjoint_bytes_per_sample(const henry_config& c, int level, int ckpt) {
+  const LevelGeom lg = geom(c, level);
+  const size_t N = (size_t)lg.nx * lg.ny;
+  const size_t nck = (size_t)((lg.steps + ckpt - 1) / ckpt);
+  return (2 * nck + (size_t)ckpt + 1) * N * sizeof(double2) + (size_t)A_NPLANE * N * sizeof(double);
+}
+
+int ensure_adj_mem(henry_handle* H, size_t bytes) {
+  if (H->adj_bytes >= bytes) return HENRY_OK;
+  if (H->adj_mem) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaFree(H->adj_mem));
+    H->adj_mem = nullptr;
+    H->adj_bytes = 0;
+  }
+  if (cudaMalloc(&H->adj_mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    H->adj_mem = nullptr;
+    return set_err(HENRY_ENOMEM, "cudaMalloc of %zu bytes for the adjoint's checkpoints failed", bytes);
+  }
+  H->adj_bytes = bytes;
+  return HENRY_OK;
+}
+
+int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, const double* w, double* grad,
+                  double* qoi, int C, cudaStream_t st) {
+  typedef VT<double>::b4 B4;
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  const Phys ph = phys_of(c);
+  Level& L = G.lv[0];
+  const int N = L.N;
+  const int64_t n0 = (int64_t)B * N;
+  const size_t vbytes = sizeof(double2) * (size_t)n0;
+  const double inv_tau = 1.0 / lg.tau;
+  const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
+  const double vt = lg.h * lg.h * inv_tau * inv_s;
+  const int steps = lg.steps;
+  const int nck = (steps + C - 1) / C;
+  Carver cv{H->adj_mem, 0};
+  double2* ck = cv.take<double2>(vbytes * 2 * nck);  // [nck][x_n, x_{n-1}][B N]
+  double2* seg = cv.take<double2>(vbytes * C);       // [C][B N]: states of one segment
+  double2* rhs = cv.take<double2>(vbytes);
+  double* S = cv.take<double>(sizeof(double) * A_NPLANE * (size_t)n0);
+  double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
+  // forward, with checkpoints
+  CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
+  H->nact = B;
+  k_init_state<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0 * c.g, c.Ly, L.x);
+  CKL();
+  CK(cudaMemcpyAsync(L.xo, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
+  for (int step = 0; step < steps; ++step) {
+    if (step % C == 0) {
+      CK(cudaMemcpyAsync(ck + (int64_t)(2 * (step / C)) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ck + (int64_t)(2 * (step / C) + 1) * n0, L.xo, vbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    int rc = implicit_step<double>(H, G, B, step, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(seg + (int64_t)(step % C) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
+  }
+  k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc);
+  CKL();
+  // backward
+  k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.lin_active, G.newton_it);
+  k_adj_start<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.cc, w, L.x, rhs, S,
+                                         G.lin_active);
+  CKL();
+  for (int k = nck - 1; k >= 0; --k) {
+    const int s0 = k * C, s1 = std::min(s0 + C, steps);
+    if (k != nck - 1) {  // recompute the segment's states from its checkpoint pair
+      CK(cudaMemcpyAsync(L.x, ck + (int64_t)(2 * k) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(L.xo, ck + (int64_t)(2 * k + 1) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
+      for (int step = s0; step < s1; ++step) {
+        int rc = implicit_step<double>(H, G, B, step, st);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(seg + (int64_t)(step - s0) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    for (int step = s1 - 1; step >= s0; --step) {  // state m = step + 1
+      const double2* xm = seg + (int64_t)(step - s0) * n0;
+      const double2* xm1 = step == s0 ? ck + (int64_t)(2 * k) * n0 : seg + (int64_t)(step - s0 - 1) * n0;
+      CK(cudaMemcpyAsync(L.x, xm, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(L.xo, xm1, vbytes, cudaMemcpyDeviceToDevice, st));
+      k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.lin_active, G.newton_it);
+      CKL();
+      H->nact = B;
+      launch(H, st, HENRY_K_ASSEMBLE, (double)n0 * (48.0 + 6.0 * sizeof(B4)), [&] {
+        if (L.cc)
+          k_assemble<double, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt,
+                                                                  inv_s, L.x, L.xo, G.lin_active, G.F, (B4*)L.J,
+                                                                  L.plane, pmax, L.cc, L.fc);
+        else
+          k_assemble<double, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s,
+                                                            L.x, L.xo, G.lin_active, G.F, (B4*)L.J, L.plane, pmax);
+      });
+      CKL();
+      int rc;
+      if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
+        rc = restrict_states<double>(H, G, B, true, G.lin_active, st);
+        if (rc) return rc;
+        rc = restrict_states<double>(H, G, B, false, G.lin_active, st);
+        if (rc) return rc;
+      }
+      rc = build_coarse_ops<double>(H, G, B, inv_tau, inv_s, st);
+      if (rc) return rc;
+      for (int kk = 0; kk <= G.K; ++kk) {
+        Level& Lk = G.lv[kk];
+        k_transpose_blocks<double><<<nblk((int64_t)B * Lk.N), TPB, 0, st>>>(B, Lk.nx, Lk.ny, (B4*)Lk.J, Lk.plane,
+                                                                            G.lin_active);
+      }
+      Level& Lc = G.lv[G.K];
+      k_coarse_inverse<double><<<nblk(B, 64), 64, 0, st>>>(B, (const B4*)Lc.J, Lc.plane, G.Ainv, G.lin_active);
+      k_adj_neg<<<nblk(n0), TPB, 0, st>>>(n0, rhs, G.F);
+      CKL();
+      rc = linear_solve<double>(H, G, B, st, nullptr, c.adj_rtol, c.adj_maxit);
+      if (rc) return rc;
+      k_adj_lin_status<<<nblk(B, 128), 128, 0, st>>>(B, G.iters, G.status, G.lin_active);
+      k_adj_step<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.dx,
+                                          L.cc, S, rhs, G.lin_active);
+      CKL();
+    }
+  }
+  k_adj_cell_grad<<<nblk(n0), TPB, 0, st>>>(B, L.nx, L.ny, c.mu, c.Dm, G.coef, L.cc, S, G.r, G.lin_active);
+  CKL();
+  AdjModel M;
+  std::memset(&M, 0, sizeof M);
+  M.model = c.coef_model == HENRY_MODEL_KL ? 1 : (c.coef_model == HENRY_MODEL_TWO_LAYER ? 2 : 0);
+  M.n_in = n_inputs(c);
+  M.terms = c.kl_terms;
+  M.phi_mean = c.phi_mean; M.phi_amp = c.phi_amp; M.K_mean = c.K_mean; M.logK_amp = c.logK_amp;
+  M.qin_mean = c.qin_mean; M.qin_amp = c.qin_amp; M.mu = c.mu;
+  M.sigma_logK = c.kl_sigma_logK; M.sigma_phi = c.kl_sigma_phi; M.phi_lo = c.phi_lo; M.phi_hi = c.phi_hi;
+  M.kappa = c.K_mean * (1.0 - c.phi_mean * c.phi_mean) / (c.phi_mean * c.phi_mean * c.phi_mean);
+  M.Ly = c.Ly; M.y_if = -0.75; M.h = lg.h;
+  const int *ti = nullptr, *tj = nullptr;
+  const double *sl = nullptr, *psx = nullptr, *psy = nullptr;
+  if (M.model == 1) {
+    KLTables* t = nullptr;
+    int rc = ensure_kl_tables(H, G.level, &t);
+    if (rc) return rc;
+    ti = t->ti; tj = t->tj; sl = t->sl; psx = t->psx; psy = t->psy;
+  }
+  k_adj_project<<<B, TPB, 0, st>>>(M, B, L.nx, L.ny, G.coef, L.cc, G.r, S, ti, tj, sl, psx, psy, xi, grad,
+                                   G.lin_active);
+  CKL();
+  return HENRY_OK;
+}
+
+int adjoint_level(henry_handle* H, int level, const double* xi, int n, const double* w, double* grad, double* qoi,
+                  int ckpt, int32_t* status, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, level);
+  const int C = std::max(1, std::min(ckpt, lg.steps));
+  const double per = (double)bytes_per_sample<double>(c, level, false) + (double)adjoint_bytes_per_sample(c, level, C);
+  const int Bmax = (int)std::max(1.0, std::min(std::floor(c.workspace_bytes / per), 1.0e6));
+  const int Bcap = std::min(Bmax, n);
+  const int nin = n_inputs(c);
+  int rc = ensure_adj_mem(H, adjoint_bytes_per_sample(c, level, C) * (size_t)Bcap + 8 * 256);
+  if (rc) return rc;
+  for (int off = 0; off < n; off += Bmax) {
+    const int B = std::min(Bmax, n - off);
+    Group<double>* G = nullptr;
+    rc = get_group<double>(H, level, Bcap, &G);
+    if (rc) return rc;
+    rc = set_coefficients<double>(H, *G, xi + (int64_t)nin * off, B, st);
+    if (rc) return rc;
+    rc = adjoint_group(H, *G, B, xi + (int64_t)nin * off, w + 2 * (int64_t)off, grad + (int64_t)nin * off,
+                       qoi + 2 * (int64_t)off, C, st);
+    if (rc) return rc;
+    k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, 1);
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+
 
 template <typename T>
 int step_entry(henry_handle* H, int which, int level, const double* xi, int n, const double* state,
@@ -999,6 +1207,8 @@ void henry_default_config(henry_config* c) {
   c->newton_dc_limit = 1.0;
   c->lin_retry = 1;
   c->finalize_nct = 512;
+  c->adj_rtol = 1e-10;
+  c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
   c->kl_terms = 32;
@@ -1046,6 +1256,7 @@ void henry_destroy(henry_handle* h) {
   for (auto& kv : h->kid_streams) cudaStreamDestroy(kv.second);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->perm_mem) cudaFree(h->perm_mem);
+  if (h->adj_mem) cudaFree(h->adj_mem);
   for (auto& p : h->prof.pend) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -1308,6 +1519,27 @@ int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const d
     *stats_host = local;
   }
   if (failed) return set_err(HENRY_ENOCONV, "%lld of %d samples did not converge", (long long)failed, n);
+  return HENRY_OK;
+}
+
+int henry_adjoint(henry_handle* h, int level, const double* xi_dev, int n, const double* qoi_weights_dev,
+                  double* grad_dev, double* qoi_dev, int checkpoint_every, int32_t* status_dev, void* stream) {
+  if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
+  if (!xi_dev || !qoi_weights_dev || !grad_dev || !qoi_dev || !status_dev)
+    return set_err(HENRY_EINVAL, "NULL device pointer");
+  if (checkpoint_every <= 0) return set_err(HENRY_EINVAL, "checkpoint_every = %d must be positive", checkpoint_every);
+  if (!(h->cfg.adj_rtol > 0.0) || h->cfg.adj_maxit <= 0) return set_err(HENRY_EINVAL, "bad adj_rtol / adj_maxit");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = adjoint_level(h, level, xi_dev, n, qoi_weights_dev, grad_dev, qoi_dev, checkpoint_every, status_dev, st);
+  if (rc) return rc;
+  std::vector<int32_t> hs(n);
+  CK(cudaMemcpyAsync(hs.data(), status_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int64_t failed = 0;
+  for (int i = 0; i < n; ++i) failed += hs[i] != 0;
+  if (failed) return set_err(HENRY_ENOCONV, "%lld of %d samples failed (status_dev)", (long long)failed, n);
   return HENRY_OK;
 }
 

@@ -24,7 +24,7 @@ N_XI = 3
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
-           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test")
+           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused")
 
@@ -40,7 +40,8 @@ class HenryConfig(ctypes.Structure):
                 ("newton_dc_limit", ctypes.c_double),
                 ("fused_small_grids", ctypes.c_int32), ("coef_model", ctypes.c_int32), ("kl_terms", ctypes.c_int32)] + \
                [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")] + \
-               [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32)]
+               [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32), ("adj_rtol", ctypes.c_double),
+                ("adj_maxit", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -78,6 +79,7 @@ def lib():
         L.henry_last_error.restype = ctypes.c_char_p
         L.henry_sample_xi.argtypes = [U64, I, U64, I, P, P]
         L.henry_level_batch_solve.argtypes = [P, I, I, P, I, P, P, P, ctypes.POINTER(HenryStats), P]
+        L.henry_adjoint.argtypes = [P, I, P, I, P, P, P, I, P, P]
         L.henry_batch_solve_mixed.argtypes = [P, P, I, I, P, P, P, P, ctypes.POINTER(HenryStats), P]
         L.mlmc_accumulate.argtypes = [I, I, I, P, P, P, P, P]
         L.mlmc_allocate.argtypes = [I, ctypes.POINTER(D), ctypes.POINTER(D), D, ctypes.POINTER(I64)]
@@ -280,6 +282,20 @@ class Solver:
         _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
         return qf, qc, st, stats.as_dict()
 
+    def adjoint(self, level, xi, weights, checkpoint_every=20, stream=None, allow_failures=False):
+        """dQ/dxi for Q = weights[:, 0] mass + weights[:, 1] c_point (henry_adjoint).
+        Returns (grad[n][n_xi], qoi[n][2], status[n] int32)."""
+        n = xi.shape[0]
+        _dev_f64(xi, (n, self.n_xi))
+        _dev_f64(weights, (n, N_QOI))
+        grad = torch.empty((n, self.n_xi), dtype=torch.float64, device=xi.device)
+        qoi = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
+        st = torch.empty((n,), dtype=torch.int32, device=xi.device)
+        rc = lib().henry_adjoint(self._h, level, _ptr(xi), n, _ptr(weights), _ptr(grad), _ptr(qoi),
+                                 int(checkpoint_every), _ptr(st), _stream(stream))
+        _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
+        return grad, qoi, st
+
     def _states(self, level, state, state_old):
         ny, nx = self.grid(level)
         n = state.shape[0]
@@ -319,3 +335,32 @@ class Solver:
         _check(lib().henry_linear_solve(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),
                                         _ptr(x), _ptr(its), _stream(stream)))
         return x, its
+
+
+class _ScenarioQoI(torch.autograd.Function):
+    """qoi[n][2] = solve(xi) with the discrete adjoint as its backward: the
+    forward is henry_level_batch_solve; backward calls henry_adjoint with the
+    incoming gradient as the QoI weights (the adjoint recomputes the forward
+    with checkpoints)."""
+
+    @staticmethod
+    def forward(ctx, xi, solver, level, checkpoint_every):
+        qf, _, st, _ = solver.level_batch_solve(level, xi.detach().contiguous(), allow_failures=True)
+        ctx.solver, ctx.level, ctx.ckpt = solver, level, checkpoint_every
+        ctx.save_for_backward(xi)
+        ctx.status = st
+        return qf
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (xi,) = ctx.saved_tensors
+        grad, _, _ = ctx.solver.adjoint(ctx.level, xi.detach().contiguous(), grad_out.contiguous(),
+                                        checkpoint_every=ctx.ckpt, allow_failures=True)
+        return grad, None, None, None
+
+
+def scenario_qoi(solver, level, xi, checkpoint_every=20):
+    """Differentiable QoIs of a batch of scenarios (torch.autograd): qoi[n][2]
+    at MLMC level ``level`` for inputs xi[n][n_xi]; backward through
+    henry_adjoint."""
+    return _ScenarioQoI.apply(xi, solver, level, checkpoint_every)

@@ -3,7 +3,8 @@
 * Central differences of the full forward solve (Newton tightened to 1e-13 so
   that the differences resolve 1e-8): all three xi of the three-parameter
   model and six of the 65 inputs of the KL model (log K and phi coefficients,
-  and xi3 of the recharge), at level 0.
+  and xi3 of the recharge), and the two-layer model's three inputs, at
+  level 0.
 * The two structural facts the adjoint recursion relies on: the residual of
   a cell depends on the old state only through that cell's mass fraction
   (a cell-local, diagonal coupling), and not on the old pressure; the QoIs do
@@ -40,6 +41,14 @@ def test_adjoint_matches_central_differences_kl():
     which = [0, 5, 31, 32, 40, 64]
     fd = adjoint.finite_difference_gradient(PRM, 0, th, W, model="kl", delta=1e-5, which=which)
     np.testing.assert_allclose(g[which], fd, rtol=0, atol=1e-8 * np.abs(g).max())
+
+
+def test_adjoint_matches_central_differences_two_layer():
+    xi = np.array([0.3, -0.4, 0.2])
+    g, q, ok = adjoint.adjoint_gradient(PRM, 0, xi, W, model="two_layer")
+    assert ok
+    fd = adjoint.finite_difference_gradient(PRM, 0, xi, W, model="two_layer", delta=1e-5)
+    np.testing.assert_allclose(g, fd, rtol=0, atol=1e-8 * np.abs(g).max())
 
 
 def test_old_state_coupling_is_cell_local_and_pressure_free():
