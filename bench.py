@@ -351,6 +351,7 @@ def run_uneven(args):
     counts = list(UNEVEN_COUNTS)
     cfg = henry.default_config()
     kw = {"coef_model": henry.HENRY_MODEL_KL} if kl else {}
+    kw.update(config_overrides(args))
     prec = henry.HENRY_MIXED if kl else henry.HENRY_FP64
     gen = torch.Generator(device=dev)
     gen.manual_seed(inputs.SEED)
@@ -404,6 +405,63 @@ def run_uneven(args):
     return 0
 
 
+def config_overrides(args):
+    """--set KEY=VALUE pairs as Solver keyword arguments (int or float values)."""
+    out = {}
+    for kv in args.set:
+        k, v = kv.split("=", 1)
+        out[k] = int(v) if v.lstrip("-").isdigit() else float(v)
+    return out
+
+
+def run_adjoint(args):
+    """Discrete-adjoint workload: dQ/dtheta (64 KL coefficients + xi3) for a
+    batch of KL samples on the 256 x 128 grid with 200 implicit steps (level 3
+    with 25 steps at level 0), checkpoints every 20 steps, FP64; the value is
+    forward cell-steps per second of the whole gradient computation (forward
+    with checkpoints, recomputation and backward sweep), next to the plain
+    forward solve of the same batch."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_07804_gb300 import henry, inputs
+    dev = torch.device("cuda", 0)
+    n = args.adjoint_batch
+    kw = dict(coef_model=henry.HENRY_MODEL_KL, steps0=25, workspace_bytes=96e9)
+    kw.update(config_overrides(args))
+    s = henry.Solver(**kw)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(inputs.SEED)
+    th = torch.randn((n, 64), generator=gen, device=dev, dtype=torch.float64)
+    x3 = torch.rand((n, 1), generator=gen, device=dev, dtype=torch.float64) * 2 - 1
+    xi = torch.cat([th, x3], dim=1).contiguous()
+    w = torch.tensor([0.01, 1.0], dtype=torch.float64, device=dev).repeat(n, 1).contiguous()
+    level = 3
+    s.adjoint(level, xi[:8].contiguous(), w[:8].contiguous(), checkpoint_every=20)  # warm-up
+    torch.cuda.synchronize()
+    cs = n * (s.cfg.nx0 << level) * (s.cfg.ny0 << level) * (s.cfg.steps0 << level)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record()
+        grad, q, st = s.adjoint(level, xi, w, checkpoint_every=20, allow_failures=True)
+        e1.record()
+        torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    e0.record()
+    qf, _, st2, stats = s.level_batch_solve(level, xi, allow_failures=True)
+    e1.record()
+    torch.cuda.synchronize()
+    fsec = e0.elapsed_time(e1) / 1e3
+    line = {"workload": "adjoint-kl-256x128x200-batch%d" % n, "metric": METRIC, "value": cs / sec,
+            "unit": "cell-steps/s", "seconds": sec, "forward_seconds": fsec, "adjoint_over_forward": sec / fsec,
+            "cell_steps": cs, "checkpoint_every": 20, "failed_samples": int((st != 0).sum()),
+            "forward_qoi_equal": bool(torch.equal(q, qf)), "grad_finite": bool(torch.isfinite(grad).all()),
+            "clocks": clk.summary(), "dtype": "f64"}
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def run_case(args):
     """Profiling case: one batch of N scenarios at one level (no MLMC)."""
     import numpy as np
@@ -413,7 +471,7 @@ def run_case(args):
     from paper_2302_07804_gb300 import henry, inputs
     lev, n = (int(v) for v in args.case.split(":"))
     prec = henry.HENRY_MIXED if args.precision == "mixed" else henry.HENRY_FP64
-    s = henry.Solver(precision=prec)
+    s = henry.Solver(precision=prec, **config_overrides(args))
     xi = henry.sample_xi(inputs.SEED, lev, 0, n)
     if args.vcycle:
         # one V-cycle on a batch where every sample is active (kernel captures)
@@ -440,7 +498,7 @@ def run_case(args):
     e1.record()
     torch.cuda.synchronize()
     sec = e0.elapsed_time(e1) / 1e3
-    line = {"case": args.case, "precision": args.precision, "seconds": sec,
+    line = {"case": args.case, "precision": args.precision, "set": args.set, "seconds": sec,
             "cell_steps_per_s": stats["cell_steps"] / sec, "stats": stats}
     if args.profile:
         s.profile(True)
@@ -463,11 +521,17 @@ def main():
     ap.add_argument("--case", default=None, help="LEVEL:N profiling case (one batch solve, no MLMC)")
     ap.add_argument("--profile", action="store_true", help="with --case: also read the kernel timer")
     ap.add_argument("--vcycle", action="store_true", help="with --case: one assembly + V-cycle per call instead of a solve")
-    ap.add_argument("--workload", default="mlmc", choices=["mlmc", "uneven", "kl-mixed"],
-                    help="mlmc: the bench line; uneven / kl-mixed: 4096 scenarios over levels 0..5")
+    ap.add_argument("--workload", default="mlmc", choices=["mlmc", "uneven", "kl-mixed", "adjoint"],
+                    help="mlmc: the bench line; uneven / kl-mixed: 4096 scenarios over levels 0..5; adjoint: "
+                         "dQ/dtheta of 1024 KL samples, 256x128 cells, 200 steps")
+    ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
+                    help="with --case / uneven / kl-mixed / adjoint: override a henry_config field")
+    ap.add_argument("--adjoint-batch", type=int, default=1024)
     args = ap.parse_args()
     if args.case:
         return run_case(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.workload != "mlmc":
         return run_uneven(args)
     rank, world, local = dist_setup(args.gpus)
