@@ -126,6 +126,9 @@ typedef struct {
                            once per sample by a separate kernel (default 512; 0: never); same values */
   double adj_rtol;   /* henry_adjoint: relative residual of each adjoint solve J^T lam = rhs (default 1e-10) */
   int32_t adj_maxit; /* henry_adjoint: BiCGStab iteration cap of each adjoint solve (default 200) */
+  int32_t cuda_graphs; /* 1 (default): each BiCGStab iteration's body (two V-cycles, two matvecs, vector
+                          updates) is captured once per workspace and batch size into a CUDA graph and
+                          replayed; 0: plain launches.  Same values either way; off while profiling */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */

@@ -107,6 +107,15 @@ struct Group {
   LinScal* sc;
   T* Ainv;
   void* Jp = nullptr;  // fine-level fallback preconditioner operator (field models only)
+  // Instantiated CUDA graphs of one BiCGStab iteration's body, by (batch
+  // size, preconditioner operator); they hold this workspace's pointers and
+  // are dropped with it.
+  std::map<std::pair<int, const void*>, cudaGraphExec_t> gexec;
+  bool graphs = true;  // false: never capture (the allocation-free entry point)
+  void drop_graphs() {
+    for (auto& kv : gexec) cudaGraphExecDestroy(kv.second);
+    gexec.clear();
+  }
 
   // Lay out (or size, with base == nullptr) the workspace for B samples.
   // `light`: only what the fused small-grid solver uses (fine old state,
@@ -227,6 +236,7 @@ struct henry_handle {
   // henry_adjoint: checkpoints, one segment of states, right-hand side and sensitivity sums
   char* adj_mem = nullptr;
   size_t adj_bytes = 0;
+  cudaStream_t cap_stream = nullptr;  // CUDA-graph capture
 };
 
 namespace {
@@ -367,6 +377,7 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out, bool light = fa
   }
   if (g.mem) {
     CK(cudaDeviceSynchronize());
+    g.drop_graphs();
     CK(cudaFree(g.mem));
     g.mem = nullptr;
   }
@@ -639,15 +650,74 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
   // Large grids: reduce each sample's partials once (one warp per sample)
   // instead of in every CTA of the consumer kernel.
   double* fin = (H->cfg.finalize_nct > 0 && G.nct >= H->cfg.finalize_nct) ? G.fin : nullptr;
-  auto finalize = [&](int a, int b) {
+  auto finalize = [&](int a, int b, cudaStream_t ss) {
     if (!fin) return;
-    launch(H, st, HENRY_K_KRYLOV, (double)B * G.nct * 16.0,
-           [&] { k_finalize<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, G.part, a, b, fin); });
+    launch(H, ss, HENRY_K_KRYLOV, (double)B * G.nct * 16.0,
+           [&] { k_finalize<<<nblk((int64_t)B * 32, 128), 128, 0, ss>>>(B, G.nct, G.part, a, b, fin); });
   };
-  finalize(P_RR, P_RN);
+  finalize(P_RR, P_RN, st);
   const double rt = rtol > 0.0 ? rtol : H->cfg.lin_rtol;
   const int mi = maxit > 0 ? maxit : H->cfg.lin_maxit;
   const double rtol2 = rt * rt;
+  // One iteration after the convergence test: two preconditioned matvecs and
+  // the vector updates (every argument fixed for this group and B; the
+  // samples' activity is read from lin_active on the device).
+  auto body = [&](int n_act, cudaStream_t ss) -> int {
+    const double nc = (double)n_act * N;
+    int rc = vcycle<T>(H, G, B, G.p, G.ph, ss, Jpre0);
+    if (rc) return rc;
+    launch(H, ss, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 1), [&] {
+      k_spmv<T, 1><<<g, TPB, 0, ss>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.ph, G.v, G.rh, G.part, P_RV, 0,
+                                       G.lin_active);
+    });
+    finalize(P_RV, -1, ss);
+    launch(H, ss, HENRY_K_KRYLOV, nc * 3 * v2,
+           [&] { k_bicg_s<T><<<g, TPB, 0, ss>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active, fin); });
+    CKL();
+    rc = vcycle<T>(H, G, B, G.s, G.sh, ss, Jpre0);
+    if (rc) return rc;
+    launch(H, ss, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 2), [&] {
+      k_spmv<T, 2><<<g, TPB, 0, ss>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.sh, G.t, G.s, G.part, P_TS, P_TT,
+                                       G.lin_active);
+    });
+    finalize(P_TS, P_TT, ss);
+    launch(H, ss, HENRY_K_KRYLOV, nc * 8 * v2, [&] {
+      k_bicg_update<T><<<g, TPB, 0, ss>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active,
+                                           fin);
+    });
+    finalize(P_RR, P_RN, ss);
+    CKL();
+    return HENRY_OK;
+  };
+  // The body is captured once into a CUDA graph and replayed: one launch
+  // instead of ~80 at level 0, which matters on launch-bound groups (small
+  // grids, coarse levels).  Captured on the handle's own stream (capturing
+  // the legacy default stream is not allowed; capture executes nothing) and
+  // launched on `st`.  Off while the kernel timer runs.
+  const bool use_graph = H->cfg.cuda_graphs && G.graphs && !H->prof.on;
+  auto run_graph = [&]() -> int {
+    const auto key = std::make_pair(B, Jpre0);
+    auto f = G.gexec.find(key);
+    if (f == G.gexec.end()) {
+      if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = body(B, H->cap_stream);
+      const cudaError_t e = cudaStreamEndCapture(H->cap_stream, &gr);
+      if (rc) {
+        if (e == cudaSuccess && gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e != cudaSuccess) return set_err(HENRY_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e2 = cudaGraphInstantiate(&ex, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e2 != cudaSuccess) return set_err(HENRY_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+      f = G.gexec.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(f->second, st));
+    return HENRY_OK;
+  };
   for (int it = 0; it <= mi; ++it) {
     CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
     launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (it == 0 ? 2 : 4) * v2, [&] {
@@ -660,30 +730,8 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
     if (rc) return rc;
     if (n_act == 0) break;
     H->nact = n_act;
-    const double nc = (double)n_act * N;
-    rc = vcycle<T>(H, G, B, G.p, G.ph, st, Jpre0);
+    rc = use_graph ? run_graph() : body(n_act, st);
     if (rc) return rc;
-    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 1), [&] {
-      k_spmv<T, 1><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.ph, G.v, G.rh, G.part, P_RV, 0,
-                                       G.lin_active);
-    });
-    finalize(P_RV, -1);
-    launch(H, st, HENRY_K_KRYLOV, nc * 3 * v2,
-           [&] { k_bicg_s<T><<<g, TPB, 0, st>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active, fin); });
-    CKL();
-    rc = vcycle<T>(H, G, B, G.s, G.sh, st, Jpre0);
-    if (rc) return rc;
-    launch(H, st, HENRY_K_SPMV, nc * (5 * b4 + 3 * v2), n_act * spmv_flops(L.nx, L.ny, 2), [&] {
-      k_spmv<T, 2><<<g, TPB, 0, st>>>(B, L.nx, L.ny, (const B4*)L.J, L.plane, G.sh, G.t, G.s, G.part, P_TS, P_TT,
-                                       G.lin_active);
-    });
-    finalize(P_TS, P_TT);
-    launch(H, st, HENRY_K_KRYLOV, nc * 8 * v2, [&] {
-      k_bicg_update<T><<<g, TPB, 0, st>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active,
-                                           fin);
-    });
-    finalize(P_RR, P_RN);
-    CKL();
   }
   return HENRY_OK;
 }
@@ -1208,6 +1256,7 @@ void henry_default_config(henry_config* c) {
   c->lin_retry = 1;
   c->finalize_nct = 512;
   c->adj_rtol = 1e-10;
+  c->cuda_graphs = 1;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -1257,15 +1306,20 @@ void henry_destroy(henry_handle* h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->perm_mem) cudaFree(h->perm_mem);
   if (h->adj_mem) cudaFree(h->adj_mem);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& p : h->prof.pend) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
   }
   for (auto e : h->prof.pool) cudaEventDestroy(e);
-  for (auto& kv : h->g64)
+  for (auto& kv : h->g64) {
+    kv.second.drop_graphs();
     if (kv.second.mem) cudaFree(kv.second.mem);
-  for (auto& kv : h->g32)
+  }
+  for (auto& kv : h->g32) {
+    kv.second.drop_graphs();
     if (kv.second.mem) cudaFree(kv.second.mem);
+  }
   for (auto& kv : h->kl_tables) {
     cudaFree(kv.second.ti);
     cudaFree(kv.second.tj);
@@ -1746,6 +1800,7 @@ int static_solve(henry_handle* H, int level, int with_coarse, const double* xi, 
   if (rc) return rc;
   const LevelGeom gf = geom(H->cfg, level);
   Group<T> Gf, Gc;
+  Gf.graphs = Gc.graphs = false;  // instantiating a graph would allocate
   size_t need = (Gf.carve(nullptr, n, gf.nx, gf.ny, gf.h) + 255) & ~size_t(255);
   size_t need_c = 0;
   LevelGeom gc{};
