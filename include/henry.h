@@ -314,7 +314,7 @@ enum {
   HENRY_K_ASSEMBLE = 0,          /* a4: fine-grid residual + Jacobian */
   HENRY_K_COARSE_OPS = 1,        /* a5: coarse operators (rediscretised or Galerkin) + coarsest inverse */
   HENRY_K_STATE_RESTRICT = 2,    /* a5: 2x2 averages of the state for rediscretisation */
-  HENRY_K_SMOOTH = 3,            /* a7: red-black block Gauss-Seidel half-sweeps */
+  HENRY_K_SMOOTH = 3,            /* a7: red-black block Gauss-Seidel half-sweeps on the solve's fine grid */
   HENRY_K_RESIDUAL_RESTRICT = 4, /* a7: residual + restriction (and x += P x_c without post-smoothing) */
   HENRY_K_COARSE_SOLVE = 5,      /* a7: 4x4 solve on the 2 x 1 grid */
   HENRY_K_SPMV = 6,              /* a8: y = J x with dot products */
@@ -322,7 +322,8 @@ enum {
   HENRY_K_NEWTON = 8,            /* a9, a10: Newton update, tests, step start */
   HENRY_K_QOI = 9,               /* a2, a3, a11: coefficients, initial state, QoIs */
   HENRY_K_FUSED = 10,            /* a3-a11 for a small grid: the one-CTA-per-sample solver */
-  HENRY_K_COUNT = 11
+  HENRY_K_SMOOTH_COARSE = 11,    /* a7: the same half-sweeps on the coarser multigrid levels */
+  HENRY_K_COUNT = 12
 };
 
 /* Start (enable != 0: counters reset) or stop timing on this handle.  While

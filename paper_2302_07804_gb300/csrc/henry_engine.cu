@@ -555,15 +555,16 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
     const unsigned gh = nblk((int64_t)B * L.N / 2);
     const double hc = na * L.N / 2;  // swept cells per half-sweep
+    const int sm = k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE;
     Level& Lc = G.lv[k + 1];
     if (nu1 > 0) {
-      launch(H, st, HENRY_K_SMOOTH, hc * (b4 + 2 * v2), na * sweep_flops(L.nx, L.ny, 0),
+      launch(H, st, sm, hc * (b4 + 2 * v2), na * sweep_flops(L.nx, L.ny, 0),
              [&] { k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act); });
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
+      launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
              [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu1; ++i) {
         for (int col = 0; col < 2; ++col)
-          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
+          launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
                  [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
       launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * (10 * b4 + 7 * v2), na * restrict_flops(L.nx, L.ny), [&] {
@@ -595,14 +596,15 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
     const unsigned gh = nblk((int64_t)B * L.N / 2);
     const double hc = na * L.N / 2;
+    const int sm = k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE;
     if (nu2 > 0) {
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3.5 * v2), na * (sweep_flops(L.nx, L.ny, 1) + L.N),
+      launch(H, st, sm, hc * (5 * b4 + 3.5 * v2), na * (sweep_flops(L.nx, L.ny, 1) + L.N),
              [&] { k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act); });
-      launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
+      launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
              [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
       for (int i = 1; i < nu2; ++i) {
         for (int col = 0; col < 2; ++col)
-          launch(H, st, HENRY_K_SMOOTH, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
+          launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
                  [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
       }
     } else {

@@ -26,7 +26,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
-                  "spmv", "krylov", "newton", "qoi", "fused")
+                  "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
 
 
 class HenryConfig(ctypes.Structure):
