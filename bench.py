@@ -175,6 +175,26 @@ def reduce_sum(x, world):
 
 
 # ------------------------------------------------------------------ CPU oracle (reference arm / baseline)
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo, else the platform's)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":")[0].strip().lower()
+            if k in ("model name", "cpu part") or k.startswith("hardware"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def oracle_sample(mix=((0, 3), (1, 1)), level2_per_4_cores=1):
     """The oracle as it stands on the host cores: a bounded sample of the
     workload (level-0..2 scenarios in the workload's level mix, one process
@@ -268,6 +288,19 @@ class Workload:
         self.sums = torch.zeros((self.L, 2, 2, 3), dtype=torch.float64, device=dev)
         self.xis = [torch.cat(list(x)).contiguous() for x in xis]  # per step, samples in level order
         self.fails = 0
+        self.iters = {"newton_iters": 0, "linear_iters": 0, "newton_solves": 0}
+
+    def note_stats(self, stats):
+        for k in self.iters:
+            self.iters[k] += int(stats[k])
+
+    def iteration_means(self):
+        """Residual evaluations per implicit step (updates + the converged
+        check) and BiCGStab iterations per Newton system, over all solves."""
+        it = self.iters
+        systems = max(it["newton_iters"] - it["newton_solves"], 1)
+        return {"newton_residuals_per_step": it["newton_iters"] / max(it["newton_solves"], 1),
+                "bicgstab_per_newton_system": it["linear_iters"] / systems}
 
     def _slice(self, l):
         a, b = self.off[l], self.off[l + 1]
@@ -288,6 +321,7 @@ class Workload:
                                                            stream=stream, allow_failures=True,
                                                            out=(self.qf, self.qc, self.st))
             self.fails += int(stats["failed_samples"])
+            self.note_stats(stats)
         for l in range(self.L):
             qf, qc, st = self.outs[l]
             henry.mlmc_accumulate(l, qf, qc, st, self.sums[l], stream=stream)
@@ -309,6 +343,7 @@ class Workload:
             _, _, _, stats = self._level_solvers()[l].level_batch_solve(l, xi[a:b], with_coarse=wc, stream=stream,
                                                                         allow_failures=True, out=self.outs[l])
             self.fails += int(stats["failed_samples"])
+            self.note_stats(stats)
 
     def profile(self, on):
         for s in self._level_solvers():
@@ -623,6 +658,7 @@ def main():
                        "l2": "working set > L2 (level-0 batch alone is GBs); no flush needed",
                        "failed_samples": W.fails},
             "e2e": {"value": e2e, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "iterations": W.iteration_means(),
             "clocks": clk.summary()}
 
     if rank == 0 and not args.no_extras:
@@ -692,7 +728,7 @@ def main():
         # ---- CPU oracle on the host cores (bounded sample)
         try:
             v, cores, desc, wall = oracle_sample()
-            line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+            line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
                                     "sample": desc}
         except Exception as exc:  # the baseline must not hide the GPU line
             line["cpu_baseline"] = {"value": None, "unit": "cell-steps/s", "cores": os.cpu_count(),
