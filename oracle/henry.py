@@ -447,6 +447,58 @@ def qoi(prm, grid, coef, p, c):
     return mass, cpt
 
 
+# The paper's 12 observation points, Eq. (12points), in its coordinates
+# (x in [0, 2], y in [-1, 0]); y here is y_paper + Ly.
+POINTS_12 = [(x, y) for y in (-0.95, -0.75, -0.50) for x in (1.10, 1.35, 1.60, 1.85)]
+C_FRESH = 0.012178  # Eq. (integral_fw): fresh water where c <= 0.012178
+
+
+def point_value(prm, grid, c, x, y):
+    """c at (x, y) (this domain's coordinates) by bilinear interpolation of
+    the four surrounding cell-centre values."""
+    tx = x * grid.nx / prm.Lx - 0.5
+    ty = y * grid.ny / prm.Ly - 0.5
+    ix, iy = int(math.floor(tx)), int(math.floor(ty))
+    fx, fy = tx - ix, ty - iy
+    return ((1 - fy) * ((1 - fx) * c[iy, ix] + fx * c[iy, ix + 1])
+            + fy * ((1 - fx) * c[iy + 1, ix] + fx * c[iy + 1, ix + 1]))
+
+
+def freshwater_area(grid, c):
+    """Eq. (integral_fw) by the midpoint rule: the area of the cells whose
+    mass fraction is at most 0.012178."""
+    return float(np.count_nonzero(c <= C_FRESH)) * grid.h * grid.h
+
+
+def field_level0(prm, grid, c):
+    """c averaged over the cells of the level-0 grid (nx0 x ny0), row-major."""
+    f = grid.nx // prm.nx0
+    return c.reshape(prm.ny0, f, prm.nx0, f).mean(axis=(1, 3)).ravel()
+
+
+def qoi_paper(prm, grid, coef, p, c, field=False):
+    """The paper's QoIs at T (Sec. 2.2 and 4): salt mass and c(1.5, 0.25) as in
+    ``qoi``, the freshwater integral Q_FW, c at the 12 points of Eq. (12points)
+    and, with ``field``, the c field averaged to the level-0 grid (whose MLMC
+    mean and variance are the paper's mean and variance fields)."""
+    mass, cpt = qoi(prm, grid, coef, p, c)
+    out = [mass, cpt, freshwater_area(grid, c)]
+    out += [float(point_value(prm, grid, c, x, y + prm.Ly)) for x, y in POINTS_12]
+    if field:
+        out += list(field_level0(prm, grid, c))
+    return np.array(out)
+
+
+def paper_params(**kw):
+    """The paper's variant of the problem (Table tab:HenryParam, Sec. 4):
+    g = 9.8, rho1 = 1024.99, Dm = 18.8571e-6, K = 1.020408e-9, recharge
+    amplitude 0.5, T = 6016 s in 188 steps at level 0 (tau = 32 s); used with
+    the two-layer porosity model."""
+    base = dict(g=9.8, rho1=1024.99, Dm=18.8571e-6, K_mean=1.020408e-9, qin_amp=0.5, T=6016.0, steps0=188)
+    base.update(kw)
+    return Params(**base)
+
+
 def coefficient_model(model):
     """'uniform3' (default), 'kl' (oracle.kl) or 'two_layer'."""
     if model == "uniform3":
@@ -459,9 +511,10 @@ def coefficient_model(model):
     raise ValueError(model)
 
 
-def solve_scenario(prm, level, xi, return_state=False, stats=None, model="uniform3"):
+def solve_scenario(prm, level, xi, return_state=False, stats=None, model="uniform3", qoi_set=0):
     """All r_l implicit-Euler steps of one scenario at MLMC level ``level`` for
-    random input ``xi``; returns (mass, c_point) and a convergence flag."""
+    random input ``xi``; returns the QoIs ((mass, c_point) for qoi_set 0,
+    ``qoi_paper`` for 1, with the level-0 field for 2) and a convergence flag."""
     grid = Grid.level(prm, level)
     coef = coefficient_model(model)(prm, grid, xi)
     p, c = initial_state(prm, grid)
@@ -469,22 +522,21 @@ def solve_scenario(prm, level, xi, return_state=False, stats=None, model="unifor
     for _ in range(grid.steps):
         p, c, conv = newton_step(prm, grid, coef, p, c, stats=stats)
         ok = ok and conv
-    q = qoi(prm, grid, coef, p, c)
+    q = qoi(prm, grid, coef, p, c) if qoi_set == 0 else qoi_paper(prm, grid, coef, p, c, field=qoi_set == 2)
     if return_state:
         return q, ok, (p, c)
     return q, ok
 
 
-def solve_scenarios(prm, level, xis, stats=None, model="uniform3"):
-    """Sequential loop over samples: returns q[n][2] and ok[n]."""
+def solve_scenarios(prm, level, xis, stats=None, model="uniform3", qoi_set=0):
+    """Sequential loop over samples: returns q[n][n_qoi] and ok[n]."""
     xis = np.asarray(xis, dtype=np.float64)
-    out = np.empty((xis.shape[0], 2))
-    ok = np.empty(xis.shape[0], dtype=bool)
+    rows, ok = [], np.empty(xis.shape[0], dtype=bool)
     for i, xi in enumerate(xis):
-        q, o = solve_scenario(prm, level, xi, stats=stats, model=model)
-        out[i] = q
+        q, o = solve_scenario(prm, level, xi, stats=stats, model=model, qoi_set=qoi_set)
+        rows.append(np.asarray(q, dtype=np.float64))
         ok[i] = o
-    return out, ok
+    return np.array(rows).reshape(xis.shape[0], -1), ok
 
 
 def _solve_one(args):
