@@ -82,6 +82,18 @@ enum { HENRY_FP64 = 0, HENRY_MIXED = 1 /* FP32 Jacobian, BiCGStab and V-cycle */
  * The field models use harmonic means of K and phi Dm on faces. */
 enum { HENRY_MODEL_UNIFORM3 = 0, HENRY_MODEL_KL = 1, HENRY_MODEL_TWO_LAYER = 2 };
 
+/* QoI sets (henry_config.qoi_set); henry_n_qoi gives the count per sample.
+ * STANDARD (2): [0] salt mass sum phi rho(c) c h^2 at T (kg per metre of
+ *   depth), [1] c at (1.5, 0.25), the mean of the four cells at that vertex.
+ * PAPER (15): those two, [2] the freshwater integral Q_FW of Eq.
+ *   (integral_fw), the area of the cells with c <= 0.012178, and [3..14] c at
+ *   the 12 points of Eq. (12points) in the paper's order (its y in [-1, 0] is
+ *   y - Ly here) by bilinear interpolation of the surrounding cell centres.
+ * PAPER_FIELD (15 + nx0 ny0): those 15 and the c field averaged over the cells
+ *   of the level-0 grid, row-major; its MLMC mean and variance (mlmc_accumulate)
+ *   are the paper's mean and variance fields (Sec. 4). */
+enum { HENRY_QOI_STANDARD = 0, HENRY_QOI_PAPER = 1, HENRY_QOI_PAPER_FIELD = 2 };
+
 /* Coarse-grid operators of the multigrid hierarchy. */
 enum { HENRY_COARSE_REDISCRETISE = 0, HENRY_COARSE_GALERKIN = 1 };
 
@@ -129,6 +141,7 @@ typedef struct {
   int32_t cuda_graphs; /* 1 (default): each BiCGStab iteration's body (two V-cycles, two matvecs, vector
                           updates) is captured once per workspace and batch size into a CUDA graph and
                           replayed; 0: plain launches.  Same values either way; off while profiling */
+  int32_t qoi_set;     /* HENRY_QOI_* (default STANDARD); sets other than STANDARD use the multi-kernel path */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -142,6 +155,17 @@ typedef struct {
 
 /* Fill *cfg with the defaults described above.  Never fails. */
 void henry_default_config(henry_config* cfg);
+
+/* The defaults changed to the paper's variant of the problem (Table
+ * tab:HenryParam and Sec. 4): g = 9.8, rho1 = 1024.99, Dm = 18.8571e-6, K_mean
+ * = 1.020408e-9, T = 6016 s in steps0 = 188 steps (tau = 32 s at level 0),
+ * the two-layer porosity with Kozeny-Carman K, recharge amplitude 0.5 and the
+ * paper's QoIs (HENRY_QOI_PAPER).  Never fails. */
+void henry_paper_config(henry_config* cfg);
+
+/* QoIs per sample for cfg's qoi_set (2, 15 or 15 + nx0 ny0); -HENRY_EINVAL for a
+ * NULL pointer or an unknown set. */
+int henry_n_qoi(const henry_config* cfg);
 
 /* Create a handle for `cfg` (copied).  Allocates no device memory yet.
  * Errors: EINVAL on a NULL pointer or inconsistent grid sizes. */
@@ -164,10 +188,10 @@ const char* henry_last_error(void);
 int henry_sample_xi(uint64_t seed, int level, uint64_t first_sample, int n, double* xi_dev, void* stream);
 
 /* a2-a11. Solve n scenarios at MLMC level `level` (0 <= level <= max_level)
- * for inputs xi_dev[n][n_xi] (n_xi = 3, or 2 kl_terms + 1 for HENRY_MODEL_KL) and write the QoIs at T to qoi_fine_dev[n][2].
+ * for inputs xi_dev[n][n_xi] (n_xi = 3, or 2 kl_terms + 1 for HENRY_MODEL_KL) and write the QoIs at T to qoi_fine_dev[n][n_qoi] (n_qoi = henry_n_qoi).
  * If with_coarse != 0 (level >= 1) also solve the same xi on level - 1 (the
  * coarse partner of the telescoping difference, Eq. (A): same xi, grid and
- * time step of the coarser level) into qoi_coarse_dev[n][2].
+ * time step of the coarser level) into qoi_coarse_dev[n][n_qoi].
  * status_dev[n] (int32) receives HENRY_SAMPLE_* (worst over fine and coarse).
  * stats_host may be NULL.  Synchronises `stream`.  Returns HENRY_ENOCONV if
  * any sample failed (its QoIs are then unspecified). */
@@ -179,8 +203,8 @@ int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const d
  * the situation of an MLMC pass, Sec. 3: each level l needs m_l samples of
  * Y_l, Eq. (A)).  Sample i is solved at level levels_host[i] (host array,
  * 0 <= level <= max_level, any order) with inputs xi_dev[i][n_xi]; its QoIs go
- * to qoi_fine_dev[i][2] and, when with_coarse != 0, those of its coarse partner
- * (level - 1, same xi) to qoi_coarse_dev[i][2] (zeros for level-0 samples).
+ * to qoi_fine_dev[i][n_qoi] and, when with_coarse != 0, those of its coarse partner
+ * (level - 1, same xi) to qoi_coarse_dev[i][n_qoi] (zeros for level-0 samples).
  * status_dev[i] as in henry_level_batch_solve.  The levels run concurrently:
  * each on its own child handle (created on first use, same configuration,
  * its own workspace), CUDA stream and host thread, forked from `stream` by an
@@ -200,7 +224,7 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
  * henry_level_batch_solve and weights qoi_weights_dev[n][2], Q = w0 salt mass +
  * w1 c(1.5, 0.25) at T; writes grad_dev[n][n_xi] = dQ/dxi (three-parameter
  * and two-layer models: d/d(xi1, xi2, xi3); KL: d/d(theta_K[terms],
- * theta_phi[terms], xi3)), qoi_dev[n][2] (the forward QoIs, the same values as
+ * theta_phi[terms], xi3)), qoi_dev[n][n_qoi] (the forward QoIs; the weights act on the first two, the standard QoIs; the same values as
  * henry_level_batch_solve) and status_dev[n] (HENRY_SAMPLE_*; 2: an adjoint
  * solve did not converge).  Always computed in FP64, whatever `precision`.
  * The forward keeps the state pair every checkpoint_every steps (>= 1; values

@@ -455,10 +455,13 @@ C_FRESH = 0.012178  # Eq. (integral_fw): fresh water where c <= 0.012178
 
 def point_value(prm, grid, c, x, y):
     """c at (x, y) (this domain's coordinates) by bilinear interpolation of
-    the four surrounding cell-centre values."""
+    the four surrounding cell-centre values (clamped stencil)."""
     tx = x * grid.nx / prm.Lx - 0.5
     ty = y * grid.ny / prm.Ly - 0.5
-    ix, iy = int(math.floor(tx)), int(math.floor(ty))
+    # the 2 x 2 stencil stays on the grid: a point outside the hull of the cell
+    # centres (only on coarse grids) is extrapolated linearly
+    ix = min(max(int(math.floor(tx)), 0), grid.nx - 2)
+    iy = min(max(int(math.floor(ty)), 0), grid.ny - 2)
     fx, fy = tx - ix, ty - iy
     return ((1 - fy) * ((1 - fx) * c[iy, ix] + fx * c[iy, ix + 1])
             + fy * ((1 - fx) * c[iy + 1, ix] + fx * c[iy + 1, ix + 1]))

@@ -302,6 +302,10 @@ void prof_drain(henry_handle* H) {
 }
 
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
+int qoi_count(const henry_config& c) {
+  return c.qoi_set == HENRY_QOI_STANDARD ? 2 : (c.qoi_set == HENRY_QOI_PAPER ? 15 : 15 + c.nx0 * c.ny0);
+}
+QoiSpec qoi_spec(const henry_config& c) { return QoiSpec{c.qoi_set, qoi_count(c), c.nx0, c.ny0, c.Lx, c.Ly}; }
 int n_inputs(const henry_config& c) { return c.coef_model == HENRY_MODEL_KL ? 2 * c.kl_terms + 1 : 3; }
 
 Phys phys_of(const henry_config& c) {
@@ -341,7 +345,7 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   // 1 (default): only with FP32 linear algebra, where it measured faster; on
   // GB300 the FP64 variant (one CTA per SM for lack of shared memory) is
   // FP64-latency bound and slower than the multi-kernel path.  2: always.
-  if (c.fused_small_grids <= 0 || has_fields(c)) return false;
+  if (c.fused_small_grids <= 0 || has_fields(c) || c.qoi_set != HENRY_QOI_STANDARD) return false;
   if (c.fused_small_grids == 1 && sizeof(T) != sizeof(float)) return false;
   const LevelGeom lg = geom(c, level);
   if (!cta_layout(lg.nx, lg.ny, (int)sizeof(T), L)) return false;
@@ -861,7 +865,8 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
     if (rc) return rc;
   }
   launch(H, st, HENRY_K_QOI, (double)n0 * 16, [&] {
-    k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc);
+    k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc,
+                             qoi_spec(c));
   });
   CKL();
   return HENRY_OK;
@@ -925,8 +930,9 @@ int batch_solve_level(henry_handle* H, int level, const double* xi, int n, doubl
     if (rc) return rc;
     rc = set_coefficients<T>(H, *G, xi + (int64_t)n_inputs(H->cfg) * off, B, st);
     if (rc) return rc;
-    rc = fused ? solve_group_fused<T>(H, *G, B, CL, qoi + 2 * (int64_t)off, st)
-               : solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
+    const int nq = qoi_count(H->cfg);
+    rc = fused ? solve_group_fused<T>(H, *G, B, CL, qoi + nq * (int64_t)off, st)
+               : solve_group<T>(H, *G, B, qoi + nq * (int64_t)off, st);
     if (rc) return rc;
     k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, first ? 1 : 0);
     CKL();
@@ -1059,7 +1065,8 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
     if (rc) return rc;
     CK(cudaMemcpyAsync(seg + (int64_t)(step % C) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
   }
-  k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc);
+  k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc,
+                             qoi_spec(c));
   CKL();
   // backward
   k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.lin_active, G.newton_it);
@@ -1166,7 +1173,7 @@ int adjoint_level(henry_handle* H, int level, const double* xi, int n, const dou
     rc = set_coefficients<double>(H, *G, xi + (int64_t)nin * off, B, st);
     if (rc) return rc;
     rc = adjoint_group(H, *G, B, xi + (int64_t)nin * off, w + 2 * (int64_t)off, grad + (int64_t)nin * off,
-                       qoi + 2 * (int64_t)off, C, st);
+                       qoi + qoi_count(c) * (int64_t)off, C, st);
     if (rc) return rc;
     k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, 1);
     CKL();
@@ -1259,6 +1266,7 @@ void henry_default_config(henry_config* c) {
   c->finalize_nct = 512;
   c->adj_rtol = 1e-10;
   c->cuda_graphs = 1;
+  c->qoi_set = HENRY_QOI_STANDARD;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -1268,6 +1276,24 @@ void henry_default_config(henry_config* c) {
   c->kl_sigma_phi = 0.1;
   c->phi_lo = 0.05;
   c->phi_hi = 0.65;
+}
+
+void henry_paper_config(henry_config* c) {
+  if (!c) return;
+  henry_default_config(c);
+  c->g = 9.8; c->rho1 = 1024.99; c->Dm = 18.8571e-6; c->K_mean = 1.020408e-9;
+  c->qin_amp = 0.5;
+  c->T = 6016.0;
+  c->steps0 = 188;
+  c->coef_model = HENRY_MODEL_TWO_LAYER;
+  c->qoi_set = HENRY_QOI_PAPER;
+}
+
+int henry_n_qoi(const henry_config* c) {
+  if (!c) return -set_err(HENRY_EINVAL, "NULL argument");
+  if (c->qoi_set < HENRY_QOI_STANDARD || c->qoi_set > HENRY_QOI_PAPER_FIELD)
+    return -set_err(HENRY_EINVAL, "bad qoi_set");
+  return qoi_count(*c);
 }
 
 int henry_create(const henry_config* cfg, henry_handle** out) {
@@ -1286,6 +1312,7 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
     return set_err(HENRY_EINVAL, "bad coarse_op");
   if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
     return set_err(HENRY_EINVAL, "bad coef_model");
+  if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_FIELD) return set_err(HENRY_EINVAL, "bad qoi_set");
   if (c.coef_model == HENRY_MODEL_KL &&
       (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
        !(c.phi_lo < c.phi_hi)))
@@ -1362,6 +1389,7 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int nin = n_inputs(h->cfg);
+  const int nq = qoi_count(h->cfg);
   const double* xs = xi_dev;
   double* qf = qoi_fine_dev;
   double* qc = qoi_coarse_dev;
@@ -1377,8 +1405,8 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
       };
       *pd = (int*)take(sizeof(int) * cap);
       *x = (double*)take(sizeof(double) * cap * nin);
-      *f = (double*)take(sizeof(double) * cap * 2);
-      *c = (double*)take(sizeof(double) * cap * 2);
+      *f = (double*)take(sizeof(double) * cap * nq);
+      *c = (double*)take(sizeof(double) * cap * nq);
       *sd = (int32_t*)take(sizeof(int32_t) * cap);
       return o;
     };
@@ -1444,7 +1472,7 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
       std::memset(&sts[l], 0, sizeof sts[l]);
       const int wc = (with_coarse && l > 0) ? 1 : 0;
       const int64_t o = first[l];
-      rcs[l] = henry_level_batch_solve(h->kids[l], l, wc, xs + o * nin, cnt[l], qf + o * 2, wc ? qc + o * 2 : nullptr,
+      rcs[l] = henry_level_batch_solve(h->kids[l], l, wc, xs + o * nin, cnt[l], qf + o * nq, wc ? qc + o * nq : nullptr,
                                        ss + o, &sts[l], h->kid_streams[l]);
       if (rcs[l] != HENRY_OK && rcs[l] != HENRY_ENOCONV) msg[l] = henry_last_error();
     });
@@ -1453,12 +1481,12 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
   // every level solve synchronised its own stream, so its results are in memory
   for (int l : act)
     if (rcs[l] != HENRY_OK && rcs[l] != HENRY_ENOCONV) return set_err(rcs[l], "level %d: %s", l, msg[l].c_str());
-  if (with_coarse && cnt[0]) CK(cudaMemsetAsync(qc + (int64_t)first[0] * 2, 0, sizeof(double) * 2 * cnt[0], st));
+  if (with_coarse && cnt[0]) CK(cudaMemsetAsync(qc + (int64_t)first[0] * nq, 0, sizeof(double) * nq * cnt[0], st));
   if (!sorted) {
-    k_permute_rows<double, true><<<nblk((int64_t)n * 2), TPB, 0, st>>>(n, 2, perm_dev, qf, qoi_fine_dev);
+    k_permute_rows<double, true><<<nblk((int64_t)n * nq), TPB, 0, st>>>(n, nq, perm_dev, qf, qoi_fine_dev);
     CKL();
     if (with_coarse) {
-      k_permute_rows<double, true><<<nblk((int64_t)n * 2), TPB, 0, st>>>(n, 2, perm_dev, qc, qoi_coarse_dev);
+      k_permute_rows<double, true><<<nblk((int64_t)n * nq), TPB, 0, st>>>(n, nq, perm_dev, qc, qoi_coarse_dev);
       CKL();
     }
     k_permute_rows<int32_t, true><<<nblk(n), TPB, 0, st>>>(n, 1, perm_dev, ss, status_dev);
@@ -1604,8 +1632,8 @@ int mlmc_accumulate(int level, int n, int n_qoi, const double* qoi_fine_dev, con
   if (level < 0) return set_err(HENRY_EINVAL, "level %d < 0", level);
   if (n <= 0 || n_qoi <= 0) return set_err(HENRY_EINVAL, "n = %d and n_qoi = %d must be positive", n, n_qoi);
   if (!qoi_fine_dev || !sums_dev) return set_err(HENRY_EINVAL, "NULL device pointer");
-  k_mlmc_accumulate<<<1, 1024, 0, (cudaStream_t)stream>>>(n, n_qoi, qoi_fine_dev, qoi_coarse_dev, status_dev,
-                                                          sums_dev);
+  k_mlmc_accumulate<<<dim3(n_qoi, 2), 1024, 0, (cudaStream_t)stream>>>(n, n_qoi, qoi_fine_dev, qoi_coarse_dev,
+                                                                        status_dev, sums_dev);
   CKL();
   return HENRY_OK;
 }
@@ -1782,6 +1810,8 @@ int static_check_config(const henry_config& c) {
     return set_err(HENRY_EINVAL, "bad coarse_op");
   if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
     return set_err(HENRY_EINVAL, "bad coef_model");
+  if (c.qoi_set != HENRY_QOI_STANDARD)
+    return set_err(HENRY_EINVAL, "the allocation-free entry point writes the two standard QoIs only (qoi_set 0)");
   if (c.coef_model == HENRY_MODEL_KL &&
       (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
        !(c.phi_lo < c.phi_hi)))

@@ -199,30 +199,69 @@ __global__ void __launch_bounds__(TPB) k_init_state(int B, int nx, int ny, doubl
   x[e] = make_double2(rho0g * (Ly - (iy + 0.5) * h), 0.0);
 }
 
-// a11: QoIs, one CTA per sample: salt mass sum phi rho c h^2 and c at
+// a11: QoIs, one CTA per sample, qoi[s][nq]: salt mass sum phi rho c h^2 and c at
 // (1.5, 0.25) = mean of the cells (ix0, iy0), (ix0+1, iy0), (ix0, iy0+1),
 // (ix0+1, iy0+1) with ix0 = 1.5 / h - 1, iy0 = 0.25 / h - 1.
 // With per-cell coefficients (cc != NULL) the porosity weights each cell.
+// QS >= 1 (the paper's QoIs, Sec. 2.2 and 4) adds [2] the freshwater integral
+// Q_FW of Eq. (integral_fw), the area of the cells with c <= 0.012178, and
+// [3..14] c at the 12 points of Eq. (12points) (paper y in [-1, 0], here y +
+// Ly) by bilinear interpolation of the four surrounding cell centres (the
+// stencil clamped to the grid); QS = 2
+// adds [15..] the c field averaged over the cells of the nx0 x ny0 level-0
+// grid, row-major.
+struct QoiSpec {
+  int set, nq, nx0, ny0;
+  double Lx, Ly;
+};
+__device__ __forceinline__ double cell_c(const double2* xs, int ix, int iy, int nx) { return xs[st_of(ix, iy, nx)].y; }
 __global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, double rho0, double drho,
                                              const Coef* __restrict__ coef, const double2* __restrict__ x,
-                                             double* __restrict__ qoi, const double2* __restrict__ cc = nullptr) {
+                                             double* __restrict__ qoi, const double2* __restrict__ cc = nullptr,
+                                             QoiSpec Q = QoiSpec{0, 2, 0, 0, 2.0, 1.0}) {
   __shared__ double sh[40];
   const int s = blockIdx.x;
   const int N = nx * ny;
   const double2* xs = x + (int64_t)s * N;
-  double acc = 0.0;
+  double* out = qoi + (int64_t)s * Q.nq;
+  double acc = 0.0, fresh = 0.0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const double c = xs[i].y;
     const double w = cc ? cc[(int64_t)s * N + i].x : 1.0;
     acc += w * (rho0 + drho * c) * c;
+    fresh += (c <= 0.012178) ? 1.0 : 0.0;
   }
   acc = block_reduce<false>(acc, sh);
+  if (Q.set >= 1) fresh = block_reduce<false>(fresh, sh);
   if (threadIdx.x == 0) {
     const int ix0 = (3 * ny) / 2 - 1, iy0 = ny / 4 - 1;
     const double c00 = xs[st_of(ix0, iy0, nx)].y, c10 = xs[st_of(ix0 + 1, iy0, nx)].y;
     const double c01 = xs[st_of(ix0, iy0 + 1, nx)].y, c11 = xs[st_of(ix0 + 1, iy0 + 1, nx)].y;
-    qoi[2 * (int64_t)s] = (cc ? 1.0 : coef[s].phi) * acc * h * h;
-    qoi[2 * (int64_t)s + 1] = 0.25 * (((c00 + c10) + c01) + c11);
+    out[0] = (cc ? 1.0 : coef[s].phi) * acc * h * h;
+    out[1] = 0.25 * (((c00 + c10) + c01) + c11);
+    if (Q.set >= 1) out[2] = fresh * h * h;
+  }
+  if (Q.set < 1) return;
+  if (threadIdx.x < 12) {
+    const double px = 1.10 + 0.25 * (threadIdx.x & 3);
+    const int row = threadIdx.x >> 2;
+    const double py = (row == 0 ? -0.95 : (row == 1 ? -0.75 : -0.50)) + Q.Ly;
+    const double tx = px * nx / Q.Lx - 0.5, ty = py * ny / Q.Ly - 0.5;
+    // the 2 x 2 stencil is kept on the grid (linear extrapolation for a point
+    // outside the hull of the cell centres, which only coarse user grids have)
+    const int ix = min(max((int)floor(tx), 0), nx - 2), iy = min(max((int)floor(ty), 0), ny - 2);
+    const double fx = tx - ix, fy = ty - iy;
+    out[3 + threadIdx.x] = (1 - fy) * ((1 - fx) * cell_c(xs, ix, iy, nx) + fx * cell_c(xs, ix + 1, iy, nx)) +
+                           fy * ((1 - fx) * cell_c(xs, ix, iy + 1, nx) + fx * cell_c(xs, ix + 1, iy + 1, nx));
+  }
+  if (Q.set < 2) return;
+  const int f = nx / Q.nx0;
+  for (int c0 = threadIdx.x; c0 < Q.nx0 * Q.ny0; c0 += blockDim.x) {
+    const int IY = c0 / Q.nx0, IX = c0 - IY * Q.nx0;
+    double a = 0.0;
+    for (int jy = 0; jy < f; ++jy)
+      for (int jx = 0; jx < f; ++jx) a += cell_c(xs, IX * f + jx, IY * f + jy, nx);
+    out[15 + c0] = a / (double)(f * f);
   }
 }
 
@@ -311,8 +350,9 @@ __global__ void __launch_bounds__(1024) k_mlmc_accumulate(int n, int n_qoi, cons
                                                           const int32_t* __restrict__ status,
                                                           double* __restrict__ sums) {
   __shared__ double sh[40];
-  for (int which = 0; which < 2; ++which) {
-    for (int q = 0; q < n_qoi; ++q) {
+  {  // block (q, which): the moments of one QoI of Y (which = 0) or of the fine QoI (which = 1)
+    const int which = blockIdx.y, q = blockIdx.x;
+    {
       double cnt = 0.0, sum = 0.0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         if (status && status[i] != 0) continue;
@@ -323,7 +363,7 @@ __global__ void __launch_bounds__(1024) k_mlmc_accumulate(int n, int n_qoi, cons
       }
       cnt = block_reduce<false>(cnt, sh);
       sum = block_reduce<false>(sum, sh);
-      if (cnt == 0.0) continue;
+      if (cnt == 0.0) return;  // uniform: every thread holds the reduced count
       const double mb = sum / cnt;
       double m2 = 0.0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) {

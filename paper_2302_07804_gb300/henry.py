@@ -18,13 +18,15 @@ HENRY_SAMPLE_OK, HENRY_SAMPLE_NEWTON, HENRY_SAMPLE_LINEAR, HENRY_SAMPLE_NONFINIT
 HENRY_FP64, HENRY_MIXED = 0, 1
 HENRY_COARSE_REDISCRETISE, HENRY_COARSE_GALERKIN = 0, 1
 HENRY_MODEL_UNIFORM3, HENRY_MODEL_KL, HENRY_MODEL_TWO_LAYER = 0, 1, 2
+HENRY_QOI_STANDARD, HENRY_QOI_PAPER, HENRY_QOI_PAPER_FIELD = 0, 1, 2
 N_QOI = 2
 N_XI = 3
 
 EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_error", "henry_sample_xi",
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
-           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint")
+           "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint", "henry_n_qoi",
+           "henry_paper_config")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
 
@@ -41,7 +43,7 @@ class HenryConfig(ctypes.Structure):
                 ("fused_small_grids", ctypes.c_int32), ("coef_model", ctypes.c_int32), ("kl_terms", ctypes.c_int32)] + \
                [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")] + \
                [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32), ("adj_rtol", ctypes.c_double),
-                ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32)]
+                ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -73,6 +75,9 @@ def lib():
         U64 = ctypes.c_uint64
         L.henry_default_config.argtypes = [ctypes.POINTER(HenryConfig)]
         L.henry_default_config.restype = None
+        L.henry_paper_config.argtypes = [ctypes.POINTER(HenryConfig)]
+        L.henry_paper_config.restype = None
+        L.henry_n_qoi.argtypes = [ctypes.POINTER(HenryConfig)]
         L.henry_create.argtypes = [ctypes.POINTER(HenryConfig), ctypes.POINTER(P)]
         L.henry_destroy.argtypes = [P]
         L.henry_destroy.restype = None
@@ -133,6 +138,17 @@ def default_config(**overrides):
             raise KeyError(k)
         setattr(cfg, k, v)
     return cfg
+
+
+def paper_config(**overrides):
+    """henry_paper_config: the paper's variant (constants, T = 6016 s in 188
+    level-0 steps, two-layer porosity, the paper's QoIs) as Solver keyword
+    arguments, with ``overrides`` applied."""
+    cfg = HenryConfig()
+    lib().henry_paper_config(ctypes.byref(cfg))
+    kw = {name: getattr(cfg, name) for name, _ in HenryConfig._fields_}
+    kw.update(overrides)
+    return kw
 
 
 def sample_xi(seed, level, first_sample, n, device="cuda", stream=None):
@@ -237,6 +253,14 @@ class Solver:
         return out
 
     @property
+    def n_qoi(self):
+        """QoIs per sample for this configuration's qoi_set (henry_n_qoi)."""
+        rc = lib().henry_n_qoi(ctypes.byref(self.cfg))
+        if rc < 0:
+            raise HenryError(-rc, lib().henry_last_error().decode())
+        return rc
+
+    @property
     def n_xi(self):
         """Random inputs per sample for this configuration's coefficient model."""
         return 2 * self.cfg.kl_terms + 1 if self.cfg.coef_model == HENRY_MODEL_KL else N_XI
@@ -249,8 +273,8 @@ class Solver:
         n = xi.shape[0]
         _dev_f64(xi, (n, self.n_xi))
         if out is None:
-            qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
-            qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
+            qf = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
+            qc = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device) if with_coarse else None
             st = torch.empty((n,), dtype=torch.int32, device=xi.device)
         else:
             qf, qc, st = out
@@ -270,8 +294,8 @@ class Solver:
             raise ValueError("levels must hold one level per row of xi")
         _dev_f64(xi, (n, self.n_xi))
         if out is None:
-            qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
-            qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
+            qf = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
+            qc = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device) if with_coarse else None
             st = torch.empty((n,), dtype=torch.int32, device=xi.device)
         else:
             qf, qc, st = out
@@ -289,7 +313,7 @@ class Solver:
         _dev_f64(xi, (n, self.n_xi))
         _dev_f64(weights, (n, N_QOI))
         grad = torch.empty((n, self.n_xi), dtype=torch.float64, device=xi.device)
-        qoi = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
+        qoi = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
         st = torch.empty((n,), dtype=torch.int32, device=xi.device)
         rc = lib().henry_adjoint(self._h, level, _ptr(xi), n, _ptr(weights), _ptr(grad), _ptr(qoi),
                                  int(checkpoint_every), _ptr(st), _stream(stream))

@@ -28,10 +28,10 @@ def level_cost_model(cfg, level):
 
 
 class LevelState:
-    def __init__(self, level, device):
+    def __init__(self, level, device, n_qoi=henry.N_QOI):
         self.level = level
         self.n_used = 0          # Philox counter offset: samples drawn so far
-        self.sums = torch.zeros((2, henry.N_QOI, 3), dtype=torch.float64, device=device)
+        self.sums = torch.zeros((2, n_qoi, 3), dtype=torch.float64, device=device)
         self.gpu_seconds = 0.0
         self.cell_steps = 0.0
         self.failed = 0
@@ -41,7 +41,7 @@ class LevelState:
         S = self.sums.cpu()
         n = float(S[0, 0, 0])
         mean = S[0, :, 1].tolist()
-        var = [(float(S[0, q, 2]) / (n - 1)) if n > 1 else float("nan") for q in range(henry.N_QOI)]
+        var = [(float(S[0, q, 2]) / (n - 1)) if n > 1 else float("nan") for q in range(S.shape[1])]
         return n, mean, var
 
     def to_json(self):
@@ -50,7 +50,7 @@ class LevelState:
 
     @staticmethod
     def from_json(d, device):
-        st = LevelState(d["level"], device)
+        st = LevelState(d["level"], device, n_qoi=len(d["sums"][0]))
         st.n_used = d["n_used"]
         st.sums = torch.tensor(d["sums"], dtype=torch.float64, device=device)
         st.gpu_seconds = d["gpu_seconds"]
@@ -109,7 +109,7 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
     seed = inputs.SEED if seed is None else seed
     dev = torch.device("cuda", torch.cuda.current_device())
     levels = list(state) if state else []
-    levels += [LevelState(l, dev) for l in range(len(levels), max_level + 1)]
+    levels += [LevelState(l, dev, n_qoi=solver.n_qoi) for l in range(len(levels), max_level + 1)]
     t0 = time.perf_counter()
     for l in range(max_level + 1):
         need = max(0, pilot[l] - levels[l].n_used)

@@ -123,3 +123,18 @@ def test_mlmc_rates_reject_bad_input(L):
                  ([1.0, float("nan")], 1.0, 1e-3)):
         with pytest.raises(henry.HenryError):
             henry.mlmc_bias_test(*args)
+
+
+def test_qoi_sets_and_paper_config(L):
+    from paper_2302_07804_gb300 import henry
+    for qs, nq in ((0, 2), (1, 15), (2, 15 + 32 * 16)):
+        cfg = henry.default_config(qoi_set=qs)
+        assert L.henry_n_qoi(ctypes.byref(cfg)) == nq
+    assert L.henry_n_qoi(ctypes.byref(henry.default_config(qoi_set=3))) == -henry.HENRY_EINVAL
+    with pytest.raises(henry.HenryError) as e:
+        henry.Solver(qoi_set=3)
+    assert e.value.code == henry.HENRY_EINVAL
+    kw = henry.paper_config()
+    assert (kw["T"], kw["steps0"], kw["g"], kw["rho1"]) == (6016.0, 188, 9.8, 1024.99)
+    assert kw["coef_model"] == henry.HENRY_MODEL_TWO_LAYER and kw["qoi_set"] == henry.HENRY_QOI_PAPER
+    assert henry.Solver(**kw).n_qoi == 15
