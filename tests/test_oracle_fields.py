@@ -5,8 +5,8 @@ W^1/2 K W^1/2 = sum_q w_q k(x_q, x_q)); eigenfunctions are orthonormal in
 the quadrature inner product; the eigen-expansion with all modes reproduces
 the kernel at points off the quadrature grid (the Nystrom interpolant); the
 truncated 2-D field's pointwise variance never exceeds the covariance's.
-Two-layer model: kappa_KC from K(E[phi]) = K_mean (2.0884e-8 for the
-paper's K = 1.020408e-9, quoted in the survey of the paper's Sec. 2.2);
+Two-layer model: kappa_KC from K(E[phi]) = K_mean (Sec. 2.2), i.e. K_mean
+(1 - phi^2) / phi^3 = 2.0884e-8 for the paper's K = 1.020408e-9 and E[phi] = 0.35;
 phi at the paper's xi* (Sec. 4) peaks at 0.499 as printed (its printed
 minimum 0.248 is not reproduced by the printed formula: parity unpinned).
 """
