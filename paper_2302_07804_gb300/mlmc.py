@@ -81,6 +81,31 @@ def run_level(solver, st, n, seed, stream=None, xi=None):
     return stats
 
 
+def run_levels(solver, states, counts, seed):
+    """Solve counts[i] new samples of every level states[i].level (with coarse
+    partners) in ONE henry_batch_solve_mixed call, so that the levels run
+    concurrently, and merge each level's Y into its sums.  The samples, their
+    Philox counters and each level's accumulation batches are those of
+    run_level called level by level, so the sums are the same."""
+    import numpy as np
+    dev = states[0].sums.device
+    todo = [(st, n) for st, n in zip(states, counts) if n > 0]
+    if not todo:
+        return
+    xs = [henry.sample_xi(seed, st.level, st.n_used, n, device=dev) for st, n in todo]
+    levels = np.concatenate([np.full(n, st.level, dtype=np.int32) for st, n in todo])
+    xi = torch.cat(xs).contiguous()
+    qf, qc, status, _ = solver.batch_solve_mixed(levels, xi, with_coarse=True, allow_failures=True)
+    a = 0
+    for st, n in todo:
+        b = a + n
+        henry.mlmc_accumulate(st.level, qf[a:b], qc[a:b] if st.level > 0 else None, status[a:b], st.sums)
+        st.n_used += n
+        st.cell_steps += n * level_cost_model(solver.cfg, st.level)
+        st.failed += int((status[a:b] != 0).sum())
+        a = b
+
+
 def merge_sums(parts):
     """Chan's pairwise merge of a list of (count, mean, M2) tables, on the host
     (used to combine replicas that ran disjoint counter ranges)."""
@@ -102,19 +127,29 @@ def merge_sums(parts):
 
 
 def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None, qoi=1, cost="model",
-             var_fraction=0.5, max_rounds=4, state=None, log=None):
+             var_fraction=0.5, max_rounds=4, state=None, log=None, concurrent=True):
     """MLMC estimate of E[g_L] for QoI ``qoi`` (0 salt mass, 1 c at the point)
-    to a variance budget var_fraction * eps^2 (Eq. MSE); returns a dict."""
+    to a variance budget var_fraction * eps^2 (Eq. MSE); returns a dict.
+    concurrent (with the model cost): each round's samples of all levels go
+    to one henry_batch_solve_mixed call; otherwise level by level (needed for
+    cost="measured", which times each level's solves)."""
     from . import inputs
     seed = inputs.SEED if seed is None else seed
     dev = torch.device("cuda", torch.cuda.current_device())
     levels = list(state) if state else []
     levels += [LevelState(l, dev, n_qoi=solver.n_qoi) for l in range(len(levels), max_level + 1)]
     t0 = time.perf_counter()
-    for l in range(max_level + 1):
-        need = max(0, pilot[l] - levels[l].n_used)
-        if need:
-            run_level(solver, levels[l], need, seed)
+    together = concurrent and cost == "model"
+
+    def solve_round(counts):
+        if together:
+            run_levels(solver, levels, counts, seed)
+        else:
+            for st, n in zip(levels, counts):
+                if n:
+                    run_level(solver, st, n, seed)
+
+    solve_round([max(0, pilot[l] - levels[l].n_used) for l in range(max_level + 1)])
     budget = var_fraction * eps * eps
     alloc = None
     for rnd in range(max_rounds):
@@ -131,9 +166,7 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
             log("round %d: V=%s m=%s extra=%s" % (rnd, ["%.3g" % v for v in V], alloc, extra))
         if sum(extra) == 0:
             break
-        for st, e in zip(levels, extra):
-            if e:
-                run_level(solver, st, e, seed)
+        solve_round(extra)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     est = 0.0

@@ -38,3 +38,21 @@ def test_adaptive_mlmc_bias_test_and_rates(hl):
     assert r["variance"] <= 1.5 * 0.5 * eps * eps
     assert all(p["failed"] == 0 for p in r["levels"])
     s.close()
+
+
+def test_concurrent_rounds_give_the_same_estimate(hl):
+    """run_mlmc's rounds as one henry_batch_solve_mixed call over all levels
+    solve the same samples (same Philox counters) and accumulate the same
+    per-level batches as the level-by-level driver: identical sums."""
+    from paper_2302_07804_gb300 import mlmc
+    import json
+    out = []
+    for conc in (True, False):
+        s = hl.Solver()
+        r = mlmc.run_mlmc(s, eps=4e-3, max_level=2, pilot=(300, 60, 20), concurrent=conc)
+        out.append(r)
+        s.close()
+    assert out[0]["estimate"] == out[1]["estimate"] and out[0]["alloc"] == out[1]["alloc"]
+    a, b = json.loads(out[0]["checkpoint"]), json.loads(out[1]["checkpoint"])
+    for la, lb in zip(a, b):
+        assert la["sums"] == lb["sums"] and la["n_used"] == lb["n_used"] and la["cell_steps"] == lb["cell_steps"]
