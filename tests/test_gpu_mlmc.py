@@ -56,3 +56,22 @@ def test_concurrent_rounds_give_the_same_estimate(hl):
     a, b = json.loads(out[0]["checkpoint"]), json.loads(out[1]["checkpoint"])
     for la, lb in zip(a, b):
         assert la["sums"] == lb["sums"] and la["n_used"] == lb["n_used"] and la["cell_steps"] == lb["cell_steps"]
+
+
+def test_resume_from_checkpoint_continues_identically(hl):
+    """An MLMC run stopped after its first top-up round, serialised
+    (per-level sums and Philox counter offsets) and resumed from the JSON,
+    ends with exactly the sums of an uninterrupted run."""
+    from paper_2302_07804_gb300 import mlmc
+    import json
+    kw = dict(eps=4e-3, max_level=2, pilot=(300, 60, 20))
+    s = hl.Solver()
+    full = mlmc.run_mlmc(s, **kw)
+    part = mlmc.run_mlmc(s, max_rounds=1, **kw)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    state = [mlmc.LevelState.from_json(d, dev) for d in json.loads(part["checkpoint"])]
+    resumed = mlmc.run_mlmc(s, state=state, **kw)
+    assert resumed["estimate"] == full["estimate"]
+    for a, b in zip(json.loads(resumed["checkpoint"]), json.loads(full["checkpoint"])):
+        assert a["sums"] == b["sums"] and a["n_used"] == b["n_used"]
+    s.close()
