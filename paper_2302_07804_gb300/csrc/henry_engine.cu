@@ -301,6 +301,13 @@ void prof_drain(henry_handle* H) {
   P.pend.clear();
 }
 
+// The assembly kernel for a grid nx cells wide: the face-once tile form
+// where a tile of TPB cells holds whole rows (nx <= TPB), else the per-cell
+// form (same arguments, same results up to rounding).
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, FINE, FIELDS, DROP>) {
+  return (c.tile_assembly && nx <= TPB) ? &k_assemble_tile<T, FINE, FIELDS, DROP> : &k_assemble<T, FINE, FIELDS, DROP>;
+}
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
 int qoi_count(const henry_config& c) {
   return c.qoi_set == HENRY_QOI_STANDARD ? 2 : (c.qoi_set == HENRY_QOI_PAPER ? 15 : 15 + c.nx0 * c.ny0);
@@ -507,14 +514,14 @@ int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double
     } else {
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          k_assemble<T, false, true, DROP><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+          assemble_kernel<T, false, true, DROP>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h, L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo, G.lin_active,
               nullptr, (B4*)L.J, L.plane, nullptr, L.cc, L.fc);
         else
-          k_assemble<T, false><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
+          assemble_kernel<T, false>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
                                                                         L.h * L.h * inv_tau * inv_s, inv_s, L.x,
                                                                         L.xo, G.lin_active, nullptr, (B4*)L.J,
-                                                                        L.plane, nullptr);
+                                                                        L.plane, nullptr, nullptr, nullptr);
       });
     }
     CKL();
@@ -761,7 +768,7 @@ int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, doub
   if (n_retry == 0) return HENRY_OK;
   H->nact = n_retry;
   double* pscratch = G.part + P_MAX * (int64_t)B * G.nct;
-  k_assemble<T, true, true, true><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+  assemble_kernel<T, true, true, true>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
       phys_of(c), G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
       G.lin_active, nullptr, (B4*)G.Jp, L.plane, pscratch, L.cc, L.fc);
   CKL();
@@ -803,14 +810,14 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
     launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
       if (L.cc)
-        k_assemble<T, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+        assemble_kernel<T, true, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
                                                              lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
                                                              G.newton_active, G.F, (B4*)L.J, L.plane, pmax, L.cc,
                                                              L.fc);
       else
-        k_assemble<T, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+        assemble_kernel<T, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
                                                        lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax);
+                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax, nullptr, nullptr);
     });
     launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
       k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
@@ -978,14 +985,14 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   Level& L = G.lv[0];
   if (L.cc)
-    k_assemble<T, true, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+    assemble_kernel<T, true, true>(H->cfg, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
         phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
         G.newton_active, G.F, (B4*)L.J, L.plane, G.part + P_MAX * (int64_t)n * G.nct, L.cc, L.fc);
   else
-    k_assemble<T, true><<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
+    assemble_kernel<T, true>(H->cfg, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
                                                                  lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
                                                                  G.newton_active, G.F, (B4*)L.J, L.plane,
-                                                                 G.part + P_MAX * (int64_t)n * G.nct);
+                                                                 G.part + P_MAX * (int64_t)n * G.nct, nullptr, nullptr);
   CKL();
   if (!coarse) return HENRY_OK;
   int rc = restrict_states<T>(H, G, n, true, G.lin_active, st);
@@ -1094,12 +1101,12 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
       H->nact = B;
       launch(H, st, HENRY_K_ASSEMBLE, (double)n0 * (48.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          k_assemble<double, true, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt,
+          assemble_kernel<double, true, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt,
                                                                   inv_s, L.x, L.xo, G.lin_active, G.F, (B4*)L.J,
                                                                   L.plane, pmax, L.cc, L.fc);
         else
-          k_assemble<double, true><<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s,
-                                                            L.x, L.xo, G.lin_active, G.F, (B4*)L.J, L.plane, pmax);
+          assemble_kernel<double, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s,
+                                                            L.x, L.xo, G.lin_active, G.F, (B4*)L.J, L.plane, pmax, nullptr, nullptr);
       });
       CKL();
       int rc;
@@ -1267,6 +1274,7 @@ void henry_default_config(henry_config* c) {
   c->adj_rtol = 1e-10;
   c->cuda_graphs = 1;
   c->qoi_set = HENRY_QOI_STANDARD;
+  c->tile_assembly = 1;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;

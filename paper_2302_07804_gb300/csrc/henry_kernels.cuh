@@ -173,6 +173,43 @@ __device__ __forceinline__ B4 mkblk(double a00, double a01, double a10, double a
   return b;
 }
 
+// Land (ix = 0) and seaside (ix = nx - 1) boundary terms of one cell, added
+// to its scaled residuals and centre block (assemble_cell and the tile
+// assembly share them).
+template <typename T, typename S, bool DROP>
+__device__ __forceinline__ void boundary_terms(const Phys& ph, double qin, double inv_s, S kmu, S PD, int nx, int ix,
+                                               int iy, S hS, S ihS, S rhoP, S pP, S cP, S& Rm, S& Rs, T& C00,
+                                               T& C01, T& C10, T& C11) {
+  const S drho = (S)ph.drho, rho0 = (S)ph.rho0;
+  const T kmuP_T = (T)kmu, PDP_T = (T)PD, hT = (T)hS, hdT = (T)(0.5 * ph.drho);
+  if (ix == 0) {  // land side: prescribed inflow of fresh water, c_b = 0
+    const S Fl = -rho0 * (S)(qin * inv_s) * hS;
+    const S rb = (S)0.5 * (rhoP + rho0);
+    const bool up = Fl >= (S)0;
+    Rm += Fl;
+    Rs += fma_(Fl, up ? cP : (S)0, (S)2 * rb * PD * cP);
+    C11 += (up ? (T)Fl : (T)0) + PDP_T * (T)fma_(drho, cP, (S)2 * rb);
+  }
+  if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
+    const S yP = ((S)iy + (S)0.5) * hS;
+    const S pb = (S)ph.rho1 * (S)ph.g * ((S)ph.Ly - yP);
+    const S rb = (S)0.5 * (rhoP + (S)ph.rho1);
+    const S q = -kmu * (pb - pP) * ((S)2 * ihS);
+    const S Fr = rb * q * hS;
+    const bool up = Fr >= (S)0;
+    const S cup = up ? cP : (S)1;
+    const S dif = PD * ((S)1 - cP);
+    Rm += Fr;
+    Rs += fma_(Fr, cup, -(S)2 * rb * dif);
+    const T dFdp = (T)2 * (T)rb * kmuP_T;
+    const T dFdc = DROP ? (T)0 : hdT * (T)q * hT;
+    C00 += dFdp;
+    C01 += dFdc;
+    C10 = fma_(dFdp, (T)cup, C10);
+    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDP_T));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // a4 (and coarse operators by rediscretisation): residual and Jacobian of one
 // cell.  `xs`, `xos` point at the cell arrays of one sample (storage layout;
@@ -266,32 +303,8 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     o.Nb[k][2] = -dFdp * cupT;
     o.Nb[k][3] = fma_(dFdc, cupT, (up ? (T)0 : FfT) - dGdifN);
   }
-  if (ix == 0) {  // land side: prescribed inflow of fresh water, c_b = 0
-    const S Fl = -rho0 * (S)(cf.qin * inv_s) * hS;
-    const S rb = (S)0.5 * (rhoP + rho0);
-    const bool up = Fl >= (S)0;
-    Rm += Fl;
-    Rs += fma_(Fl, up ? cP : (S)0, (S)2 * rb * PD * cP);
-    C11 += (up ? (T)Fl : (T)0) + PDP_T * (T)fma_(drho, cP, (S)2 * rb);
-  }
-  if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
-    const S yP = ((S)iy + (S)0.5) * hS;
-    const S pb = (S)ph.rho1 * (S)ph.g * ((S)ph.Ly - yP);
-    const S rb = (S)0.5 * (rhoP + (S)ph.rho1);
-    const S q = -kmu * (pb - pP) * ((S)2 * ihS);
-    const S Fr = rb * q * hS;
-    const bool up = Fr >= (S)0;
-    const S cup = up ? cP : (S)1;
-    const S dif = PD * ((S)1 - cP);
-    Rm += Fr;
-    Rs += fma_(Fr, cup, -(S)2 * rb * dif);
-    const T dFdp = (T)2 * (T)rb * kmuP_T;
-    const T dFdc = DROP ? (T)0 : hdT * (T)q * hT;
-    C00 += dFdp;
-    C01 += dFdc;
-    C10 = fma_(dFdp, (T)cup, C10);
-    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDP_T));
-  }
+  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C00, C01, C10,
+                             C11);
   o.fm = Rm;
   o.fs = Rs;
   o.C[0] = C00; o.C[1] = C01; o.C[2] = C10; o.C[3] = C11;
@@ -349,6 +362,193 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
     }
   }
   if (J) store_blocks<T>(J, plane, e, o.C, o.Nb);
+}
+
+// ---------------------------------------------------------------------------
+// a4, face-once form.  A face between a left/lower cell L and a right/upper
+// cell R carries the scaled mass and salt fluxes F, G from L to R; L's
+// residuals gain +F, +G and R's lose them, so R's derivative terms are the
+// negated ones of L.  The tile kernel evaluates each face once (assemble_cell
+// evaluates every interior face from both sides): the same arithmetic from
+// L's side, upwinding included (the tie F = 0 takes L's value, as the
+// oracle's face loop does).
+template <typename T, typename S>
+struct FaceData {
+  S F, G;   // fluxes L -> R (scaled)
+  T aL[4];  // d(F, G)/d(p_L, c_L): dF/dp, dF/dc, dG/dp, dG/dc
+  T aR[4];  // d(F, G)/d(p_R, c_R)
+};
+
+template <typename T, typename S, bool DROP>
+__device__ __forceinline__ void face_eval(const Phys& ph, S kmu_f, S PD_f, S sg, S hS, S ihS, double2 xL, double2 xR,
+                                          FaceData<T, S>& f) {
+  const S drho = (S)ph.drho, rho0 = (S)ph.rho0;
+  const S pL = (S)xL.x, cL = (S)xL.y, pR = (S)xR.x, cR = (S)xR.y;
+  const S rhoL = rho0 + drho * cL, rhoR = rho0 + drho * cR;
+  const S rhof = (S)0.5 * (rhoL + rhoR);
+  const S q = -kmu_f * fma_((pR - pL), ihS, sg * rhof);
+  const S Ff = rhof * q * hS;
+  const bool up = Ff >= (S)0;
+  const S cup = up ? cL : cR;
+  const S dif = PD_f * (cR - cL);
+  f.F = Ff;
+  f.G = fma_(Ff, cup, -rhof * dif);
+  const T kmuT = (T)kmu_f, PDT = (T)PD_f, hT = (T)hS, hdT = (T)(0.5 * ph.drho);
+  const T rhofT = (T)rhof, cupT = (T)cup, FfT = (T)Ff, difT = (T)dif;
+  const T dFdp = rhofT * kmuT;
+  const T dFdc = DROP ? (T)0 : hdT * hT * fma_((T)q, (T)1, -rhofT * kmuT * (T)sg);
+  const T dGdifL = fma_(hdT, difT, -rhofT * PDT);
+  const T dGdifR = fma_(hdT, difT, rhofT * PDT);
+  f.aL[0] = dFdp;
+  f.aL[1] = dFdc;
+  f.aL[2] = dFdp * cupT;
+  f.aL[3] = fma_(dFdc, cupT, (up ? FfT : (T)0) - dGdifL);
+  f.aR[0] = -dFdp;
+  f.aR[1] = dFdc;
+  f.aR[2] = -dFdp * cupT;
+  f.aR[3] = fma_(dFdc, cupT, (up ? (T)0 : FfT) - dGdifR);
+}
+
+// The residual and Jacobian of one cell from its faces' data (sgn = +1: the
+// cell is the face's L, -1: its R; k = 0 W, 1 E, 2 S, 3 N).
+template <typename T, typename S>
+__device__ __forceinline__ void add_face(const FaceData<T, S>& f, bool cell_is_L, int k, S& Rm, S& Rs, T C[4],
+                                         T Nb[4][4]) {
+  if (cell_is_L) {
+    Rm += f.F;
+    Rs += f.G;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      C[j] += f.aL[j];
+      Nb[k][j] = f.aR[j];
+    }
+  } else {
+    Rm -= f.F;
+    Rs -= f.G;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      C[j] -= f.aR[j];
+      Nb[k][j] = -f.aL[j];
+    }
+  }
+}
+
+// Tile assembly: a CTA holds TPB consecutive cells in storage order, i.e.
+// TPB / nx whole rows (nx <= TPB), possibly of several samples.  Phase 1:
+// every cell evaluates its east and north faces into shared memory.  Phase
+// 2: every cell sums its four faces (a cell of the tile's first row
+// evaluates the face below it itself: its other cell lies in another tile),
+// its accumulation and boundary terms, and stores F, the blocks and C^-1
+// like k_assemble (same arguments; FINE: N % TPB == 0, one sample per CTA).
+// Shared memory: 2 x TPB faces (40 KB in FP64).
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+__global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
+                                                       double h, double inv_h, double vt_s, double inv_s,
+                                                       const double2* __restrict__ x, const double2* __restrict__ xo,
+                                                       const int* __restrict__ active, double2* __restrict__ F,
+                                                       typename VT<T>::b4* __restrict__ J, int64_t plane,
+                                                       double* __restrict__ rmax_part,
+                                                       const double2* __restrict__ cc = nullptr,
+                                                       const double4_32a* __restrict__ fc = nullptr) {
+  typedef typename std::conditional<FINE, double, T>::type S;
+  __shared__ FaceData<T, S> fE[TPB], fN[TPB];
+  __shared__ double sh[40];
+  const int N = nx * ny;
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t total = (int64_t)B * N;
+  const int s = (int)(e / N);
+  if (FINE) {
+    if (!active[s]) return;  // uniform over the CTA
+  }
+  const bool on = e < total && active[s];
+  const int st = (int)(e - (int64_t)s * N);
+  int ix = 0, iy = 0;
+  xy_of(st, nx, ix, iy);
+  const int64_t base = e - st;
+  // tile slot of the cell (ix, row r of the tile); rows hold nx consecutive storage entries
+  const int r = threadIdx.x / nx;
+  const int slot = r * nx + ix;
+  const S hS = (S)h, ihS = (S)inv_h;
+  const Coef cf = on ? coef[s] : Coef{};
+  S kmu = (S)0, PD = (S)0, phi = (S)0;
+  if (on) {
+    if (FIELDS) {
+      const double2 c = cc[base + st];
+      phi = (S)c.x;
+      kmu = (S)(c.y * inv_s);
+      PD = (S)(c.x * ph.Dm * inv_s);
+    } else {
+      kmu = (S)(cf.kmu * inv_s);
+      PD = (S)(cf.PD * inv_s);
+      phi = (S)cf.phi;
+    }
+    const double2 xP = x[base + st];
+    if (ix + 1 < nx) {  // east face, P = L
+      S kf = kmu, pf = PD;
+      if (FIELDS) {
+        const double4_32a q = fc[base + st];
+        kf = (S)(q.x * inv_s);
+        pf = (S)(q.y * inv_s);
+      }
+      face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
+    }
+    if (iy + 1 < ny) {  // north face, P = L
+      S kf = kmu, pf = PD;
+      if (FIELDS) {
+        const double4_32a q = fc[base + st];
+        kf = (S)(q.z * inv_s);
+        pf = (S)(q.w * inv_s);
+      }
+      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
+    }
+  }
+  __syncthreads();
+  if (!on) return;
+  const double2 xP = x[base + st], xO = xo[base + st];
+  const S drho = (S)ph.drho, rho0 = (S)ph.rho0;
+  const S pP = (S)xP.x, cP = (S)xP.y, cO = (S)xO.y;
+  const S rhoP = rho0 + drho * cP;
+  const S rhoO = rho0 + drho * cO;
+  const S vt = (S)vt_s;
+  S Rm = phi * (rhoP - rhoO) * vt;
+  S Rs = phi * (rhoP * cP - rhoO * cO) * vt;
+  T C[4] = {(T)0, (T)(phi * drho * vt), (T)0, (T)(phi * (drho * cP + rhoP) * vt)};
+  T Nb[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = (T)0;
+  if (ix > 0) add_face<T, S>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);                     // W: P = R
+  if (ix + 1 < nx) add_face<T, S>(fE[slot], true, 1, Rm, Rs, C, Nb);                     // E: P = L
+  if (iy > 0) {  // S: P = R
+    if (r > 0) {
+      add_face<T, S>(fN[slot - nx], false, 2, Rm, Rs, C, Nb);
+    } else {  // the lower cell is in another tile: evaluate the face here
+      const int sb = st_of(ix, iy - 1, nx);
+      S kf = kmu, pf = PD;
+      if (FIELDS) {
+        const double4_32a q = fc[base + sb];
+        kf = (S)(q.z * inv_s);
+        pf = (S)(q.w * inv_s);
+      }
+      FaceData<T, S> fb;
+      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
+      add_face<T, S>(fb, false, 2, Rm, Rs, C, Nb);
+    }
+  }
+  if (iy + 1 < ny) add_face<T, S>(fN[slot], true, 3, Rm, Rs, C, Nb);                     // N: P = L
+  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
+                             C[3]);
+  if (FINE) {
+    const double fm = (double)Rm, fs = (double)Rs;
+    if (F) F[e] = make_double2(fm, fs);
+    double loc = fmax(fabs(fm), fabs(fs));
+    if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
+    const double bm = block_reduce<true>(loc, sh);
+    if (threadIdx.x == 0) {
+      const int nct = N / TPB;
+      rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
+    }
+  }
+  if (J) store_blocks<T>(J, plane, e, C, Nb);
 }
 
 // Coarse states: mean of the 2x2 children (both the iterate and the old state).

@@ -43,7 +43,8 @@ class HenryConfig(ctypes.Structure):
                 ("fused_small_grids", ctypes.c_int32), ("coef_model", ctypes.c_int32), ("kl_terms", ctypes.c_int32)] + \
                [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")] + \
                [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32), ("adj_rtol", ctypes.c_double),
-                ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32)]
+                ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32),
+                ("tile_assembly", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
