@@ -479,6 +479,11 @@ def field_level0(prm, grid, c):
     return c.reshape(prm.ny0, f, prm.nx0, f).mean(axis=(1, 3)).ravel()
 
 
+def series_stride(prm, grid):
+    """Fine steps per level-0 step (2^l at level l)."""
+    return grid.steps // prm.steps0
+
+
 def qoi_paper(prm, grid, coef, p, c, field=False):
     """The paper's QoIs at T (Sec. 2.2 and 4): salt mass and c(1.5, 0.25) as in
     ``qoi``, the freshwater integral Q_FW, c at the 12 points of Eq. (12points)
@@ -517,15 +522,21 @@ def coefficient_model(model):
 def solve_scenario(prm, level, xi, return_state=False, stats=None, model="uniform3", qoi_set=0):
     """All r_l implicit-Euler steps of one scenario at MLMC level ``level`` for
     random input ``xi``; returns the QoIs ((mass, c_point) for qoi_set 0,
-    ``qoi_paper`` for 1, with the level-0 field for 2) and a convergence flag."""
+    ``qoi_paper`` for 1, with the level-0 field for 2, with the freshwater
+    integral after every level-0 time step for 3) and a convergence flag."""
     grid = Grid.level(prm, level)
     coef = coefficient_model(model)(prm, grid, xi)
     p, c = initial_state(prm, grid)
     ok = True
-    for _ in range(grid.steps):
+    series = []
+    for n in range(grid.steps):
         p, c, conv = newton_step(prm, grid, coef, p, c, stats=stats)
         ok = ok and conv
+        if qoi_set == 3 and (n + 1) % series_stride(prm, grid) == 0:
+            series.append(freshwater_area(grid, c))  # Q_FW at the level-0 step times (Sec. 4)
     q = qoi(prm, grid, coef, p, c) if qoi_set == 0 else qoi_paper(prm, grid, coef, p, c, field=qoi_set == 2)
+    if qoi_set == 3:
+        q = np.concatenate([q, series])
     if return_state:
         return q, ok, (p, c)
     return q, ok

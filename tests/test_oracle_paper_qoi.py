@@ -72,3 +72,17 @@ def test_paper_preset_and_solve():
     assert 0.0 < q[2] < 2.0                 # salt has entered: less fresh water than the whole domain
     assert np.all((q[3:] >= -1e-12) & (q[3:] <= 1 + 1e-12))
     assert q[6] > q[3]                      # closer to the sea, saltier (same row, y = -0.95)
+
+
+def test_freshwater_series():
+    """Q_FW after every level-0 step (qoi_set 3): starts below the initial
+    2.0, ends at the final-time Q_FW, and at level 1 is recorded every second
+    fine step, at the same instants."""
+    xi = [0.2, -0.3, 0.4]
+    q0, ok0 = henry.solve_scenario(PRM, 0, xi, qoi_set=3)
+    q1, ok1 = henry.solve_scenario(PRM, 1, xi, qoi_set=3)
+    assert ok0 and ok1 and q0.shape == (15 + 20,) and q1.shape == (15 + 20,)
+    for q in (q0, q1):
+        assert q[-1] == q[2]
+        assert np.all(q[15:] <= 2.0) and q[15] < 2.0
+    assert np.all(np.diff(q0[15:]) <= 1e-12)   # salt only advances in this scenario
