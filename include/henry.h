@@ -91,8 +91,11 @@ enum { HENRY_MODEL_UNIFORM3 = 0, HENRY_MODEL_KL = 1, HENRY_MODEL_TWO_LAYER = 2 }
  *   y - Ly here) by bilinear interpolation of the surrounding cell centres.
  * PAPER_FIELD (15 + nx0 ny0): those 15 and the c field averaged over the cells
  *   of the level-0 grid, row-major; its MLMC mean and variance (mlmc_accumulate)
- *   are the paper's mean and variance fields (Sec. 4). */
-enum { HENRY_QOI_STANDARD = 0, HENRY_QOI_PAPER = 1, HENRY_QOI_PAPER_FIELD = 2 };
+ *   are the paper's mean and variance fields (Sec. 4).
+ * PAPER_SERIES (15 + steps0): the 15 of PAPER and Q_FW after every level-0 time
+ *   step (every 2^level fine steps, so the same instants at every level), the
+ *   paper's Q_FW(t) curves and crossing times (Sec. 4); the last one is [2]. */
+enum { HENRY_QOI_STANDARD = 0, HENRY_QOI_PAPER = 1, HENRY_QOI_PAPER_FIELD = 2, HENRY_QOI_PAPER_SERIES = 3 };
 
 /* Coarse-grid operators of the multigrid hierarchy. */
 enum { HENRY_COARSE_REDISCRETISE = 0, HENRY_COARSE_GALERKIN = 1 };
@@ -166,7 +169,7 @@ void henry_default_config(henry_config* cfg);
  * paper's QoIs (HENRY_QOI_PAPER).  Never fails. */
 void henry_paper_config(henry_config* cfg);
 
-/* QoIs per sample for cfg's qoi_set (2, 15 or 15 + nx0 ny0); -HENRY_EINVAL for a
+/* QoIs per sample for cfg's qoi_set (2, 15, 15 + nx0 ny0 or 15 + steps0); -HENRY_EINVAL for a
  * NULL pointer or an unknown set. */
 int henry_n_qoi(const henry_config* cfg);
 

@@ -310,7 +310,21 @@ auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, F
 }
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
 int qoi_count(const henry_config& c) {
-  return c.qoi_set == HENRY_QOI_STANDARD ? 2 : (c.qoi_set == HENRY_QOI_PAPER ? 15 : 15 + c.nx0 * c.ny0);
+  switch (c.qoi_set) {
+    case HENRY_QOI_STANDARD: return 2;
+    case HENRY_QOI_PAPER: return 15;
+    case HENRY_QOI_PAPER_FIELD: return 15 + c.nx0 * c.ny0;
+    default: return 15 + c.steps0;  // HENRY_QOI_PAPER_SERIES
+  }
+}
+// QoI set 3: Q_FW after the implicit step `step` (0-based) when it ends a
+// level-0 time step (every 2^level fine steps), into column 15 + k.
+void record_series(henry_handle* H, int level, int step, int B, int N, double h, const double2* x, double* qoi,
+                   const int* status, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  if (c.qoi_set != HENRY_QOI_PAPER_SERIES || (step + 1) % (1 << level) != 0) return;
+  const int k = (step + 1) / (1 << level) - 1;
+  k_qfw<<<B, TPB, 0, st>>>(B, N, h, x, qoi + 15 + k, qoi_count(c), status);
 }
 QoiSpec qoi_spec(const henry_config& c) { return QoiSpec{c.qoi_set, qoi_count(c), c.nx0, c.ny0, c.Lx, c.Ly}; }
 int n_inputs(const henry_config& c) { return c.coef_model == HENRY_MODEL_KL ? 2 * c.kl_terms + 1 : 3; }
@@ -870,6 +884,7 @@ int solve_group(henry_handle* H, Group<T>& G, int B, double* qoi, cudaStream_t s
   for (int step = 0; step < lg.steps; ++step) {
     const int rc = implicit_step<T>(H, G, B, step, st);
     if (rc) return rc;
+    record_series(H, G.level, step, B, L.N, lg.h, L.x, qoi, G.status, st);
   }
   launch(H, st, HENRY_K_QOI, (double)n0 * 16, [&] {
     k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc,
@@ -1070,6 +1085,7 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
     }
     int rc = implicit_step<double>(H, G, B, step, st);
     if (rc) return rc;
+    record_series(H, G.level, step, B, N, lg.h, L.x, qoi, G.status, st);
     CK(cudaMemcpyAsync(seg + (int64_t)(step % C) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
   }
   k_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, lg.h, c.rho0, c.rho1 - c.rho0, G.coef, L.x, qoi, L.cc,
@@ -1299,7 +1315,7 @@ void henry_paper_config(henry_config* c) {
 
 int henry_n_qoi(const henry_config* c) {
   if (!c) return -set_err(HENRY_EINVAL, "NULL argument");
-  if (c->qoi_set < HENRY_QOI_STANDARD || c->qoi_set > HENRY_QOI_PAPER_FIELD)
+  if (c->qoi_set < HENRY_QOI_STANDARD || c->qoi_set > HENRY_QOI_PAPER_SERIES)
     return -set_err(HENRY_EINVAL, "bad qoi_set");
   return qoi_count(*c);
 }
@@ -1320,7 +1336,7 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
     return set_err(HENRY_EINVAL, "bad coarse_op");
   if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
     return set_err(HENRY_EINVAL, "bad coef_model");
-  if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_FIELD) return set_err(HENRY_EINVAL, "bad qoi_set");
+  if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_SERIES) return set_err(HENRY_EINVAL, "bad qoi_set");
   if (c.coef_model == HENRY_MODEL_KL &&
       (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
        !(c.phi_lo < c.phi_hi)))

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, do
     out[3 + threadIdx.x] = (1 - fy) * ((1 - fx) * cell_c(xs, ix, iy, nx) + fx * cell_c(xs, ix + 1, iy, nx)) +
                            fy * ((1 - fx) * cell_c(xs, ix, iy + 1, nx) + fx * cell_c(xs, ix + 1, iy + 1, nx));
   }
-  if (Q.set < 2) return;
+  if (Q.set != 2) return;
   const int f = nx / Q.nx0;
   for (int c0 = threadIdx.x; c0 < Q.nx0 * Q.ny0; c0 += blockDim.x) {
     const int IY = c0 / Q.nx0, IX = c0 - IY * Q.nx0;
@@ -263,6 +263,19 @@ __global__ void __launch_bounds__(TPB) k_qoi(int B, int nx, int ny, double h, do
       for (int jx = 0; jx < f; ++jx) a += cell_c(xs, IX * f + jx, IY * f + jy, nx);
     out[15 + c0] = a / (double)(f * f);
   }
+}
+
+// The freshwater integral of Eq. (integral_fw) of the current state, one CTA
+// per sample, into out[s * stride] (the Q_FW(t) series of QoI set 3).
+__global__ void __launch_bounds__(TPB) k_qfw(int B, int N, double h, const double2* __restrict__ x,
+                                             double* __restrict__ out, int stride, const int* __restrict__ status) {
+  __shared__ double sh[40];
+  const int s = blockIdx.x;
+  const double2* xs = x + (int64_t)s * N;
+  double fresh = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) fresh += (xs[i].y <= 0.012178) ? 1.0 : 0.0;
+  fresh = block_reduce<false>(fresh, sh);
+  if (threadIdx.x == 0) out[(int64_t)s * stride] = status[s] == 0 ? fresh * h * h : 0.0;
 }
 
 // Natural layout [B][ny][nx] <-> storage layout (colour-split rows).

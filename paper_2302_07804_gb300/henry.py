@@ -18,7 +18,7 @@ HENRY_SAMPLE_OK, HENRY_SAMPLE_NEWTON, HENRY_SAMPLE_LINEAR, HENRY_SAMPLE_NONFINIT
 HENRY_FP64, HENRY_MIXED = 0, 1
 HENRY_COARSE_REDISCRETISE, HENRY_COARSE_GALERKIN = 0, 1
 HENRY_MODEL_UNIFORM3, HENRY_MODEL_KL, HENRY_MODEL_TWO_LAYER = 0, 1, 2
-HENRY_QOI_STANDARD, HENRY_QOI_PAPER, HENRY_QOI_PAPER_FIELD = 0, 1, 2
+HENRY_QOI_STANDARD, HENRY_QOI_PAPER, HENRY_QOI_PAPER_FIELD, HENRY_QOI_PAPER_SERIES = 0, 1, 2, 3
 N_QOI = 2
 N_XI = 3
 

@@ -127,12 +127,12 @@ def test_mlmc_rates_reject_bad_input(L):
 
 def test_qoi_sets_and_paper_config(L):
     from paper_2302_07804_gb300 import henry
-    for qs, nq in ((0, 2), (1, 15), (2, 15 + 32 * 16)):
+    for qs, nq in ((0, 2), (1, 15), (2, 15 + 32 * 16), (3, 15 + 20)):
         cfg = henry.default_config(qoi_set=qs)
         assert L.henry_n_qoi(ctypes.byref(cfg)) == nq
-    assert L.henry_n_qoi(ctypes.byref(henry.default_config(qoi_set=3))) == -henry.HENRY_EINVAL
+    assert L.henry_n_qoi(ctypes.byref(henry.default_config(qoi_set=4))) == -henry.HENRY_EINVAL
     with pytest.raises(henry.HenryError) as e:
-        henry.Solver(qoi_set=3)
+        henry.Solver(qoi_set=4)
     assert e.value.code == henry.HENRY_EINVAL
     kw = henry.paper_config()
     assert (kw["T"], kw["steps0"], kw["g"], kw["rho1"]) == (6016.0, 188, 9.8, 1024.99)

@@ -108,3 +108,25 @@ def test_uneven_batch_and_adjoint_with_wide_qoi_rows(hl):
     assert torch.equal(q1, ref)
     s.close()
     s0.close()
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_freshwater_series_matches_oracle(hl, level):
+    """QoI set 3: Q_FW after every level-0 time step.  Each instant may differ
+    from the oracle by at most one cell area (a cell within the states'
+    ~1e-12 difference of the threshold); the last entry is the final Q_FW."""
+    s = hl.Solver(qoi_set=hl.HENRY_QOI_PAPER_SERIES)
+    xi = hl.sample_xi(inputs.SEED, level, 680, 2)
+    q, _, st, _ = s.level_batch_solve(level, xi)
+    assert int(st.abs().sum()) == 0 and q.shape == (2, 35)
+    qn = q.cpu().numpy()
+    grid = ohenry.Grid.level(ohenry.Params(), level)
+    ref, ok = ohenry.solve_scenarios(ohenry.Params(), level, xi.cpu().numpy(), qoi_set=3)
+    assert ok.all()
+    assert np.all(np.abs(qn[:, 15:] - ref[:, 15:]) <= grid.h * grid.h + 1e-15)
+    assert np.array_equal(qn[:, -1], qn[:, 2])
+    np.testing.assert_allclose(qn[:, 3:15], ref[:, 3:15], rtol=0, atol=1e-10)
+    w = torch.tensor([[0.01, 1.0]] * 2, dtype=torch.float64, device="cuda")
+    _, qa, _ = s.adjoint(level, xi, w)
+    assert torch.equal(qa, q)
+    s.close()
