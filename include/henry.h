@@ -145,9 +145,9 @@ typedef struct {
                           updates) is captured once per workspace and batch size into a CUDA graph and
                           replayed; 0: plain launches.  Same values either way; off while profiling */
   int32_t qoi_set;     /* HENRY_QOI_* (default STANDARD); sets other than STANDARD use the multi-kernel path */
-  int32_t tile_assembly; /* 1 (default): grids at most 256 cells wide are assembled face-once, each tile of
-                            256 cells (whole rows) evaluating every face inside it once; 0: every cell
-                            evaluates its four faces.  Same values up to rounding */
+  int32_t tile_assembly; /* 1 (default): face-once assembly in tiles of 256 cells (whole rows up to 256 cells
+                            wide, else 128 x 2 blocks), every face inside a tile evaluated once; 0: every
+                            cell evaluates its four faces.  Same values up to rounding */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */

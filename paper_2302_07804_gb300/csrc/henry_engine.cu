@@ -301,12 +301,16 @@ void prof_drain(henry_handle* H) {
   P.pend.clear();
 }
 
-// The assembly kernel for a grid nx cells wide: the face-once tile form
-// where a tile of TPB cells holds whole rows (nx <= TPB), else the per-cell
-// form (same arguments, same results up to rounding).
+// The assembly kernel for a grid nx cells wide: the face-once tile form,
+// whole rows per tile where they fit (nx <= TPB), else 128 x 2 blocks; the
+// per-cell form with tile_assembly = 0 (same arguments, same results up to
+// rounding).
 template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
 auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, FINE, FIELDS, DROP>) {
-  return (c.tile_assembly && nx <= TPB) ? &k_assemble_tile<T, FINE, FIELDS, DROP> : &k_assemble<T, FINE, FIELDS, DROP>;
+  if (!c.tile_assembly) return &k_assemble<T, FINE, FIELDS, DROP>;
+  if (nx <= TPB) return &k_assemble_tile<T, FINE, FIELDS, DROP>;
+  if (nx % TILE_W == 0) return &k_assemble_tile2d<T, FINE, FIELDS, DROP>;  // N % TPB == 0 follows
+  return &k_assemble<T, FINE, FIELDS, DROP>;
 }
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
 int qoi_count(const henry_config& c) {

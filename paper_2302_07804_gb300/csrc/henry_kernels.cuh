@@ -551,6 +551,124 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
   if (J) store_blocks<T>(J, plane, e, C, Nb);
 }
 
+// Tile assembly for grids wider than TPB cells: a CTA covers a TW x (TPB /
+// TW) block of cells of one sample (TW = 128), mapped by position, not by
+// storage order.  Phase 1: every cell evaluates its east and north faces
+// into shared memory.  Phase 2: a cell takes its west and south faces from
+// the tile, or, on the tile's west or south edge, evaluates them itself.
+// About 2.5 face evaluations per cell.  The per-tile max |F| goes to slot
+// (tile index) of the sample's N / TPB partials.
+constexpr int TILE_W = 128;
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+__global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __restrict__ coef, int B, int nx,
+                                                         int ny, double h, double inv_h, double vt_s, double inv_s,
+                                                         const double2* __restrict__ x, const double2* __restrict__ xo,
+                                                         const int* __restrict__ active, double2* __restrict__ F,
+                                                         typename VT<T>::b4* __restrict__ J, int64_t plane,
+                                                         double* __restrict__ rmax_part,
+                                                         const double2* __restrict__ cc = nullptr,
+                                                         const double4_32a* __restrict__ fc = nullptr) {
+  typedef typename std::conditional<FINE, double, T>::type S;
+  constexpr int TH = TPB / TILE_W;
+  __shared__ FaceData<T, S> fE[TPB], fN[TPB];
+  __shared__ double sh[40];
+  const int N = nx * ny;
+  const int tiles = N / TPB;  // per sample
+  const int s = (int)(blockIdx.x / tiles);
+  const int tile = (int)(blockIdx.x - (int64_t)s * tiles);
+  if (s >= B || !active[s]) return;  // uniform over the CTA
+  const int tx = threadIdx.x % TILE_W, ty = threadIdx.x / TILE_W;
+  const int tpr = nx / TILE_W;  // tiles per row band
+  const int ix = (tile % tpr) * TILE_W + tx, iy = (tile / tpr) * TH + ty;
+  const int st = st_of(ix, iy, nx);
+  const int64_t base = (int64_t)s * N;
+  const int slot = threadIdx.x;
+  const S hS = (S)h, ihS = (S)inv_h;
+  const Coef cf = coef[s];
+  S kmu, PD, phi;
+  if (FIELDS) {
+    const double2 c = cc[base + st];
+    phi = (S)c.x;
+    kmu = (S)(c.y * inv_s);
+    PD = (S)(c.x * ph.Dm * inv_s);
+  } else {
+    kmu = (S)(cf.kmu * inv_s);
+    PD = (S)(cf.PD * inv_s);
+    phi = (S)cf.phi;
+  }
+  const double2 xP = x[base + st];
+  auto face_coef = [&](int owner, bool north, S& kf, S& pf) {
+    kf = kmu;
+    pf = PD;
+    if (FIELDS) {
+      const double4_32a q = fc[base + owner];
+      kf = (S)((north ? q.z : q.x) * inv_s);
+      pf = (S)((north ? q.w : q.y) * inv_s);
+    }
+  };
+  if (ix + 1 < nx) {  // east face, P = L
+    S kf, pf;
+    face_coef(st, false, kf, pf);
+    face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
+  }
+  if (iy + 1 < ny) {  // north face, P = L
+    S kf, pf;
+    face_coef(st, true, kf, pf);
+    face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
+  }
+  __syncthreads();
+  const double2 xO = xo[base + st];
+  const S drho = (S)ph.drho, rho0 = (S)ph.rho0;
+  const S pP = (S)xP.x, cP = (S)xP.y, cO = (S)xO.y;
+  const S rhoP = rho0 + drho * cP;
+  const S rhoO = rho0 + drho * cO;
+  const S vt = (S)vt_s;
+  S Rm = phi * (rhoP - rhoO) * vt;
+  S Rs = phi * (rhoP * cP - rhoO * cO) * vt;
+  T C[4] = {(T)0, (T)(phi * drho * vt), (T)0, (T)(phi * (drho * cP + rhoP) * vt)};
+  T Nb[4][4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = (T)0;
+  if (ix > 0) {  // W: P = R
+    if (tx > 0) {
+      add_face<T, S>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);
+    } else {
+      const int sw = st_of(ix - 1, iy, nx);
+      S kf, pf;
+      face_coef(sw, false, kf, pf);
+      FaceData<T, S> fw;
+      face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, x[base + sw], xP, fw);
+      add_face<T, S>(fw, false, 0, Rm, Rs, C, Nb);
+    }
+  }
+  if (ix + 1 < nx) add_face<T, S>(fE[slot], true, 1, Rm, Rs, C, Nb);  // E: P = L
+  if (iy > 0) {  // S: P = R
+    if (ty > 0) {
+      add_face<T, S>(fN[slot - TILE_W], false, 2, Rm, Rs, C, Nb);
+    } else {
+      const int sb = st_of(ix, iy - 1, nx);
+      S kf, pf;
+      face_coef(sb, true, kf, pf);
+      FaceData<T, S> fb;
+      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
+      add_face<T, S>(fb, false, 2, Rm, Rs, C, Nb);
+    }
+  }
+  if (iy + 1 < ny) add_face<T, S>(fN[slot], true, 3, Rm, Rs, C, Nb);  // N: P = L
+  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
+                             C[3]);
+  const int64_t e = base + st;
+  if (FINE) {
+    const double fm = (double)Rm, fs = (double)Rs;
+    if (F) F[e] = make_double2(fm, fs);
+    double loc = fmax(fabs(fm), fabs(fs));
+    if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
+    const double bm = block_reduce<true>(loc, sh);
+    if (threadIdx.x == 0) rmax_part[(int64_t)s * tiles + tile] = bm;
+  }
+  if (J) store_blocks<T>(J, plane, e, C, Nb);
+}
+
 // Coarse states: mean of the 2x2 children (both the iterate and the old state).
 __global__ void __launch_bounds__(TPB) k_restrict_state(int B, int ncx, int ncy, const double2* __restrict__ xf,
                                                         double2* __restrict__ xc, const int* __restrict__ active) {

@@ -138,3 +138,21 @@ def test_qoi_sets_and_paper_config(L):
     assert (kw["T"], kw["steps0"], kw["g"], kw["rho1"]) == (6016.0, 188, 9.8, 1024.99)
     assert kw["coef_model"] == henry.HENRY_MODEL_TWO_LAYER and kw["qoi_set"] == henry.HENRY_QOI_PAPER
     assert henry.Solver(**kw).n_qoi == 15
+
+
+def test_adjoint_and_rates_arguments_return_einval(L):
+    from paper_2302_07804_gb300 import henry
+    P = ctypes.c_void_p
+    s = henry.Solver()
+    adj = L.henry_adjoint
+    assert adj(None, 0, P(16), 1, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
+    assert adj(s._h, 0, P(16), 1, P(16), P(16), P(16), 0, P(16), None) == henry.HENRY_EINVAL
+    assert b"checkpoint_every" in L.henry_last_error()
+    assert adj(s._h, 0, P(16), 0, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
+    assert adj(s._h, 9, P(16), 1, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
+    assert adj(s._h, 0, None, 1, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
+    assert L.henry_n_qoi(None) == -henry.HENRY_EINVAL
+    s.close()
+    bad = henry.Solver(adj_rtol=0.0)
+    assert adj(bad._h, 0, P(16), 1, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
+    bad.close()

@@ -130,3 +130,25 @@ def test_autograd_function_calls_the_adjoint(hl):
     g, _, _ = s.adjoint(1, xi.detach(), w, checkpoint_every=10)
     assert torch.equal(xi.grad, g)
     s.close()
+
+
+def test_nonfinite_sample_is_isolated(hl):
+    """A sample with a non-finite input fails alone: status 3 and a zero
+    gradient for it, and every other sample bit-identical to a batch
+    without it (adjoint and uneven batch)."""
+    s = hl.Solver()
+    xi = hl.sample_xi(inputs.SEED, 0, 840, 4).clone()
+    xi[2, 1] = float("nan")
+    w = _dev(W4)
+    g, q, st = s.adjoint(0, xi, w, allow_failures=True)
+    assert st.tolist() == [0, 0, 3, 0]
+    assert bool((g[2] == 0).all())
+    keep = torch.tensor([0, 1, 3], device="cuda")
+    g2, q2, st2 = s.adjoint(0, xi[keep].contiguous(), w[keep].contiguous())
+    assert torch.equal(g[keep], g2) and torch.equal(q[keep], q2)
+    levels = np.array([0, 1, 0, 1], dtype=np.int32)
+    qf, qc, stm, stats = s.batch_solve_mixed(levels, xi, with_coarse=True, allow_failures=True)
+    assert stm.tolist() == [0, 0, 3, 0] and stats["failed_samples"] == 1
+    a, _, _, _ = s.level_batch_solve(1, xi[[1, 3]].contiguous(), with_coarse=True)
+    assert torch.equal(qf[[1, 3]], a)
+    s.close()

@@ -360,3 +360,41 @@ def test_cuda_graphs_give_identical_results(hl):
         grads.append(s.adjoint(0, xi0, w, checkpoint_every=6)[0])
         s.close()
     assert torch.equal(grads[0], grads[1])
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_tile_assembly_equals_per_cell_assembly_on_wide_grids(hl, model):
+    """Grids wider than 256 cells (level 4: 512 x 256) are assembled face-once
+    in 128 x 2 tiles with halo faces on the tiles' west and south edges; the
+    residual and every Jacobian block equal the per-cell form's to rounding,
+    for the three-parameter and the KL model, and full solves agree."""
+    level, n = 4, 2
+    if model == 1:
+        gen = inputs.rng(860)
+        xi = torch.as_tensor(np.concatenate([gen.standard_normal((n, 64)), gen.uniform(-1, 1, (n, 1))], axis=1),
+                             dtype=torch.float64, device="cuda")
+    else:
+        xi = hl.sample_xi(inputs.SEED, level, 860, n)
+    grid = ohenry.Grid.level(PRM, level)
+    p, c = inputs.random_states(861, 2 * n, grid.ny, grid.nx, 5e3, 1e4, 300.0)
+    st = torch.as_tensor(np.stack([p[:n], c[:n]], axis=-1), dtype=torch.float64, device="cuda")
+    so = torch.as_tensor(np.stack([p[n:], c[n:]], axis=-1), dtype=torch.float64, device="cuda")
+    out = []
+    for tile in (1, 0):
+        s = hl.Solver(coef_model=model, tile_assembly=tile)
+        F, J = s.assemble(level, xi, st, so)
+        out.append((F.cpu().numpy(), J.cpu().numpy()))
+        s.close()
+    (F1, J1), (F0, J0) = out
+    np.testing.assert_allclose(F1, F0, rtol=0, atol=1e-12 * np.abs(F0).max())
+    for k in range(5):
+        np.testing.assert_allclose(J1[..., k, :, :], J0[..., k, :, :], rtol=0,
+                                   atol=1e-12 * np.abs(J0[..., k, :, :]).max())
+    if model == 0:
+        q = []
+        for tile in (1, 0):
+            s = hl.Solver(tile_assembly=tile)
+            q.append(s.level_batch_solve(level, xi)[0].cpu().numpy())
+            s.close()
+        np.testing.assert_allclose(q[0][:, 0], q[1][:, 0], rtol=1e-11, atol=0)
+        np.testing.assert_allclose(q[0][:, 1], q[1][:, 1], rtol=0, atol=1e-11)
