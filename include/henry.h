@@ -333,7 +333,9 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
  * device looks up the array's device address (cudaGetSymbolAddress with that
  * device current): make that first call before any stream capture.  All
  * calls share the array and host counter words; calls that overlap on the GPU
- * or across host threads race.  Synchronises `stream`. */
+ * or across host threads race.  Only the three-parameter model and the two
+ * standard QoIs (qoi_set 0) are accepted (HENRY_EINVAL otherwise).
+ * Synchronises `stream`. */
 #define HENRY_STATIC_SCRATCH_BYTES (16u << 20)
 int henry_level_batch_solve_static(const henry_config* cfg, int level, int with_coarse, const double* xi_dev, int n,
                                    double* qoi_fine_dev, double* qoi_coarse_dev, int32_t* status_dev, void* stream);
