@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -364,7 +365,9 @@ size_t bytes_per_sample(const henry_config& c, int level, bool light = false) {
 // The fused one-CTA-per-sample solver is used when enabled, the sample's
 // hierarchy fits the shared-memory layout and the device grants that much
 // shared memory per CTA.
-int g_smem_optin[64] = {};
+// (atomic: the levels of henry_batch_solve_mixed reach here from concurrent
+// host threads; every thread stores the same attribute value)
+std::atomic<int> g_smem_optin[64] = {};
 template <typename T>
 bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   // 1 (default): only with FP32 linear algebra, where it measured faster; on
@@ -376,12 +379,12 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   if (!cta_layout(lg.nx, lg.ny, (int)sizeof(T), L)) return false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-  if (!g_smem_optin[dev]) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    g_smem_optin[dev] = v;
+  int optin = g_smem_optin[dev].load(std::memory_order_relaxed);
+  if (!optin) {
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    g_smem_optin[dev].store(optin, std::memory_order_relaxed);
   }
-  return L->bytes <= g_smem_optin[dev];
+  return L->bytes <= optin;
 }
 
 template <typename T>
