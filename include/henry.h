@@ -59,7 +59,9 @@ enum {
 enum {
   HENRY_SAMPLE_OK = 0,
   HENRY_SAMPLE_NEWTON = 1,   /* Newton did not converge within newton_maxit in some step */
-  HENRY_SAMPLE_LINEAR = 2,   /* BiCGStab hit lin_maxit or broke down in some Newton iteration */
+  HENRY_SAMPLE_LINEAR = 2,   /* henry_adjoint: an adjoint system J^T lam = rhs did not converge within
+                                adj_maxit (a forward BiCGStab that stops early leaves Newton's residual
+                                test to decide, so forward solves report 1 or 3 instead) */
   HENRY_SAMPLE_NONFINITE = 3 /* a residual or coefficient was NaN or infinite */
 };
 
