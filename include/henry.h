@@ -171,6 +171,16 @@ void henry_default_config(henry_config* cfg);
  * paper's QoIs (HENRY_QOI_PAPER).  Never fails. */
 void henry_paper_config(henry_config* cfg);
 
+/* The KL basis of HENRY_MODEL_KL for cfg (kl_terms, kl_corr_len, Lx, Ly): the
+ * square roots of the eigenvalues, sqrt_lam[kl_terms], and, if modes is not
+ * NULL, the modes psi_t at the cell centres of `level`, modes[kl_terms][ny][nx]
+ * (row-major), so that log K = log K_mean + sigma_K sum_t sqrt_lam[t] theta_K[t]
+ * psi_t (and likewise phi before its clip).  Use it to turn henry_adjoint's
+ * dQ/dtheta into fields.  The same host computation as the solves' (Nystrom
+ * on 256 Gauss-Legendre nodes, cyclic Jacobi).  Host only, no GPU; EINVAL on
+ * NULL or bad settings. */
+int henry_kl_basis(const henry_config* cfg, int level, double* sqrt_lam, double* modes);
+
 /* QoIs per sample for cfg's qoi_set (2, 15, 15 + nx0 ny0 or 15 + steps0); -HENRY_EINVAL for a
  * NULL pointer or an unknown set. */
 int henry_n_qoi(const henry_config* cfg);

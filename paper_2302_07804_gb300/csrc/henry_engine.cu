@@ -1320,6 +1320,32 @@ void henry_paper_config(henry_config* c) {
   c->qoi_set = HENRY_QOI_PAPER;
 }
 
+int henry_kl_basis(const henry_config* cfg, int level, double* sqrt_lam, double* modes) {
+  if (!cfg || !sqrt_lam) return set_err(HENRY_EINVAL, "NULL argument");
+  const henry_config& c = *cfg;
+  if (level < 0 || level > c.max_level) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, c.max_level);
+  if (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.Lx > 0) || !(c.Ly > 0) || c.nx0 <= 0 ||
+      c.ny0 <= 0)
+    return set_err(HENRY_EINVAL, "bad random-field settings");
+  hkl::Basis2D b;
+  b.build(c.Lx, c.Ly, c.kl_terms, c.kl_corr_len);
+  for (int t = 0; t < b.terms; ++t) sqrt_lam[t] = b.sqrt_lam[t];
+  if (modes) {
+    const LevelGeom lg = geom(c, level);
+    std::vector<double> px((size_t)b.bx.m * lg.nx), py((size_t)b.by.m * lg.ny);
+    for (int i = 0; i < b.bx.m; ++i)
+      for (int ix = 0; ix < lg.nx; ++ix) px[(size_t)i * lg.nx + ix] = b.bx.eval(i, (ix + 0.5) * lg.h);
+    for (int j = 0; j < b.by.m; ++j)
+      for (int iy = 0; iy < lg.ny; ++iy) py[(size_t)j * lg.ny + iy] = b.by.eval(j, (iy + 0.5) * lg.h);
+    for (int t = 0; t < b.terms; ++t)
+      for (int iy = 0; iy < lg.ny; ++iy)
+        for (int ix = 0; ix < lg.nx; ++ix)
+          modes[((size_t)t * lg.ny + iy) * lg.nx + ix] =
+              py[(size_t)b.tj[t] * lg.ny + iy] * px[(size_t)b.ti[t] * lg.nx + ix];
+  }
+  return HENRY_OK;
+}
+
 int henry_n_qoi(const henry_config* c) {
   if (!c) return -set_err(HENRY_EINVAL, "NULL argument");
   if (c->qoi_set < HENRY_QOI_STANDARD || c->qoi_set > HENRY_QOI_PAPER_SERIES)

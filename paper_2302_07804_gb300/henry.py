@@ -26,7 +26,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint", "henry_n_qoi",
-           "henry_paper_config")
+           "henry_paper_config", "henry_kl_basis")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
 
@@ -79,6 +79,7 @@ def lib():
         L.henry_paper_config.argtypes = [ctypes.POINTER(HenryConfig)]
         L.henry_paper_config.restype = None
         L.henry_n_qoi.argtypes = [ctypes.POINTER(HenryConfig)]
+        L.henry_kl_basis.argtypes = [ctypes.POINTER(HenryConfig), I, P, P]
         L.henry_create.argtypes = [ctypes.POINTER(HenryConfig), ctypes.POINTER(P)]
         L.henry_destroy.argtypes = [P]
         L.henry_destroy.restype = None
@@ -150,6 +151,19 @@ def paper_config(**overrides):
     kw = {name: getattr(cfg, name) for name, _ in HenryConfig._fields_}
     kw.update(overrides)
     return kw
+
+
+def kl_basis(level, **overrides):
+    """henry_kl_basis (host): (sqrt_lam[kl_terms], modes[kl_terms][ny][nx]) as
+    numpy arrays for the configuration with ``overrides``."""
+    import numpy as np
+    cfg = default_config(**overrides)
+    ny, nx = cfg.ny0 << level, cfg.nx0 << level
+    sl = np.empty(cfg.kl_terms)
+    modes = np.empty((cfg.kl_terms, ny, nx))
+    _check(lib().henry_kl_basis(ctypes.byref(cfg), level, sl.ctypes.data_as(ctypes.c_void_p),
+                                modes.ctypes.data_as(ctypes.c_void_p)))
+    return sl, modes
 
 
 def sample_xi(seed, level, first_sample, n, device="cuda", stream=None):

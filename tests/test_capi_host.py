@@ -156,3 +156,25 @@ def test_adjoint_and_rates_arguments_return_einval(L):
     bad = henry.Solver(adj_rtol=0.0)
     assert adj(bad._h, 0, P(16), 1, P(16), P(16), P(16), 20, P(16), None) == henry.HENRY_EINVAL
     bad.close()
+
+
+def test_kl_basis_matches_oracle(L):
+    """The library's KL basis (its own cyclic-Jacobi Nystrom eigensolver, the
+    one the solves use) against the oracle's (LAPACK through scipy): the same
+    eigenvalues, term order and modes at the cell centres."""
+    import numpy as np
+    from oracle import henry as ohenry
+    from oracle import kl as okl
+    from paper_2302_07804_gb300 import henry
+    basis = okl.KLBasis()
+    for level in (0, 2):
+        sl, modes = henry.kl_basis(level)
+        grid = ohenry.Grid.level(ohenry.Params(), level)
+        xc = (np.arange(grid.nx) + 0.5) * grid.h
+        yc = (np.arange(grid.ny) + 0.5) * grid.h
+        np.testing.assert_allclose(sl, np.sqrt(basis.lam), rtol=1e-10)
+        np.testing.assert_allclose(modes, basis.modes(xc, yc), rtol=0, atol=1e-9)
+    P = ctypes.c_void_p
+    assert L.henry_kl_basis(None, 0, P(16), None) == henry.HENRY_EINVAL
+    cfg = henry.default_config()
+    assert L.henry_kl_basis(ctypes.byref(cfg), 9, P(16), None) == henry.HENRY_EINVAL
