@@ -334,7 +334,21 @@ class Workload:
     def _level_solvers(self):
         if self.solvers is None:
             self.solvers = [self.h.Solver(precision=self.precision, **self.solver_kw) for _ in range(self.L)]
+            for l, s in enumerate(self.solvers):  # the same settings as the timed handle
+                for k in (l, l - 1):
+                    if k >= 0:
+                        s.set_tuning(k, self.solver.tuning(k))
         return self.solvers
+
+    def autotune(self, seed, trial_cap=4096):
+        """henry_autotune per level on trial batches drawn beyond the bench's
+        counters (untimed); returns {level: settings}."""
+        out = {}
+        for l in range(self.L):
+            n = max(1, min(self.alloc[l], trial_cap))
+            trial = self.h.sample_xi(seed, l, 5 * 10 ** 7, n, device=self.dev)
+            out[l] = self.solver.autotune(l, trial, with_coarse=self.with_coarse and l > 0)
+        return out
 
     def _run_sequential(self, xi, stream):
         for l in range(self.L):
@@ -562,6 +576,7 @@ def main():
     ap.add_argument("--set", action="append", default=[], metavar="KEY=VALUE",
                     help="with --case / uneven / kl-mixed / adjoint: override a henry_config field")
     ap.add_argument("--adjoint-batch", type=int, default=1024)
+    ap.add_argument("--no-tune", action="store_true", help="skip henry_autotune before the timed MLMC steps")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -598,6 +613,7 @@ def main():
     xis = [[henry.sample_xi(seed, l, 10 ** 7 + k * alloc[l], alloc[l], device=dev) for l in range(MAX_LEVEL + 1)]
            for k in range(nsteps_all)]
     W = Workload(henry, torch, dev, alloc, prec, xis)
+    tuning = {} if args.no_tune else W.autotune(seed)
     stream = torch.cuda.current_stream()
 
     def step(k):
@@ -656,7 +672,9 @@ def main():
                        "levels_concurrent": "one henry_batch_solve_mixed call per step (one stream, child "
                                             "handle and host thread per level)",
                        "l2": "working set > L2 (level-0 batch alone is GBs); no flush needed",
-                       "failed_samples": W.fails},
+                       "failed_samples": W.fails,
+                       "tuning": ({str(l): t for l, t in tuning.items()} if tuning else "configuration defaults"),
+                       "tuning_note": "henry_autotune per level on untimed trial batches before the timed region"},
             "e2e": {"value": e2e, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "iterations": W.iteration_means(),
             "clocks": clk.summary()}

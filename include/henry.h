@@ -171,6 +171,33 @@ void henry_default_config(henry_config* cfg);
  * paper's QoIs (HENRY_QOI_PAPER).  Never fails. */
 void henry_paper_config(henry_config* cfg);
 
+/* Project autotuner.  Solver settings that change only how fast a solve
+ * converges, never where (the FP64 Newton test decides): the Krylov tolerance,
+ * the V-cycle's smoothing counts and, where the level's grid allows it, the
+ * fused one-CTA-per-sample solver.  henry_autotune times every candidate -
+ * lin_rtol in {1e-4, 1e-3, 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x
+ * (fused small-grid solver on / off where eligible) - on n_trial samples
+ * xi_dev[n_trial][n_xi] of `level` (with their coarse partners if
+ * with_coarse), after one untimed warm-up, with CUDA events on `stream`, and
+ * keeps the fastest candidate that solves every sample for that level of
+ * this handle: henry_level_batch_solve and henry_batch_solve_mixed use it from
+ * then on (henry_adjoint keeps the configuration's settings).  QoIs move only
+ * within the Newton tolerance.  Allocates its trial outputs; synchronises
+ * `stream`.  best_out (nullable) receives the choice with its measured rate.
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOCONV (no candidate solved every sample). */
+typedef struct {
+  double lin_rtol;
+  int32_t nu1, nu2, fused_small_grids;
+  double cell_steps_per_s; /* measured on the trial batch (0 for the configuration's own settings) */
+} henry_tuning;
+int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
+                   henry_tuning* best_out, void* stream);
+/* The settings a level's solves use: henry_autotune's choice, else the configuration's. */
+int henry_get_tuning(henry_handle* h, int level, henry_tuning* out);
+/* Give a level these settings (for example another handle's henry_autotune
+ * choice); NULL returns the level to the configuration's.  EINVAL on bad values. */
+int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t);
+
 /* The KL basis of HENRY_MODEL_KL for cfg (kl_terms, kl_corr_len, Lx, Ly): the
  * square roots of the eigenvalues, sqrt_lam[kl_terms], and, if modes is not
  * NULL, the modes psi_t at the cell centres of `level`, modes[kl_terms][ny][nx]

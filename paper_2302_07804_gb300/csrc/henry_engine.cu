@@ -25,6 +25,7 @@
 #include <map>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "henry.h"
@@ -111,7 +112,7 @@ struct Group {
   // Instantiated CUDA graphs of one BiCGStab iteration's body, by (batch
   // size, preconditioner operator); they hold this workspace's pointers and
   // are dropped with it.
-  std::map<std::pair<int, const void*>, cudaGraphExec_t> gexec;
+  std::map<std::tuple<int, const void*, int, int>, cudaGraphExec_t> gexec;  // (B, preconditioner, nu1, nu2)
   bool graphs = true;  // false: never capture (the allocation-free entry point)
   void drop_graphs() {
     for (auto& kv : gexec) cudaGraphExecDestroy(kv.second);
@@ -238,6 +239,7 @@ struct henry_handle {
   char* adj_mem = nullptr;
   size_t adj_bytes = 0;
   cudaStream_t cap_stream = nullptr;  // CUDA-graph capture
+  std::map<int, henry_tuning> tuned;  // henry_autotune's choices per level
 };
 
 namespace {
@@ -730,7 +732,7 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
   // launched on `st`.  Off while the kernel timer runs.
   const bool use_graph = H->cfg.cuda_graphs && G.graphs && !H->prof.on;
   auto run_graph = [&]() -> int {
-    const auto key = std::make_pair(B, Jpre0);
+    const auto key = std::make_tuple(B, Jpre0, H->cfg.nu1, H->cfg.nu2);
     auto f = G.gexec.find(key);
     if (f == G.gexec.end()) {
       if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
@@ -945,9 +947,25 @@ int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, d
   return HENRY_OK;
 }
 
+// The level's autotuned settings (henry_autotune) in force for one scope.
+struct TuningScope {
+  henry_handle* H;
+  henry_config saved;
+  TuningScope(henry_handle* h, int level) : H(h), saved(h->cfg) {
+    auto f = h->tuned.find(level);
+    if (f == h->tuned.end()) return;
+    h->cfg.lin_rtol = f->second.lin_rtol;
+    h->cfg.nu1 = f->second.nu1;
+    h->cfg.nu2 = f->second.nu2;
+    h->cfg.fused_small_grids = f->second.fused_small_grids;
+  }
+  ~TuningScope() { H->cfg = saved; }
+};
+
 template <typename T>
 int batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status, bool first,
                       henry_stats* stats, cudaStream_t st) {
+  TuningScope tuning(H, level);
   CtaLayout CL;
   const bool fused = fused_eligible<T>(H->cfg, level, &CL);
   const int Bmax = max_batch<T>(H->cfg, level, fused);
@@ -1320,6 +1338,117 @@ void henry_paper_config(henry_config* c) {
   c->qoi_set = HENRY_QOI_PAPER;
 }
 
+int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
+  if (!h) return set_err(HENRY_EINVAL, "NULL handle");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  if (!t) {
+    h->tuned.erase(level);
+    return HENRY_OK;
+  }
+  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0)
+    return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d)", t->lin_rtol, t->nu1, t->nu2);
+  h->tuned[level] = *t;
+  return HENRY_OK;
+}
+
+int henry_get_tuning(henry_handle* h, int level, henry_tuning* out) {
+  if (!h || !out) return set_err(HENRY_EINVAL, "NULL argument");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  auto f = h->tuned.find(level);
+  if (f != h->tuned.end()) {
+    *out = f->second;
+  } else {
+    std::memset(out, 0, sizeof *out);
+    out->lin_rtol = h->cfg.lin_rtol;
+    out->nu1 = h->cfg.nu1;
+    out->nu2 = h->cfg.nu2;
+    out->fused_small_grids = h->cfg.fused_small_grids;
+  }
+  return HENRY_OK;
+}
+
+int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
+                   henry_tuning* best_out, void* stream) {
+  if (!h || !xi_dev) return set_err(HENRY_EINVAL, "NULL argument");
+  if (!valid_level(h, level)) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, h->cfg.max_level);
+  if (n_trial <= 0) return set_err(HENRY_EINVAL, "n_trial = %d must be positive", n_trial);
+  if (with_coarse && level == 0) return set_err(HENRY_EINVAL, "level 0 has no coarse partner");
+  cudaStream_t st = (cudaStream_t)stream;
+  const henry_config& c = h->cfg;
+  const int nq = qoi_count(c);
+  char* mem = nullptr;
+  const size_t qbytes = sizeof(double) * (size_t)n_trial * nq;
+  if (cudaMalloc(&mem, 2 * qbytes + sizeof(int32_t) * (size_t)n_trial) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(HENRY_ENOMEM, "cudaMalloc for the autotuner's trial outputs failed");
+  }
+  double* qf = (double*)mem;
+  double* qc = (double*)(mem + qbytes);
+  int32_t* sd = (int32_t*)(mem + 2 * qbytes);
+  std::vector<henry_tuning> cands;
+  const double rts[3] = {1e-4, 1e-3, 1e-2};
+  const int nus[3][2] = {{2, 2}, {1, 2}, {2, 1}};
+  CtaLayout CL;
+  const bool can_fuse = (c.precision == HENRY_MIXED ? fused_eligible<float>(c, level, &CL)
+                                                    : fused_eligible<double>(c, level, &CL)) ||
+                        (c.fused_small_grids == 0);
+  for (double rt : rts)
+    for (auto& nu : nus)
+      for (int fz = 0; fz < 2; ++fz) {
+        if (fz == 1 && !can_fuse) continue;
+        henry_tuning t;
+        std::memset(&t, 0, sizeof t);
+        t.lin_rtol = rt;
+        t.nu1 = nu[0];
+        t.nu2 = nu[1];
+        t.fused_small_grids = can_fuse ? (fz == 0 ? 0 : 1) : c.fused_small_grids;
+        cands.push_back(t);
+      }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = HENRY_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = HENRY_ECUDA;
+  const LevelGeom lg = geom(c, level);
+  double cs = (double)n_trial * lg.nx * lg.ny * lg.steps;
+  if (with_coarse) {
+    const LevelGeom lc = geom(c, level - 1);
+    cs += (double)n_trial * lc.nx * lc.ny * lc.steps;
+  }
+  h->tuned.erase(level);
+  int best = -1;
+  double best_rate = 0.0;
+  for (int i = -1; i < (int)cands.size() && !rc; ++i) {  // i = -1: warm-up (workspaces, graphs)
+    if (i >= 0) h->tuned[level] = cands[i];
+    cudaEventRecord(e0, st);
+    rc = henry_level_batch_solve(h, level, with_coarse, xi_dev, n_trial, qf, with_coarse ? qc : nullptr, sd, nullptr,
+                                 st);
+    cudaEventRecord(e1, st);
+    if (rc == HENRY_ENOCONV) {  // a candidate that loses samples is not a candidate
+      rc = HENRY_OK;
+      continue;
+    }
+    if (rc) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (i >= 0 && ms > 0.f) {
+      cands[i].cell_steps_per_s = cs / (ms * 1e-3);
+      if (cands[i].cell_steps_per_s > best_rate) {
+        best_rate = cands[i].cell_steps_per_s;
+        best = i;
+      }
+    }
+  }
+  h->tuned.erase(level);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(mem);
+  if (rc) return rc;
+  if (best < 0) return set_err(HENRY_ENOCONV, "no candidate solved every trial sample");
+  h->tuned[level] = cands[best];
+  if (best_out) *best_out = cands[best];
+  return HENRY_OK;
+}
+
 int henry_kl_basis(const henry_config* cfg, int level, double* sqrt_lam, double* modes) {
   if (!cfg || !sqrt_lam) return set_err(HENRY_EINVAL, "NULL argument");
   const henry_config& c = *cfg;
@@ -1512,6 +1641,7 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
       h->kid_streams[l] = ls;
     }
     henry_handle* k = h->kids[l];
+    k->tuned = h->tuned;
     if (k->prof.on != h->prof.on) {
       const int rc = henry_profile(k, h->prof.on ? 1 : 0);
       if (rc) return rc;

@@ -26,7 +26,8 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_level_batch_solve", "mlmc_accumulate", "mlmc_allocate", "henry_assemble",
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint", "henry_n_qoi",
-           "henry_paper_config", "henry_kl_basis")
+           "henry_paper_config", "henry_kl_basis", "henry_autotune", "henry_get_tuning",
+           "henry_set_tuning")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
 
@@ -65,6 +66,15 @@ class HenryError(RuntimeError):
 _lib = None
 
 
+class HenryTuning(ctypes.Structure):
+    """henry_tuning: a level's solver settings chosen by henry_autotune."""
+    _fields_ = [("lin_rtol", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+                ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def lib():
     """Load libhenry.so (built by ``paper_2302_07804_gb300.build``); raises if absent."""
     global _lib
@@ -80,6 +90,9 @@ def lib():
         L.henry_paper_config.restype = None
         L.henry_n_qoi.argtypes = [ctypes.POINTER(HenryConfig)]
         L.henry_kl_basis.argtypes = [ctypes.POINTER(HenryConfig), I, P, P]
+        L.henry_autotune.argtypes = [P, I, I, P, I, ctypes.POINTER(HenryTuning), P]
+        L.henry_get_tuning.argtypes = [P, I, ctypes.POINTER(HenryTuning)]
+        L.henry_set_tuning.argtypes = [P, I, ctypes.POINTER(HenryTuning)]
         L.henry_create.argtypes = [ctypes.POINTER(HenryConfig), ctypes.POINTER(P)]
         L.henry_destroy.argtypes = [P]
         L.henry_destroy.restype = None
@@ -334,6 +347,32 @@ class Solver:
                                  int(checkpoint_every), _ptr(st), _stream(stream))
         _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
         return grad, qoi, st
+
+    def autotune(self, level, xi, with_coarse=False, stream=None):
+        """henry_autotune: time the candidate settings on the trial batch xi and
+        keep the fastest for this level; returns it as a dict."""
+        n = xi.shape[0]
+        _dev_f64(xi, (n, self.n_xi))
+        t = HenryTuning()
+        _check(lib().henry_autotune(self._h, level, 1 if with_coarse else 0, _ptr(xi), n, ctypes.byref(t),
+                                    _stream(stream)))
+        return t.as_dict()
+
+    def set_tuning(self, level, tuning):
+        """henry_set_tuning: a dict as returned by tuning() / autotune(), or None."""
+        if tuning is None:
+            _check(lib().henry_set_tuning(self._h, level, None))
+            return
+        t = HenryTuning()
+        for k, _ in HenryTuning._fields_:
+            setattr(t, k, tuning.get(k, 0))
+        _check(lib().henry_set_tuning(self._h, level, ctypes.byref(t)))
+
+    def tuning(self, level):
+        """The settings this level's solves use (henry_get_tuning)."""
+        t = HenryTuning()
+        _check(lib().henry_get_tuning(self._h, level, ctypes.byref(t)))
+        return t.as_dict()
 
     def _states(self, level, state, state_old):
         ny, nx = self.grid(level)

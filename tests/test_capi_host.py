@@ -178,3 +178,17 @@ def test_kl_basis_matches_oracle(L):
     assert L.henry_kl_basis(None, 0, P(16), None) == henry.HENRY_EINVAL
     cfg = henry.default_config()
     assert L.henry_kl_basis(ctypes.byref(cfg), 9, P(16), None) == henry.HENRY_EINVAL
+
+
+def test_autotune_arguments_return_einval(L):
+    from paper_2302_07804_gb300 import henry
+    P = ctypes.c_void_p
+    s = henry.Solver()
+    t = henry.HenryTuning()
+    assert L.henry_autotune(None, 0, 0, P(16), 4, ctypes.byref(t), None) == henry.HENRY_EINVAL
+    assert L.henry_autotune(s._h, 0, 0, P(16), 0, ctypes.byref(t), None) == henry.HENRY_EINVAL
+    assert L.henry_autotune(s._h, 0, 1, P(16), 4, ctypes.byref(t), None) == henry.HENRY_EINVAL
+    assert L.henry_autotune(s._h, 9, 0, P(16), 4, ctypes.byref(t), None) == henry.HENRY_EINVAL
+    # without tuning, a level's settings are the configuration's
+    assert s.tuning(2) == {"lin_rtol": 1e-4, "nu1": 2, "nu2": 2, "fused_small_grids": 1, "cell_steps_per_s": 0.0}
+    s.close()

@@ -75,3 +75,28 @@ def test_resume_from_checkpoint_continues_identically(hl):
     for a, b in zip(json.loads(resumed["checkpoint"]), json.loads(full["checkpoint"])):
         assert a["sums"] == b["sums"] and a["n_used"] == b["n_used"]
     s.close()
+
+
+@pytest.mark.parametrize("precision,level", [(0, 0), (1, 0), (0, 2)])
+def test_autotune_picks_a_candidate_and_solves_stay_exact(hl, precision, level):
+    """henry_autotune keeps one of its candidates for the level, and solves
+    with it still reach the oracle's discrete solution (1e-10); an uneven
+    batch's level handles inherit the tuning (bit-identical results)."""
+    import numpy as np
+    from oracle import henry as ohenry
+    from paper_2302_07804_gb300 import inputs
+    s = hl.Solver(precision=precision)
+    trial = hl.sample_xi(inputs.SEED, level, 5000, 256 if level == 0 else 16)
+    best = s.autotune(level, trial)
+    assert best["lin_rtol"] in (1e-4, 1e-3, 1e-2) and (best["nu1"], best["nu2"]) in ((2, 2), (1, 2), (2, 1))
+    assert best["cell_steps_per_s"] > 0 and s.tuning(level) == best
+    xi = hl.sample_xi(inputs.SEED, level, 6000, 3)
+    q, _, st, _ = s.level_batch_solve(level, xi)
+    assert int(st.abs().sum()) == 0
+    ref, ok = ohenry.solve_scenarios(ohenry.Params(), level, xi.cpu().numpy())
+    assert ok.all()
+    np.testing.assert_allclose(q.cpu().numpy()[:, 0], ref[:, 0], rtol=1e-10, atol=0)
+    np.testing.assert_allclose(q.cpu().numpy()[:, 1], ref[:, 1], rtol=0, atol=1e-10)
+    qm, _, _, _ = s.batch_solve_mixed(np.full(3, level, dtype=np.int32), xi)
+    assert torch.equal(qm, q)
+    s.close()
