@@ -1286,6 +1286,39 @@ int check_step_args(henry_handle* h, int level, const double* xi, int n, const d
   return HENRY_OK;
 }
 
+// Configuration checks shared by henry_create and the allocation-free entry
+// point (which has no workspace_bytes budget: with_workspace false).
+int check_config(const henry_config& c, bool with_workspace) {
+  if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || (int64_t)c.nx0 != 2 * (int64_t)c.ny0)
+    return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
+  if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)
+    return set_err(HENRY_EINVAL, "domain must be Lx = 2 Ly (square cells)");
+  if (c.max_level < 0 || c.max_level > 8) return set_err(HENRY_EINVAL, "max_level %d outside [0, 8]", c.max_level);
+  const int64_t finest_cells = ((int64_t)c.nx0 << c.max_level) * ((int64_t)c.ny0 << c.max_level);
+  if (finest_cells > ((int64_t)1 << 30) || c.steps0 > ((1 << 30) >> c.max_level))
+    return set_err(HENRY_EINVAL,
+                   "finest level too large (%lld cells, %d steps at level 0; limits 2^30 cells and 2^30 steps at "
+                   "max_level)",
+                   (long long)finest_cells, c.steps0);
+  if (finest_cells % TPB != 0 || (int64_t)c.nx0 * c.ny0 < TPB)
+    return set_err(HENRY_EINVAL, "cells per sample must be a multiple of %d", TPB);
+  if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
+  if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
+    return set_err(HENRY_EINVAL, "bad coarse_op");
+  if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
+    return set_err(HENRY_EINVAL, "bad coef_model");
+  if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_SERIES) return set_err(HENRY_EINVAL, "bad qoi_set");
+  if (c.coef_model == HENRY_MODEL_KL &&
+      (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
+       !(c.phi_lo < c.phi_hi)))
+    return set_err(HENRY_EINVAL, "bad random-field settings");
+  if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
+      c.lin_rtol <= 0 || (with_workspace && c.workspace_bytes <= 0) ||
+      !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) || !(c.newton_dc_limit >= 0.0))
+    return set_err(HENRY_EINVAL, "bad solver settings");
+  return HENRY_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -1486,27 +1519,8 @@ int henry_create(const henry_config* cfg, henry_handle** out) {
   if (!cfg || !out) return set_err(HENRY_EINVAL, "NULL argument");
   *out = nullptr;
   const henry_config& c = *cfg;
-  if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || c.nx0 != 2 * c.ny0)
-    return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
-  if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)
-    return set_err(HENRY_EINVAL, "domain must be Lx = 2 Ly (square cells)");
-  if (c.max_level < 0 || c.max_level > 8) return set_err(HENRY_EINVAL, "max_level %d outside [0, 8]", c.max_level);
-  if (((int64_t)(c.nx0 << c.max_level) * (c.ny0 << c.max_level)) % TPB != 0 || c.nx0 * c.ny0 < TPB)
-    return set_err(HENRY_EINVAL, "cells per sample must be a multiple of %d", TPB);
-  if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
-  if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
-    return set_err(HENRY_EINVAL, "bad coarse_op");
-  if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
-    return set_err(HENRY_EINVAL, "bad coef_model");
-  if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_SERIES) return set_err(HENRY_EINVAL, "bad qoi_set");
-  if (c.coef_model == HENRY_MODEL_KL &&
-      (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
-       !(c.phi_lo < c.phi_hi)))
-    return set_err(HENRY_EINVAL, "bad random-field settings");
-  if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
-      c.lin_rtol <= 0 || c.workspace_bytes <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) ||
-      !(c.newton_dc_limit >= 0.0))
-    return set_err(HENRY_EINVAL, "bad solver settings");
+  const int rc = check_config(c, true);
+  if (rc) return rc;
   henry_handle* h = new henry_handle();
   h->cfg = c;
   *out = h;
@@ -1984,29 +1998,13 @@ int static_scratch_ptr(char** out) {
   return HENRY_OK;
 }
 
-// The configuration checks of henry_create, without creating a handle.
+// The configuration checks of henry_create, without creating a handle, plus
+// the entry point's own restriction to the two standard QoIs.
 int static_check_config(const henry_config& c) {
-  if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || c.nx0 != 2 * c.ny0)
-    return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
-  if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)
-    return set_err(HENRY_EINVAL, "domain must be Lx = 2 Ly (square cells)");
-  if (c.max_level < 0 || c.max_level > 8) return set_err(HENRY_EINVAL, "max_level %d outside [0, 8]", c.max_level);
-  if (c.nx0 * c.ny0 < TPB) return set_err(HENRY_EINVAL, "cells per sample must be a multiple of %d", TPB);
-  if (c.precision != HENRY_FP64 && c.precision != HENRY_MIXED) return set_err(HENRY_EINVAL, "bad precision");
-  if (c.coarse_op != HENRY_COARSE_REDISCRETISE && c.coarse_op != HENRY_COARSE_GALERKIN)
-    return set_err(HENRY_EINVAL, "bad coarse_op");
-  if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
-    return set_err(HENRY_EINVAL, "bad coef_model");
+  const int rc = check_config(c, false);
+  if (rc) return rc;
   if (c.qoi_set != HENRY_QOI_STANDARD)
     return set_err(HENRY_EINVAL, "the allocation-free entry point writes the two standard QoIs only (qoi_set 0)");
-  if (c.coef_model == HENRY_MODEL_KL &&
-      (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
-       !(c.phi_lo < c.phi_hi)))
-    return set_err(HENRY_EINVAL, "bad random-field settings");
-  if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
-      c.lin_rtol <= 0 || !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) ||
-      !(c.newton_dc_limit >= 0.0))
-    return set_err(HENRY_EINVAL, "bad solver settings");
   return HENRY_OK;
 }
 

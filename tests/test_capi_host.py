@@ -61,10 +61,34 @@ def test_mlmc_allocate_rejects_bad_input(L):
 def test_create_validates_config(L):
     from paper_2302_07804_gb300 import henry
     for bad in (dict(nx0=30), dict(ny0=12, nx0=24), dict(precision=7), dict(nu1=-1), dict(max_level=12),
-                dict(Lx=3.0)):
+                dict(Lx=3.0), dict(ny0=1 << 12, nx0=1 << 13, max_level=8), dict(ny0=1 << 29, nx0=1 << 30, max_level=0),
+                dict(steps0=1 << 26, max_level=5), dict(qoi_set=4), dict(workspace_bytes=0.0)):
         with pytest.raises(henry.HenryError) as e:
             henry.Solver(**bad)
         assert e.value.code == henry.HENRY_EINVAL
+    with pytest.raises(henry.HenryError) as e:
+        henry.Solver(ny0=1 << 12, nx0=1 << 13, max_level=8)
+    assert "finest level too large" in str(e.value)
+    henry.Solver(ny0=1 << 10, nx0=1 << 11, max_level=4, steps0=1 << 20)   # 2^29 cells, 2^24 steps: accepted
+
+
+def test_static_entry_checks_the_config_before_any_device_call(L):
+    from paper_2302_07804_gb300 import henry
+    P = ctypes.c_void_p
+    for bad, text in ((dict(ny0=1 << 12, nx0=1 << 13, max_level=8), b"finest level too large"),
+                      (dict(nx0=30), b"grid must be"), (dict(qoi_set=1), b"qoi_set 0"),
+                      (dict(coef_model=henry.HENRY_MODEL_KL), b"three-parameter model")):
+        cfg = henry.default_config()
+        for k, v in bad.items():
+            setattr(cfg, k, v)
+        rc = L.henry_level_batch_solve_static(ctypes.byref(cfg), 0, 0, P(16), 1, P(16), None, P(16), None)
+        assert rc == henry.HENRY_EINVAL
+        assert text in L.henry_last_error()
+    cfg = henry.default_config()
+    cfg.workspace_bytes = 0.0        # no workspace budget on this path: not an error by itself
+    assert L.henry_level_batch_solve_static(ctypes.byref(cfg), 0, 1, P(16), 1, P(16), P(16), P(16), None) == \
+        henry.HENRY_EINVAL
+    assert b"no coarse partner" in L.henry_last_error()
 
 
 def test_null_and_range_arguments_return_einval(L):
