@@ -213,7 +213,10 @@ int henry_kl_basis(const henry_config* cfg, int level, double* sqrt_lam, double*
 int henry_n_qoi(const henry_config* cfg);
 
 /* Create a handle for `cfg` (copied).  Allocates no device memory yet.
- * Errors: EINVAL on a NULL pointer or inconsistent grid sizes. */
+ * Errors: EINVAL on a NULL pointer, inconsistent grid sizes (nx0 = 2 ny0 with
+ * ny0 a power of two >= 4, Lx = 2 Ly, max_level in [0, 8]), a finest level
+ * past 2^30 cells per sample or 2^30 time steps, an unknown enum value, or
+ * non-positive solver settings. */
 int henry_create(const henry_config* cfg, henry_handle** out);
 
 /* Free the handle and its device workspace (synchronises the device).
