@@ -137,12 +137,49 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dev_f64(t, shape=None):
-    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+def _expect(t, dtype, shape=None, name="tensor"):
+    """Check a tensor the library will read or write through a raw pointer:
+    its shape, dtype, contiguity and that it lives on the current CUDA device
+    (the device the library launches on).  Raises ValueError otherwise."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("%s: expected a torch.Tensor, got %s" % (name, type(t).__name__))
     if shape is not None and tuple(t.shape) != tuple(shape):
-        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+        raise ValueError("%s: expected shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if t.dtype != dtype:
+        raise ValueError("%s: expected %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s: expected a contiguous tensor" % name)
+    if not t.is_cuda:
+        raise ValueError("%s: expected a CUDA tensor, got one on %s" % (name, t.device))
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError("%s: on %s, not on the current device cuda:%d" % (name, t.device, torch.cuda.current_device()))
     return t
+
+
+def _dev_f64(t, shape=None, name="tensor"):
+    return _expect(t, torch.float64, shape, name)
+
+
+def _dev_i32(t, shape=None, name="tensor"):
+    return _expect(t, torch.int32, shape, name)
+
+
+def _outputs(out, n, nq, with_coarse, device):
+    """The (qoi_fine, qoi_coarse or None, status) buffers of a batch solve:
+    new tensors, or the caller's ``out`` after checking their shapes."""
+    if out is None:
+        qf = torch.empty((n, nq), dtype=torch.float64, device=device)
+        qc = torch.empty((n, nq), dtype=torch.float64, device=device) if with_coarse else None
+        st = torch.empty((n,), dtype=torch.int32, device=device)
+        return qf, qc, st
+    qf, qc, st = out
+    _dev_f64(qf, (n, nq), "out[0] (qoi_fine)")
+    if with_coarse:
+        _dev_f64(qc, (n, nq), "out[1] (qoi_coarse)")
+    else:
+        qc = None
+    _dev_i32(st, (n,), "out[2] (status)")
+    return qf, qc, st
 
 
 def default_config(**overrides):
@@ -188,13 +225,15 @@ def sample_xi(seed, level, first_sample, n, device="cuda", stream=None):
 
 def mlmc_accumulate(level, qoi_fine, qoi_coarse, status, sums, stream=None):
     """Merge a batch into sums[2][n_qoi][3] (count, mean, M2) in place."""
+    if not isinstance(qoi_fine, torch.Tensor) or qoi_fine.dim() != 2:
+        raise ValueError("qoi_fine: expected a [n][n_qoi] tensor")
     n, nq = qoi_fine.shape
-    _dev_f64(qoi_fine)
-    _dev_f64(sums, (2, nq, 3))
+    _dev_f64(qoi_fine, None, "qoi_fine")
+    _dev_f64(sums, (2, nq, 3), "sums")
     if qoi_coarse is not None:
-        _dev_f64(qoi_coarse, (n, nq))
-    if status is not None and not (status.is_cuda and status.dtype == torch.int32):
-        raise ValueError("status must be an int32 CUDA tensor")
+        _dev_f64(qoi_coarse, (n, nq), "qoi_coarse")
+    if status is not None:
+        _dev_i32(status, (n,), "status")
     _check(lib().mlmc_accumulate(level, n, nq, _ptr(qoi_fine), _ptr(qoi_coarse), _ptr(status), _ptr(sums),
                                  _stream(stream)))
     return sums
@@ -236,10 +275,8 @@ def level_batch_solve_static(cfg, level, xi, with_coarse=False, stream=None, all
     compiled-in device workspace (no device allocation by the library); for
     callers that cannot allocate.  Returns (qoi_fine, qoi_coarse or None, status)."""
     n = xi.shape[0]
-    _dev_f64(xi, (n, N_XI))
-    qf = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device)
-    qc = torch.empty((n, N_QOI), dtype=torch.float64, device=xi.device) if with_coarse else None
-    st = torch.empty((n,), dtype=torch.int32, device=xi.device)
+    _dev_f64(xi, (n, N_XI), "xi")
+    qf, qc, st = _outputs(None, n, N_QOI, with_coarse, xi.device)
     rc = lib().henry_level_batch_solve_static(ctypes.byref(cfg), level, 1 if with_coarse else 0, _ptr(xi), n,
                                               _ptr(qf), _ptr(qc), _ptr(st), _stream(stream))
     _check(rc, allow=(HENRY_ENOCONV,) if allow_failures else ())
@@ -299,13 +336,8 @@ class Solver:
     def level_batch_solve(self, level, xi, with_coarse=False, stream=None, allow_failures=False, out=None):
         """Returns (qoi_fine[n][2], qoi_coarse[n][2] or None, status[n] int32, stats dict)."""
         n = xi.shape[0]
-        _dev_f64(xi, (n, self.n_xi))
-        if out is None:
-            qf = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
-            qc = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device) if with_coarse else None
-            st = torch.empty((n,), dtype=torch.int32, device=xi.device)
-        else:
-            qf, qc, st = out
+        _dev_f64(xi, (n, self.n_xi), "xi")
+        qf, qc, st = _outputs(out, n, self.n_qoi, with_coarse, xi.device)
         stats = HenryStats()
         rc = lib().henry_level_batch_solve(self._h, level, 1 if with_coarse else 0, _ptr(xi), n, _ptr(qf), _ptr(qc),
                                            _ptr(st), ctypes.byref(stats), _stream(stream))
@@ -320,13 +352,8 @@ class Solver:
         n = xi.shape[0]
         if lv.shape != (n,):
             raise ValueError("levels must hold one level per row of xi")
-        _dev_f64(xi, (n, self.n_xi))
-        if out is None:
-            qf = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
-            qc = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device) if with_coarse else None
-            st = torch.empty((n,), dtype=torch.int32, device=xi.device)
-        else:
-            qf, qc, st = out
+        _dev_f64(xi, (n, self.n_xi), "xi")
+        qf, qc, st = _outputs(out, n, self.n_qoi, with_coarse, xi.device)
         stats = HenryStats()
         rc = lib().henry_batch_solve_mixed(self._h, lv.ctypes.data_as(ctypes.c_void_p), n, 1 if with_coarse else 0,
                                            _ptr(xi), _ptr(qf), _ptr(qc), _ptr(st), ctypes.byref(stats),
@@ -338,8 +365,8 @@ class Solver:
         """dQ/dxi for Q = weights[:, 0] mass + weights[:, 1] c_point (henry_adjoint).
         Returns (grad[n][n_xi], qoi[n][2], status[n] int32)."""
         n = xi.shape[0]
-        _dev_f64(xi, (n, self.n_xi))
-        _dev_f64(weights, (n, N_QOI))
+        _dev_f64(xi, (n, self.n_xi), "xi")
+        _dev_f64(weights, (n, N_QOI), "weights")
         grad = torch.empty((n, self.n_xi), dtype=torch.float64, device=xi.device)
         qoi = torch.empty((n, self.n_qoi), dtype=torch.float64, device=xi.device)
         st = torch.empty((n,), dtype=torch.int32, device=xi.device)
@@ -352,7 +379,7 @@ class Solver:
         """henry_autotune: time the candidate settings on the trial batch xi and
         keep the fastest for this level; returns it as a dict."""
         n = xi.shape[0]
-        _dev_f64(xi, (n, self.n_xi))
+        _dev_f64(xi, (n, self.n_xi), "xi")
         t = HenryTuning()
         _check(lib().henry_autotune(self._h, level, 1 if with_coarse else 0, _ptr(xi), n, ctypes.byref(t),
                                     _stream(stream)))
@@ -374,15 +401,16 @@ class Solver:
         _check(lib().henry_get_tuning(self._h, level, ctypes.byref(t)))
         return t.as_dict()
 
-    def _states(self, level, state, state_old):
+    def _states(self, level, xi, state, state_old):
         ny, nx = self.grid(level)
         n = state.shape[0]
-        _dev_f64(state, (n, ny, nx, 2))
-        _dev_f64(state_old, (n, ny, nx, 2))
+        _dev_f64(xi, (n, self.n_xi), "xi")
+        _dev_f64(state, (n, ny, nx, 2), "state")
+        _dev_f64(state_old, (n, ny, nx, 2), "state_old")
         return n, ny, nx
 
     def assemble(self, level, xi, state, state_old, with_jacobian=True, stream=None):
-        n, ny, nx = self._states(level, state, state_old)
+        n, ny, nx = self._states(level, xi, state, state_old)
         F = torch.empty((n, ny, nx, 2), dtype=torch.float64, device=state.device)
         J = torch.empty((n, ny, nx, 5, 2, 2), dtype=torch.float64, device=state.device) if with_jacobian else None
         _check(lib().henry_assemble(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(F), _ptr(J),
@@ -390,24 +418,24 @@ class Solver:
         return F, J
 
     def apply_jacobian(self, level, xi, state, state_old, x, stream=None):
-        n, ny, nx = self._states(level, state, state_old)
-        _dev_f64(x, (n, ny, nx, 2))
+        n, ny, nx = self._states(level, xi, state, state_old)
+        _dev_f64(x, (n, ny, nx, 2), "x")
         y = torch.empty_like(x)
         _check(lib().henry_apply_jacobian(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(x),
                                           _ptr(y), _stream(stream)))
         return y
 
     def precondition(self, level, xi, state, state_old, b, stream=None):
-        n, ny, nx = self._states(level, state, state_old)
-        _dev_f64(b, (n, ny, nx, 2))
+        n, ny, nx = self._states(level, xi, state, state_old)
+        _dev_f64(b, (n, ny, nx, 2), "b")
         z = torch.empty_like(b)
         _check(lib().henry_precondition(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),
                                         _ptr(z), _stream(stream)))
         return z
 
     def linear_solve(self, level, xi, state, state_old, b, stream=None):
-        n, ny, nx = self._states(level, state, state_old)
-        _dev_f64(b, (n, ny, nx, 2))
+        n, ny, nx = self._states(level, xi, state, state_old)
+        _dev_f64(b, (n, ny, nx, 2), "b")
         x = torch.empty_like(b)
         its = torch.empty((n,), dtype=torch.int32, device=b.device)
         _check(lib().henry_linear_solve(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),

@@ -216,3 +216,39 @@ def test_autotune_arguments_return_einval(L):
     # without tuning, a level's settings are the configuration's
     assert s.tuning(2) == {"lin_rtol": 1e-4, "nu1": 2, "nu2": 2, "fused_small_grids": 1, "cell_steps_per_s": 0.0}
     s.close()
+
+
+def test_binding_checks_tensors_before_passing_pointers(L):
+    """Every tensor the binding hands to the library as a raw pointer is
+    checked for shape, dtype, contiguity and device first (checked in that
+    order, so each check is reachable with CPU tensors)."""
+    import torch
+    from paper_2302_07804_gb300 import henry
+    f64 = torch.zeros((4, 3), dtype=torch.float64)
+    cases = [
+        (lambda: henry._dev_f64(f64, (4, 2), "xi"), "xi: expected shape (4, 2)"),
+        (lambda: henry._dev_f64(f64.float(), (4, 3), "xi"), "expected torch.float64"),
+        (lambda: henry._dev_f64(f64.t(), (3, 4), "xi"), "contiguous"),
+        (lambda: henry._dev_f64(f64, (4, 3), "xi"), "expected a CUDA tensor"),
+        (lambda: henry._dev_i32(torch.zeros(4, dtype=torch.int64), (4,), "status"), "expected torch.int32"),
+        (lambda: henry._dev_f64([0.0], None, "xi"), "expected a torch.Tensor"),
+        (lambda: henry._outputs((torch.zeros((4, 2), dtype=torch.float64), None,
+                                 torch.zeros(4, dtype=torch.int32)), 4, 15, False, "cpu"), "out[0] (qoi_fine)"),
+        (lambda: henry.mlmc_accumulate(0, torch.zeros((4, 2), dtype=torch.float64), None,
+                                       torch.zeros(5, dtype=torch.int32), torch.zeros((2, 2, 3), dtype=torch.float64)),
+         "expected a CUDA tensor"),
+        (lambda: henry.mlmc_accumulate(0, torch.zeros(4, dtype=torch.float64), None, None, None), "[n][n_qoi]"),
+    ]
+    for call, text in cases:
+        with pytest.raises(ValueError) as e:
+            call()
+        assert text in str(e.value), (text, str(e.value))
+    s = henry.Solver(coef_model=henry.HENRY_MODEL_KL)
+    with pytest.raises(ValueError) as e:       # 3 inputs per sample where the KL model takes 2 kl_terms + 1
+        s.level_batch_solve(0, f64)
+    assert "expected shape (4, 65)" in str(e.value)
+    with pytest.raises(ValueError) as e:       # xi of the step calls is checked too
+        s.assemble(0, f64, torch.zeros((4, 16, 32, 2), dtype=torch.float64),
+                   torch.zeros((4, 16, 32, 2), dtype=torch.float64))
+    assert "xi: expected shape (4, 65)" in str(e.value)
+    s.close()
