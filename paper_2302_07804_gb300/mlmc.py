@@ -63,6 +63,8 @@ def run_level(solver, st, n, seed, stream=None, xi=None):
     """Solve n new samples of level st.level (with coarse partners) and merge
     them into st.sums; returns the henry_stats of the call."""
     lev = st.level
+    if xi is not None and xi.shape[0] != n:
+        raise ValueError("xi holds %d samples, n = %d" % (xi.shape[0], n))
     if xi is None:
         xi = henry.sample_xi(seed, lev, st.n_used, n, device=st.sums.device, stream=stream)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -134,6 +136,13 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
     to one henry_batch_solve_mixed call; otherwise level by level (needed for
     cost="measured", which times each level's solves)."""
     from . import inputs
+    if not 0 <= max_level <= solver.cfg.max_level:
+        raise ValueError("max_level %d outside [0, %d]" % (max_level, solver.cfg.max_level))
+    if len(pilot) < max_level + 1:
+        raise ValueError("pilot gives %d levels' sample numbers, max_level %d needs %d"
+                         % (len(pilot), max_level, max_level + 1))
+    if state and len(state) > max_level + 1:
+        raise ValueError("state holds %d levels, more than max_level + 1 = %d" % (len(state), max_level + 1))
     seed = inputs.SEED if seed is None else seed
     dev = torch.device("cuda", torch.cuda.current_device())
     levels = list(state) if state else []
