@@ -388,8 +388,8 @@ def run_uneven(args):
     """4096 scenarios spread over levels 0..5 (32x16x20 .. 1024x512x640), all
     levels concurrently (one stream and handle each).  --workload uneven: FP64,
     three-parameter model; --workload kl-mixed: KL random fields, mixed
-    precision, with the QoI difference to FP64 solves of the same inputs and
-    to the oracle on a few level-0/1 samples."""
+    precision, with the QoI difference to FP64 solves of the same inputs (the
+    comparison with the oracle is a test, not part of the bench)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -438,16 +438,6 @@ def run_uneven(args):
             diff.append({"level": l, "max_rel_mass": float(np.max(np.abs(a[:, 0] - b[:, 0]) / np.abs(b[:, 0]))),
                          "max_abs_c": float(np.max(np.abs(a[:, 1] - b[:, 1])))})
         line["qoi_mixed_vs_fp64_gpu"] = diff
-        from oracle import henry as oh
-        prm = oh.Params()
-        orc = []
-        for l, k in ((0, 3), (1, 1)):
-            x = xis[l][:k].cpu().numpy()
-            ref, ok = oh.solve_scenarios(prm, l, x, model="kl")
-            a = q32[l][:k].cpu().numpy()
-            orc.append({"level": l, "n": k, "max_rel_mass": float(np.max(np.abs(a[:, 0] - ref[:, 0]) / ref[:, 0])),
-                        "max_abs_c": float(np.max(np.abs(a[:, 1] - ref[:, 1])))})
-        line["qoi_mixed_vs_oracle"] = orc
         W64.close()
     W.close()
     print(json.dumps(line), flush=True)
