@@ -370,8 +370,8 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
 // residuals gain +F, +G and R's lose them, so R's derivative terms are the
 // negated ones of L.  The tile kernel evaluates each face once (assemble_cell
 // evaluates every interior face from both sides): the same arithmetic from
-// L's side, upwinding included (the tie F = 0 takes L's value, as the
-// oracle's face loop does).
+// L's side, upwinding included (at the tie F = 0 the upwind value is L's,
+// the same tie-break as assemble_cell's from L's side).
 template <typename T, typename S>
 struct FaceData {
   S F, G;   // fluxes L -> R (scaled)
