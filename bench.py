@@ -276,13 +276,16 @@ class Workload:
         self.with_coarse = with_coarse
         self.precision, self.solver_kw = precision, solver_kw
         self.solver = henry.Solver(precision=precision, **solver_kw)
+        if self.solver.n_qoi != henry.N_QOI:
+            raise ValueError("the MLMC workload accumulates the two standard QoIs (qoi_set 0), not %d per sample"
+                             % self.solver.n_qoi)
         self.solvers = None  # per-level handles of the sequential mode
         self.levels = np.concatenate([np.full(m, l, dtype=np.int32) for l, m in enumerate(alloc)])
         self.off = [0] + list(np.cumsum(alloc))
         n = int(self.off[-1])
         self.n = n
-        self.qf = torch.empty((n, 2), dtype=torch.float64, device=dev)
-        self.qc = torch.empty((n, 2), dtype=torch.float64, device=dev) if with_coarse else None
+        self.qf = torch.empty((n, henry.N_QOI), dtype=torch.float64, device=dev)
+        self.qc = torch.empty((n, henry.N_QOI), dtype=torch.float64, device=dev) if with_coarse else None
         self.st = torch.empty((n,), dtype=torch.int32, device=dev)
         self.outs = [self._slice(l) for l in range(self.L)]
         self.sums = torch.zeros((self.L, 2, 2, 3), dtype=torch.float64, device=dev)

@@ -39,3 +39,12 @@ def test_sweep_traffic_record_matches_the_current_smoother():
     t = bench.sweep_traffic(1.0e6, "f64")
     assert t is not None and 0.9e6 < t < 1.0e6          # traffic / algorithmic 0.975
     assert bench.sweep_traffic(1.0e6, "f16") is None
+
+
+def test_workload_rejects_qoi_sets_other_than_the_standard_pair():
+    import pytest
+    import torch
+    from paper_2302_07804_gb300 import henry
+    with pytest.raises(ValueError) as e:
+        bench.Workload(henry, torch, "cpu", [4], henry.HENRY_FP64, [], qoi_set=henry.HENRY_QOI_PAPER)
+    assert "not 15 per sample" in str(e.value)
