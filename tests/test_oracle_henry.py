@@ -273,6 +273,29 @@ def test_qoi_point_is_mean_of_four_cells_at_vertex():
         assert mass == pytest.approx(float(np.sum(phi * rho * c)) * grid.h ** 2, rel=1e-14)
 
 
+def test_salt_mass_closed_forms():
+    """The salt-mass QoI against closed forms, not against its own formula.
+    For uniform c the mass is phi rho(c) c Lx Ly.  For c = x / Lx the cell
+    sum is the midpoint rule of a quadratic in x: the exact integral
+    phi Ly Lx (rho0 / 2 + drho / 3) less phi Ly h^2 / 24 times the integral
+    of the second derivative, 2 drho / Lx."""
+    drho = PRM.rho1 - PRM.rho0
+    for lev in (0, 2):
+        grid = henry.Grid.level(PRM, lev)
+        coef = henry.coefficients(PRM, grid, [0.4, -0.7, 0.1])
+        phi = float(coef.phi[0, 0])
+        area = PRM.Lx * PRM.Ly
+        for cu in (0.0, 0.5, 1.0):
+            c = np.full((grid.ny, grid.nx), cu)
+            mass, _ = henry.qoi(PRM, grid, coef, np.zeros_like(c), c)
+            assert mass == pytest.approx(phi * (PRM.rho0 + drho * cu) * cu * area, rel=1e-13, abs=1e-300)
+        xc = (np.arange(grid.nx) + 0.5) * grid.h
+        c = np.broadcast_to(xc / PRM.Lx, (grid.ny, grid.nx)).copy()
+        mass, _ = henry.qoi(PRM, grid, coef, np.zeros_like(c), c)
+        exact = phi * PRM.Ly * (PRM.Lx * (PRM.rho0 / 2 + drho / 3) - grid.h ** 2 / 24 * 2 * drho / PRM.Lx)
+        assert mass == pytest.approx(exact, rel=1e-13)
+
+
 def test_grid_hierarchy_counts():
     """N_l = 512 * 4^l cells, r_l = 20 * 2^l steps, tau_l = 360 / 2^l s
     (regular refinement and halved time step, Sec. 2.3)."""
