@@ -296,6 +296,31 @@ def test_salt_mass_closed_forms():
         assert mass == pytest.approx(exact, rel=1e-13)
 
 
+def test_three_parameter_coefficients_ranges_and_separation():
+    """The three-parameter model at the corners of [-1, 1]^3: the ranges the
+    configuration states (phi in [0.28, 0.42], K in 1.02e-9 [e^-0.5, e^0.5],
+    q_in in [5.28e-5, 7.92e-5]), means at xi = 0, each coefficient moved by
+    its own xi component only, and log K affine in xi2."""
+    grid = henry.Grid.level(PRM, 0)
+    c0 = henry.coefficients(PRM, grid, [0.0, 0.0, 0.0])
+    assert (c0.phi == 0.35).all() and (c0.K == 1.02e-9).all() and c0.qin == 6.6e-5
+    lo = henry.coefficients(PRM, grid, [-1.0, -1.0, -1.0])
+    hi = henry.coefficients(PRM, grid, [1.0, 1.0, 1.0])
+    # abs=0: pytest's default absolute tolerance (1e-12) would swamp K ~ 1e-9
+    assert lo.phi[0, 0] == pytest.approx(0.28, rel=1e-15, abs=0) and hi.phi[0, 0] == pytest.approx(0.42, rel=1e-15, abs=0)
+    assert lo.K[0, 0] == pytest.approx(6.186613e-10, rel=1e-6, abs=0)
+    assert hi.K[0, 0] == pytest.approx(1.681696e-9, rel=1e-6, abs=0)
+    assert lo.qin == pytest.approx(5.28e-5, rel=1e-14, abs=0) and hi.qin == pytest.approx(7.92e-5, rel=1e-14, abs=0)
+    for k in range(3):
+        e = [0.0, 0.0, 0.0]
+        e[k] = 0.7
+        ck = henry.coefficients(PRM, grid, e)
+        moved = [not np.array_equal(ck.phi, c0.phi), not np.array_equal(ck.K, c0.K), ck.qin != c0.qin]
+        assert moved == [j == k for j in range(3)]
+    logK = [np.log(henry.coefficients(PRM, grid, [0.0, t, 0.0]).K[0, 0]) for t in (-0.8, 0.1, 0.6)]
+    assert (logK[2] - logK[1]) / 0.5 == pytest.approx((logK[1] - logK[0]) / 0.9, rel=1e-12)
+
+
 def test_grid_hierarchy_counts():
     """N_l = 512 * 4^l cells, r_l = 20 * 2^l steps, tau_l = 360 / 2^l s
     (regular refinement and halved time step, Sec. 2.3)."""

@@ -74,7 +74,7 @@ def test_total_cost_formula():
     tot = sum(math.sqrt(v * c) for v, c in zip(V, s))
     m = [math.sqrt(v / c) * tot / 1e-6 for v, c in zip(V, s)]
     assert mlmc.total_cost(V, s, 1e-6) == pytest.approx(sum(mi * si for mi, si in zip(m, s)), rel=1e-12)
-    assert sum(v / mi for v, mi in zip(V, m)) == pytest.approx(1e-6, rel=1e-12)
+    assert sum(v / mi for v, mi in zip(V, m)) == pytest.approx(1e-6, rel=1e-12, abs=0)
 
 
 def test_two_pass_moments_match_numpy():
@@ -237,7 +237,7 @@ def test_bias_test_is_the_geometric_tail():
         means = [c * 2.0 ** (-alpha * l) for l in range(L + 1)]
         tail = sum(c * 2.0 ** (-alpha * l) for l in range(L + 1, 400))
         b, ok = mlmc.bias_test(means, alpha, 1.0)
-        assert b == pytest.approx(tail, rel=1e-12)
+        assert b == pytest.approx(tail, rel=1e-12, abs=0)
         assert ok
         assert mlmc.bias_test(means, alpha, math.sqrt(2.0) * tail * 0.999)[1] is False
         assert mlmc.bias_test(means, alpha, math.sqrt(2.0) * tail * 1.001)[1] is True
