@@ -85,6 +85,54 @@ def sweep_traffic(alg_bytes_per_launch, precision):
         return None
 
 
+def roofline_from_profile(prof, alu_key, peak, peak_src):
+    """The bench line's roofline and kernel-class table from one profiled
+    step: prof maps each kernel class to (ms, launches, algorithmic bytes,
+    algorithmic flops), summed over the step's launches.  The dominant kernel
+    is the class with the most time, with the smoother's two timer classes
+    (fine grids, coarser multigrid levels) merged into their one kernel,
+    k_sweep.  achieved = algorithmic bytes (flops) / event time; frac =
+    achieved / peak, against HBM (peak: GB/s) and the ALU peak for alu_key;
+    the larger fraction names the bound.  Returns (roofline, kernel_classes,
+    launches in the step)."""
+    launches = sum(v[1] for v in prof.values())
+    tot_ms = sum(v[0] for v in prof.values())
+    kernels = {k: list(v) for k, v in prof.items() if k not in ("smooth", "smooth_coarse")}
+    kernels["k_sweep"] = [prof["smooth"][i] + prof["smooth_coarse"][i] for i in range(4)]
+    name, (ms, nl, nbytes, nflops) = max(kernels.items(), key=lambda kv: kv[1][0])
+    by_grid = {}
+    for cls, label in (("smooth", "fine grids"), ("smooth_coarse", "coarser multigrid levels")):
+        c_ms, c_nl, c_b, c_f = prof[cls]
+        by_grid[label] = {"ms": c_ms, "launches": c_nl,
+                          "GBps": c_b / (c_ms / 1e3) / 1e9 if c_ms > 0 else None,
+                          "frac": (c_b / (c_ms / 1e3) / 1e9) / peak if c_ms > 0 else None}
+    sec = ms / 1e3
+    gbs = nbytes / sec / 1e9 if sec > 0 else 0.0
+    tfl = nflops / sec / 1e12 if sec > 0 else 0.0
+    f_hbm = gbs / peak
+    f_alu = tfl / ALU_PEAK_TFLOPS[alu_key]
+    traffic = sweep_traffic(nbytes / max(1, nl), alu_key) if name == "k_sweep" else None
+    src = ("measured (MEASURED_PEAKS.json hbm_gbs, a copy kernel)" if peak_src == "measured"
+           else "fallback (6.8 TB/s; no MEASURED_PEAKS.json)")
+    hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": f_hbm, "peak_source": src}
+    alu = {"achieved": tfl, "peak": ALU_PEAK_TFLOPS[alu_key], "unit": "TFLOP/s", "frac": f_alu,
+           "peak_source": "unit counts x 2.07 GHz (%s)" % alu_key}
+    main = alu if f_alu > f_hbm else hbm
+    roof = {"bound": "alu" if f_alu > f_hbm else "hbm", "kernel": name,
+            "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
+            "frac": main["frac"], "traffic": traffic, "hbm": hbm, "alu": alu,
+            "avg_launch_us": 1e3 * ms / max(1, nl), "alg_bytes_per_launch": nbytes / max(1, nl),
+            "alg_flops_per_launch": nflops / max(1, nl),
+            "timing": "CUDA events around every launch of the kernel during one extra step, "
+                      "levels run one after another, plain launches (no graph replay)"}
+    if name == "k_sweep":
+        roof["by_grid"] = by_grid
+    classes = {k: {"ms": v[0], "share": v[0] / tot_ms if tot_ms else None, "launches": v[1],
+                   "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
+               for k, v in prof.items()}
+    return roof, classes, launches
+
+
 class Clocks:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -679,42 +727,8 @@ def main():
         torch.cuda.synchronize()
         prof = W.profile_read()
         W.profile(False)
-        gpu_launches_step = sum(v[1] for v in prof.values())
-        tot_ms = sum(v[0] for v in prof.values())
-        # kernels: the smoother's two timer classes (fine grids, coarser multigrid levels) are one kernel, k_sweep
-        kernels = {k: list(v) for k, v in prof.items() if k not in ("smooth", "smooth_coarse")}
-        kernels["k_sweep"] = [prof["smooth"][i] + prof["smooth_coarse"][i] for i in range(4)]
-        name, (ms, nl, nbytes, nflops) = max(kernels.items(), key=lambda kv: kv[1][0])
-        by_grid = {}
-        for cls, label in (("smooth", "fine grids"), ("smooth_coarse", "coarser multigrid levels")):
-            c_ms, c_nl, c_b, c_f = prof[cls]
-            by_grid[label] = {"ms": c_ms, "launches": c_nl,
-                              "GBps": c_b / (c_ms / 1e3) / 1e9 if c_ms > 0 else None,
-                              "frac": (c_b / (c_ms / 1e3) / 1e9) / peaks()[0] if c_ms > 0 else None}
-        peak, src = peaks()
-        sec = ms / 1e3
-        gbs = nbytes / sec / 1e9 if sec > 0 else 0.0
-        tfl = nflops / sec / 1e12 if sec > 0 else 0.0
         alu_key = "f64" if prec == henry.HENRY_FP64 else "f32"
-        f_hbm = gbs / peak
-        f_alu = tfl / ALU_PEAK_TFLOPS[alu_key]
-        traffic = sweep_traffic(nbytes / max(1, nl), alu_key) if name == "k_sweep" else None
-        hbm = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": f_hbm, "peak_source": src + " (MEASURED_PEAKS.json copy)"}
-        alu = {"achieved": tfl, "peak": ALU_PEAK_TFLOPS[alu_key], "unit": "TFLOP/s", "frac": f_alu,
-               "peak_source": "unit counts x 2.07 GHz (%s)" % alu_key}
-        main = alu if f_alu > f_hbm else hbm
-        line["roofline"] = {"bound": "alu" if f_alu > f_hbm else "hbm", "kernel": name,
-                            "achieved": main["achieved"], "peak": main["peak"], "unit": main["unit"],
-                            "frac": main["frac"], "traffic": traffic, "hbm": hbm, "alu": alu,
-                            "avg_launch_us": 1e3 * ms / max(1, nl), "alg_bytes_per_launch": nbytes / max(1, nl),
-                            "alg_flops_per_launch": nflops / max(1, nl),
-                            "timing": "CUDA events around every launch of the kernel during one extra step, "
-                                      "levels run one after another, plain launches (no graph replay)"}
-        if name == "k_sweep":
-            line["roofline"]["by_grid"] = by_grid
-        line["kernel_classes"] = {k: {"ms": v[0], "share": v[0] / tot_ms if tot_ms else None, "launches": v[1],
-                                      "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None}
-                                  for k, v in prof.items()}
+        line["roofline"], line["kernel_classes"], gpu_launches_step = roofline_from_profile(prof, alu_key, *peaks())
         line["gpu_launches"] = gpu_launches_step * args.steps
         # ---- MLMC time to RMSE 1e-3, FP64 vs mixed (fresh counters)
         times = {}

@@ -48,3 +48,27 @@ def test_workload_rejects_qoi_sets_other_than_the_standard_pair():
     with pytest.raises(ValueError) as e:
         bench.Workload(henry, torch, "cpu", [4], henry.HENRY_FP64, [], qoi_set=henry.HENRY_QOI_PAPER)
     assert "not 15 per sample" in str(e.value)
+
+
+def test_roofline_from_profile_picks_the_dominant_kernel_and_its_bound():
+    from paper_2302_07804_gb300 import henry
+    prof = {k: [0.0, 0, 0.0, 0.0] for k in henry.KERNEL_CLASSES}
+    prof["smooth"] = [30.0, 100, 150e9, 10e9]          # 30 ms over 100 launches
+    prof["smooth_coarse"] = [10.0, 300, 10e9, 1e9]
+    prof["spmv"] = [35.0, 50, 175e9, 12e9]             # more time than either smoother class alone
+    roof, classes, launches = bench.roofline_from_profile(prof, "f64", 6000.0, "measured")
+    assert launches == 450
+    # the smoother's classes are one kernel: 40 ms, 400 launches, 160 GB -> 4000 GB/s
+    assert roof["kernel"] == "k_sweep" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert abs(roof["achieved"] - 4000.0) < 1e-9 and abs(roof["frac"] - 4000.0 / 6000.0) < 1e-12
+    assert abs(roof["avg_launch_us"] - 100.0) < 1e-9 and roof["alg_bytes_per_launch"] == 160e9 / 400
+    assert abs(roof["alu"]["achieved"] - 11e9 / 0.04 / 1e12) < 1e-12
+    assert abs(roof["by_grid"]["fine grids"]["GBps"] - 5000.0) < 1e-9
+    assert abs(classes["spmv"]["share"] - 35.0 / 75.0) < 1e-12 and classes["qoi"]["GBps"] is None
+    # a flop-heavy kernel is reported against the ALU peak
+    prof["smooth"], prof["smooth_coarse"] = [1.0, 1, 1e9, 0.0], [0.0, 0, 0.0, 0.0]
+    prof["spmv"] = [35.0, 50, 7e9, 40e12 * 0.035]      # 0.2 TB/s, 40 TFLOP/s
+    roof, _, _ = bench.roofline_from_profile(prof, "f32", 6000.0, "fallback")
+    assert roof["kernel"] == "spmv" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    assert roof["traffic"] is None and "by_grid" not in roof
+    assert roof["hbm"]["peak_source"].startswith("fallback")
