@@ -18,6 +18,11 @@ Contents, each function citing the passage of arXiv 2302.07804 it follows:
   (e_cont_eq), (e_tran_eq), (e_Darcy_vel), (e_lin_density), (e_mol_diff) with
   the boundary conditions of Sec. 2.1, implicit Euler in time and Newton's
   method with a direct sparse solve (Sec. 2.3); QoIs.
+* ``henry_vc`` - the paper's own vertex-centred finite volumes (two unknowns
+  per grid vertex, Sec. 2.3 and Table tab:adaptiveTS_times), with the
+  readings of its "consistent velocity" and partial upwinding stated in the
+  module; the same equations, boundary conditions, time stepping and QoIs.
+  No CUDA counterpart yet: it fixes the target of that path.
 * ``mg``      - the textbook definitions of the multigrid pieces the CUDA
   path uses (Galerkin coarse operator, red-black block Gauss-Seidel, V-cycle,
   right-preconditioned BiCGStab from the Templates book cited in Sec. 2.3).
