@@ -160,10 +160,18 @@ def inflow_lengths(grid):
     return L
 
 
-def fv_residual(prm, grid, coef, p, c, p_old, c_old):
+def cv_areas(grid):
+    """|CV| of every vertex: h^2 inside, h^2/2 on an edge, h^2/4 at a corner."""
+    a = np.zeros((grid.ny + 1, grid.nx + 1))
+    for k in range(4):
+        a[_CORNER[k]] += 1.0
+    return a * (grid.h * grid.h / 4.0)
+
+
+def fv_residual(prm, grid, coef, p, c, p_old, c_old, inflow=True):
     """The finite-volume balances (R^m, R^s) of every vertex, (ny+1, nx+1)
     each, before the Dirichlet vertices' equations are replaced: storage
-    plus outgoing face fluxes, plus the inflow term at x = 0."""
+    plus outgoing face fluxes, plus (if ``inflow``) the inflow term at x = 0."""
     rho, rho_o = density(prm, c), density(prm, c_old)
     w = storage_weights(grid, coef)
     Rm = w * (rho - rho_o) / grid.tau
@@ -175,7 +183,8 @@ def fv_residual(prm, grid, coef, p, c, p_old, c_old):
         Rm[_CORNER[b]] -= F
         Rs[_CORNER[a]] += G
         Rs[_CORNER[b]] -= G
-    Rm[:, 0] -= prm.rho0 * coef.qin * inflow_lengths(grid)
+    if inflow:
+        Rm[:, 0] -= prm.rho0 * coef.qin * inflow_lengths(grid)
     return Rm, Rs
 
 
@@ -183,13 +192,29 @@ def residual_scale(prm, grid):
     return prm.rho0 * grid.h * grid.h / grid.tau
 
 
-def residual(prm, grid, coef, p, c, p_old, c_old):
+def residual(prm, grid, coef, p, c, p_old, c_old, src=None, dirichlet=None):
     """Newton's residual: the balances, with the Dirichlet vertices'
-    equations replaced by (value - boundary value) x residual scale."""
-    Rm, Rs = fv_residual(prm, grid, coef, p, c, p_old, c_old)
+    equations replaced by (value - boundary value) x residual scale.
+
+    For the manufactured-solution test only: ``src`` = vertex sources
+    (S_m, S_s) in kg/(m^3 s), subtracted as S |CV|; ``dirichlet`` = vertex
+    arrays (p_b, c_b) whose boundary entries replace the Henry boundary
+    conditions by Dirichlet data for p and c on all four sides."""
+    Rm, Rs = fv_residual(prm, grid, coef, p, c, p_old, c_old, inflow=dirichlet is None)
     s = residual_scale(prm, grid)
+    pscale = prm.rho0 * prm.g * prm.Ly
+    if src is not None:
+        a = cv_areas(grid)
+        Rm = Rm - src[0] * a
+        Rs = Rs - src[1] * a
+    if dirichlet is not None:
+        edge = np.zeros((grid.ny + 1, grid.nx + 1), dtype=bool)
+        edge[0, :] = edge[-1, :] = edge[:, 0] = edge[:, -1] = True
+        Rm = np.where(edge, s * (p - dirichlet[0]) / pscale, Rm)
+        Rs = np.where(edge, s * (c - dirichlet[1]), Rs)
+        return Rm, Rs
     y = vertex_y(grid)
-    Rm[:, -1] = s * (p[:, -1] - prm.rho1 * prm.g * (prm.Ly - y)) / (prm.rho0 * prm.g * prm.Ly)
+    Rm[:, -1] = s * (p[:, -1] - prm.rho1 * prm.g * (prm.Ly - y)) / pscale
     Rs[:, -1] = s * (c[:, -1] - 1.0)
     Rs[:, 0] = s * c[:, 0]
     return Rm, Rs
@@ -205,7 +230,7 @@ def unpack(v, grid):
     return v[:, 0].reshape(shape), v[:, 1].reshape(shape)
 
 
-def jacobian(prm, grid, coef, p, c, p_old, c_old, step=1e-30):
+def jacobian(prm, grid, coef, p, c, p_old, c_old, src=None, dirichlet=None, step=1e-30):
     """d(R^m, R^s)/d(p, c) by the complex step: vertices coloured by (j mod 3,
     i mod 3) are perturbed together; a vertex couples only to the corners of
     its elements, so each row sees at most one perturbed vertex per colour."""
@@ -223,7 +248,7 @@ def jacobian(prm, grid, coef, p, c, p_old, c_old, step=1e-30):
                     pz = pz + 1j * step * mask
                 else:
                     cz = cz + 1j * step * mask
-                Rm, Rs = residual(prm, grid, coef, pz, cz, p_old, c_old)
+                Rm, Rs = residual(prm, grid, coef, pz, cz, p_old, c_old, src, dirichlet)
                 dj = (cj - J) % 3
                 di = (ci - I) % 3
                 jp = J + np.where(dj == 2, -1, dj)
@@ -240,19 +265,19 @@ def jacobian(prm, grid, coef, p, c, p_old, c_old, step=1e-30):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
 
 
-def newton_step(prm, grid, coef, p_old, c_old, stats=None):
+def newton_step(prm, grid, coef, p_old, c_old, stats=None, src=None, dirichlet=None):
     """One implicit-Euler step by Newton's method with direct sparse solves;
     the stopping rule and the mass-fraction step limit of oracle.henry."""
     s = residual_scale(prm, grid)
     pref = prm.rho0 * prm.g * prm.Ly
     p, c = p_old.copy(), c_old.copy()
     for it in range(prm.newton_maxit):
-        Rm, Rs = residual(prm, grid, coef, p, c, p_old, c_old)
+        Rm, Rs = residual(prm, grid, coef, p, c, p_old, c_old, src, dirichlet)
         if max(np.abs(Rm).max(), np.abs(Rs).max()) / s <= prm.newton_atol:
             if stats is not None:
                 stats.append(it)
             return p, c, True
-        Jm = jacobian(prm, grid, coef, p, c, p_old, c_old)
+        Jm = jacobian(prm, grid, coef, p, c, p_old, c_old, src, dirichlet)
         dp, dc = unpack(spla.spsolve(Jm.tocsc(), -pack(Rm, Rs)), grid)
         dcmax = np.abs(dc).max()
         theta = prm.newton_dc_limit / dcmax if (prm.newton_dc_limit > 0 and dcmax > prm.newton_dc_limit) else 1.0
