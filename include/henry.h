@@ -184,7 +184,8 @@ void henry_paper_config(henry_config* cfg);
  * then on (henry_adjoint keeps the configuration's settings).  QoIs move only
  * within the Newton tolerance.  Allocates its trial outputs; synchronises
  * `stream`.  best_out (nullable) receives the choice with its measured rate.
- * Errors: EINVAL, ENOMEM, ECUDA, ENOCONV (no candidate solved every sample). */
+ * Errors: EINVAL, ENOMEM, ECUDA, ENOCONV (no candidate solved every sample);
+ * after an error the level keeps the settings it had before the call. */
 typedef struct {
   double lin_rtol;
   int32_t nu1, nu2, fused_small_grids;

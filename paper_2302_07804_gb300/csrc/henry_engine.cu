@@ -1439,13 +1439,20 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = HENRY_OK;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = HENRY_ECUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    rc = set_err(HENRY_ECUDA, "cudaEventCreate for the autotuner's timing failed");
+  }
   const LevelGeom lg = geom(c, level);
   double cs = (double)n_trial * lg.nx * lg.ny * lg.steps;
   if (with_coarse) {
     const LevelGeom lc = geom(c, level - 1);
     cs += (double)n_trial * lc.nx * lc.ny * lc.steps;
   }
+  // a failed run leaves the level's settings as they were
+  const auto prior = h->tuned.find(level);
+  const bool had_prior = prior != h->tuned.end();
+  const henry_tuning prior_t = had_prior ? prior->second : henry_tuning{};
   h->tuned.erase(level);
   int best = -1;
   double best_rate = 0.0;
@@ -1475,8 +1482,10 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(mem);
-  if (rc) return rc;
-  if (best < 0) return set_err(HENRY_ENOCONV, "no candidate solved every trial sample");
+  if (rc || best < 0) {
+    if (had_prior) h->tuned[level] = prior_t;
+    return rc ? rc : set_err(HENRY_ENOCONV, "no candidate solved every trial sample");
+  }
   h->tuned[level] = cands[best];
   if (best_out) *best_out = cands[best];
   return HENRY_OK;
