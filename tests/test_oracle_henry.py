@@ -13,6 +13,7 @@ wrong index in ``oracle.henry`` fails at least one of them:
 * bounds 0 <= c <= 1, discrete salt-mass conservation
 * Newton with a brute-force finite-difference Jacobian and a dense solve
   reaches the same state (the solution is the root of the residual)
+* mistakes planted in the oracle's source each fail one of the above
 """
 import math
 
@@ -330,3 +331,91 @@ def test_grid_hierarchy_counts():
         assert g.steps == 20 * 2 ** lev
         assert g.tau == pytest.approx(360.0 / 2 ** lev)
         assert g.h == pytest.approx(1.0 / (16 * 2 ** lev))
+
+
+# Mistakes planted in the oracle's source.  The planted copy gets a complex-
+# step Jacobian of its own (planted) residual, so that Newton still converges
+# to the planted scheme's solution and only the physics pins above can tell.
+CC_MISTAKES = {
+    "horizontal upwind reversed": ("cup = np.where(np.real(F) >= 0.0, c[:, :-1], c[:, 1:])",
+                                   "cup = np.where(np.real(F) >= 0.0, c[:, 1:], c[:, :-1])"),
+    "gravity with the reference density": ("((p[1:, :] - p[:-1, :]) / h + rhof * prm.g)",
+                                           "((p[1:, :] - p[:-1, :]) / h + prm.rho0 * prm.g)"),
+    "seaside distance h instead of h/2": ("q = -(K[:, -1] / prm.mu) * (pr - p[:, -1]) / (0.5 * h)",
+                                          "q = -(K[:, -1] / prm.mu) * (pr - p[:, -1]) / h"),
+    "salt scatter sign": ("    Rs[:, 1:] -= G\n", "    Rs[:, 1:] += G\n"),
+    "land-side diffusion distance h": ("rhob * PD[:, 0] * (cl - c[:, 0]) / (0.5 * h) * h",
+                                       "rhob * PD[:, 0] * (cl - c[:, 0]) / h * h"),
+    "storage without porosity": ("Rs = phi * (rho * c - rho_old * c_old) * V / tau",
+                                 "Rs = (rho * c - rho_old * c_old) * V / tau"),
+}
+
+
+def _planted_cc(name=None):
+    """A copy of oracle.henry with the named mistake planted (None: no
+    mistake) and a complex-step Jacobian."""
+    import os
+    import types
+    import scipy.sparse as sp
+    src = open(os.path.join(os.path.dirname(henry.__file__), "henry.py")).read()
+    if name is not None:
+        a, b = CC_MISTAKES[name]
+        assert src.count(a) == 1, name
+        src = src.replace(a, b)
+    mod = types.ModuleType("oracle._henry_planted")
+    mod.__package__ = "oracle"
+    exec(compile(src, "henry_planted", "exec"), mod.__dict__)
+
+    def cs_jacobian(prm, grid, coef, p, c, p_old, c_old, bc=None, step=1e-30):
+        # 5-point coupling: colour (i + 2 j) mod 5 separates a cell from its four neighbours
+        J_, I_ = np.meshgrid(np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
+        colour = (I_ + 2 * J_) % 5
+        rows, cols, vals = [], [], []
+        nbrs = [(0, 0), (0, 1), (0, -1), (1, 0), (-1, 0)]
+        for var in (0, 1):
+            for k in range(5):
+                mask = colour == k
+                pz, cz = p.astype(complex), c.astype(complex)
+                if var == 0:
+                    pz = pz + 1j * step * mask
+                else:
+                    cz = cz + 1j * step * mask
+                Rm, Rs = mod.residual(prm, grid, coef, pz, cz, p_old, c_old, bc=bc)
+                for dj, di in nbrs:
+                    jn, inn = J_ + dj, I_ + di
+                    ok = (jn >= 0) & (jn < grid.ny) & (inn >= 0) & (inn < grid.nx)
+                    ok &= ((inn + 2 * jn) % 5) == k
+                    for eq, R in ((0, Rm), (1, Rs)):
+                        d = R.imag / step
+                        sel = ok & (d != 0)
+                        rows.append((2 * (J_ * grid.nx + I_) + eq)[sel])
+                        cols.append((2 * (jn * grid.nx + inn) + var)[sel])
+                        vals.append(d[sel])
+        n = 2 * grid.ncell
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+    mod.jacobian = cs_jacobian
+    return mod
+
+
+def test_planted_copy_without_a_mistake_passes_the_pins(monkeypatch):
+    """The harness itself: an unplanted copy, with the complex-step Jacobian,
+    passes the physics pins, so a failure below is the planted mistake's."""
+    monkeypatch.setitem(globals(), "henry", _planted_cc())
+    test_constant_density_limit(6.6e-5)
+    test_bounds_and_salt_conservation()
+
+
+@pytest.mark.parametrize("name", sorted(CC_MISTAKES))
+def test_pins_detect_a_mistake_planted_in_the_source(name, monkeypatch):
+    monkeypatch.setitem(globals(), "henry", _planted_cc(name))
+    failed = []
+    for label, check in (("constant density", lambda: test_constant_density_limit(6.6e-5)),
+                         ("bounds and conservation", test_bounds_and_salt_conservation),
+                         ("manufactured solution", test_manufactured_solution_first_order)):
+        try:
+            check()
+        except AssertionError:
+            failed.append(label)
+            break
+    assert failed, name
