@@ -360,6 +360,22 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
                        const double* state_old_dev, const double* b_dev, double* x_dev, int32_t* iters_dev,
                        void* stream);
 
+/* a4 of the paper's own vertex-centred scheme (Sec. 2.3: two unknowns per
+ * grid vertex, n_l = 2 (nx+1)(ny+1) as in Table tab:adaptiveTS_times, a
+ * "consistent velocity" and partial upwinding; the readings are stated in
+ * henry_vc.cuh).  Three-parameter model only (EINVAL otherwise).
+ * state_dev, state_old_dev: [n][ny+1][nx+1][2] (p, c) at the vertices of
+ * `level` (nx = nx0 2^level, ny = ny0 2^level), natural order.
+ * R_dev[n][ny+1][nx+1][2] receives the unscaled residuals (fluid, salt), with
+ * the Dirichlet vertices' equations (x = Lx: p and c; x = 0: c) replaced by
+ * (value - boundary value) x rho0 h^2 / tau (p in units of rho0 g Ly).
+ * J_dev (may be NULL) receives [n][ny+1][nx+1][3][3][2][2]: for each vertex
+ * the 2x2 blocks d(R^m, R^s)/d(p, c) of the vertices (j+dj, i+di),
+ * dj, di in {-1, 0, 1} (zero outside the grid).  Asynchronous on `stream`
+ * (a stream-ordered scratch of n x 36 bytes). */
+int henry_vc_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                      const double* state_old_dev, double* R_dev, double* J_dev, void* stream);
+
 /* ---- Allocation-free variant of henry_level_batch_solve (the paper has no
  * counterpart: this is a deployment aid).  For callers that cannot call
  * cudaMalloc at run time - processes whose device memory is owned by another

@@ -34,6 +34,7 @@
 #include "henry_cta.cuh"
 #include "henry_kl.cuh"
 #include "henry_adjoint.cuh"
+#include "henry_vc.cuh"
 
 using namespace hk;
 
@@ -1277,6 +1278,22 @@ int step_entry(henry_handle* H, int which, int level, const double* xi, int n, c
   return HENRY_OK;
 }
 
+// Vertex-centred assembly (henry_vc.cuh): one thread per (sample, vertex);
+// states, residuals and Jacobian rows in the natural vertex order.
+__global__ void __launch_bounds__(TPB) k_vc_assemble(VcParams P, int B, const Coef* __restrict__ coef,
+                                                     const double* __restrict__ x, const double* __restrict__ xo,
+                                                     double* __restrict__ R, double* __restrict__ J) {
+  const int64_t nv = (int64_t)(P.nx + 1) * (P.ny + 1);
+  const int64_t t = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (t >= (int64_t)B * nv) return;
+  const int64_t s = t / nv;
+  const int v = (int)(t - s * nv);
+  const int j = v / (P.nx + 1), i = v - j * (P.nx + 1);
+  const Coef cf = coef[s];
+  const VcCoef c{cf.phi, cf.kmu, cf.PD, cf.qin};
+  vc_vertex(P, c, x + 2 * s * nv, xo + 2 * s * nv, j, i, R + 2 * t, J ? J + 36 * t : nullptr);
+}
+
 int check_step_args(henry_handle* h, int level, const double* xi, int n, const double* state,
                     const double* state_old) {
   if (!h) return set_err(HENRY_EINVAL, "handle is NULL");
@@ -1960,6 +1977,35 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
   if (rc) return rc;
   if (!b_dev || !x_dev) return set_err(HENRY_EINVAL, "NULL vector pointer");
   return STEP_DISPATCH(3, b_dev, x_dev, nullptr, iters_dev);
+}
+
+int henry_vc_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
+                      const double* state_old_dev, double* R_dev, double* J_dev, void* stream) {
+  int rc = check_step_args(h, level, xi_dev, n, state_dev, state_old_dev);
+  if (rc) return rc;
+  if (!R_dev) return set_err(HENRY_EINVAL, "R_dev is NULL");
+  const henry_config& c = h->cfg;
+  if (c.coef_model != HENRY_MODEL_UNIFORM3)
+    return set_err(HENRY_EINVAL, "the vertex-centred assembly supports the three-parameter model only");
+  cudaStream_t st = (cudaStream_t)stream;
+  const LevelGeom lg = geom(c, level);
+  const VcParams P{lg.nx, lg.ny, lg.h, lg.tau, c.rho0, c.rho1 - c.rho0, c.rho1, c.g, c.Ly};
+  const size_t cbytes = sizeof(Coef) * (size_t)n;
+  char* mem = nullptr;
+  if (cudaMallocAsync((void**)&mem, cbytes + sizeof(int) * (size_t)n, st) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(HENRY_ENOMEM, "cudaMallocAsync for %d samples' coefficients failed", n);
+  }
+  Coef* coef = (Coef*)mem;
+  int* status = (int*)(mem + cbytes);
+  const CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
+  k_coefficients<<<nblk(n, 128), 128, 0, st>>>(m, n, xi_dev, coef, status);
+  const int64_t total = (int64_t)n * (lg.nx + 1) * (lg.ny + 1);
+  k_vc_assemble<<<nblk(total), TPB, 0, st>>>(P, n, coef, state_dev, state_old_dev, R_dev, J_dev);
+  const cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(mem, st);
+  if (e != cudaSuccess) return set_err(HENRY_ECUDA, "vertex-centred assembly launch: %s", cudaGetErrorString(e));
+  return HENRY_OK;
 }
 
 }  // extern "C"

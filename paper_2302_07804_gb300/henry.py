@@ -27,7 +27,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint", "henry_n_qoi",
            "henry_paper_config", "henry_kl_basis", "henry_autotune", "henry_get_tuning",
-           "henry_set_tuning")
+           "henry_set_tuning", "henry_vc_assemble")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
 
@@ -110,6 +110,7 @@ def lib():
         L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_linear_solve.argtypes = [P, I, P, I, P, P, P, P, P, P]
+        L.henry_vc_assemble.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_level_batch_solve_static.argtypes = [ctypes.POINTER(HenryConfig), I, I, P, I, P, P, P, P]
         L.henry_profile.argtypes = [P, I]
         L.henry_profile_read.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
@@ -441,6 +442,22 @@ class Solver:
         _check(lib().henry_linear_solve(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(b),
                                         _ptr(x), _ptr(its), _stream(stream)))
         return x, its
+
+    def vc_assemble(self, level, xi, state, state_old, with_jacobian=True, stream=None):
+        """henry_vc_assemble: residual (n, ny+1, nx+1, 2) and Jacobian rows
+        (n, ny+1, nx+1, 3, 3, 2, 2) of the vertex-centred scheme at the vertex
+        states (n, ny+1, nx+1, 2)."""
+        ny, nx = self.grid(level)
+        n = state.shape[0]
+        _dev_f64(xi, (n, self.n_xi), "xi")
+        _dev_f64(state, (n, ny + 1, nx + 1, 2), "state")
+        _dev_f64(state_old, (n, ny + 1, nx + 1, 2), "state_old")
+        R = torch.empty_like(state)
+        J = torch.empty((n, ny + 1, nx + 1, 3, 3, 2, 2), dtype=torch.float64, device=state.device) \
+            if with_jacobian else None
+        _check(lib().henry_vc_assemble(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(R),
+                                       _ptr(J), _stream(stream)))
+        return R, J
 
 
 class _ScenarioQoI(torch.autograd.Function):
