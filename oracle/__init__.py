@@ -26,6 +26,8 @@ Contents, each function citing the passage of arXiv 2302.07804 it follows:
 * ``mg``      - the textbook definitions of the multigrid pieces the CUDA
   path uses (Galerkin coarse operator, red-black block Gauss-Seidel, V-cycle,
   right-preconditioned BiCGStab from the Templates book cited in Sec. 2.3).
+* ``mg_vc``   - the same multigrid pieces for the vertex-centred scheme
+  (vertex-nested grids, bilinear transfer, four-colour block Gauss-Seidel).
 * ``mlmc``    - the telescoping estimator (Eqs. EgL, A, Def. Yell), its
   variance, and the sample allocation of Eq. (M_ell), with two-pass moments.
 

@@ -166,7 +166,9 @@ def vcycle(ops, b, nu1=2, nu2=2, k=0):
 def bicgstab(A, b, precond, rtol, maxit=500):
     """Right-preconditioned BiCGStab (Templates book, Sec. 2.3.8, with the
     preconditioner applied on the right) from x = 0 with shadow residual
-    r_hat = b.  Returns (x, iterations, converged)."""
+    r_hat = b.  ``A``: a block stencil of this module, or any callable
+    z -> A z.  Returns (x, iterations, converged)."""
+    matvec = A if callable(A) else (lambda z: apply(A, z))
     x = np.zeros_like(b)
     r = b.copy()
     rh = b.copy()
@@ -181,11 +183,11 @@ def bicgstab(A, b, precond, rtol, maxit=500):
         beta = (rho / rho_prev) * (alpha / omega)
         p = r + beta * (p - omega * v)
         ph = precond(p)
-        v = apply(A, ph)
+        v = matvec(ph)
         alpha = rho / np.vdot(rh, v)
         s = r - alpha * v
         sh = precond(s)
-        t = apply(A, sh)
+        t = matvec(sh)
         omega = np.vdot(t, s) / np.vdot(t, t)
         x = x + alpha * ph + omega * sh
         r = s - omega * t
