@@ -55,7 +55,12 @@ def allocate(V, s, var_budget):
     """Eq. (M_ell): m_l = ceil(var_budget^-1 sqrt(V_l/s_l) sum_i sqrt(V_i s_i))."""
     V = [float(v) for v in V]
     s = [float(x) for x in s]
-    tot = sum(math.sqrt(v * c) for v, c in zip(V, s))
+    # plain FP64 accumulation, level by level: ceil() is an integer decision
+    # taken on a floating-point value, and both sides take it on the same
+    # value (Python's sum() of floats is compensated, so it is not used here)
+    tot = 0.0
+    for v, c in zip(V, s):
+        tot += math.sqrt(v * c)
     return [int(math.ceil(math.sqrt(v / c) * tot / var_budget)) for v, c in zip(V, s)]
 
 

@@ -1,0 +1,84 @@
+"""Property-based checks (hypothesis) of the host-side MLMC functions on
+random inputs: the sample allocation of Eq. (M_ell), the host merge of
+replica tables against the two-pass moments of the union, and the rate fit
+of Theorem costMLMC on exact power laws.  Skipped where hypothesis is not
+installed."""
+import math
+
+import numpy as np
+import pytest
+
+hyp = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st
+
+from oracle import mlmc as omlmc
+
+pos = st.floats(min_value=1e-8, max_value=1e3, allow_nan=False, allow_infinity=False)
+
+
+@pytest.fixture(scope="module")
+def henry():
+    from paper_2302_07804_gb300 import build, henry as h
+    build.build()
+    return h
+
+
+@settings(max_examples=60, deadline=None)
+@given(st.lists(st.tuples(pos, pos), min_size=1, max_size=7), st.floats(min_value=1e-9, max_value=1e-2))
+def test_allocation_properties(henry, levels, budget):
+    """m_l = ceil of the optimum of Eq. (M_ell): it meets the variance budget,
+    stays within one sample of the real optimum per level, follows the
+    oracle, and more samples go where V_l / s_l is larger."""
+    V = [v for v, _ in levels]
+    s = [c for _, c in levels]
+    m = henry.mlmc_allocate(V, s, budget)
+    assert m == omlmc.allocate(V, s, budget)
+    tot = math.fsum(math.sqrt(v * c) for v, c in levels)
+    for ml, v, c in zip(m, V, s):
+        opt = math.sqrt(v / c) * tot / budget      # the real optimum, to a few ulps
+        assert opt * (1 - 1e-14) <= ml < opt * (1 + 1e-14) + 1
+    assert math.fsum(v / ml for v, ml in zip(V, m)) <= budget * (1 + 1e-12)
+    for a in range(len(V)):
+        for b in range(len(V)):
+            if V[a] / s[a] > 1.01 * V[b] / s[b]:
+                assert m[a] >= m[b]
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.lists(st.integers(min_value=1, max_value=40), min_size=1, max_size=5), st.integers(0, 2 ** 31))
+def test_merged_replica_tables_equal_two_pass_moments(sizes, seed):
+    from paper_2302_07804_gb300 import mlmc
+    gen = np.random.default_rng(seed)
+    parts, data = [], []
+    for n in sizes:
+        y = gen.normal(gen.uniform(-5, 5), gen.uniform(0.01, 3.0), size=(n, 3))
+        data.append(y)
+        t = np.zeros((2, 3, 3))
+        t[:, :, 0] = n
+        t[:, :, 1] = y.mean(axis=0)
+        t[:, :, 2] = ((y - y.mean(axis=0)) ** 2).sum(axis=0)
+        parts.append(t)
+    merged = mlmc.merge_sums(parts).numpy()
+    allv = np.concatenate(data)
+    n, mean, m2 = omlmc.two_pass_moments(allv)
+    assert np.all(merged[0, :, 0] == n)
+    np.testing.assert_allclose(merged[0, :, 1], mean, rtol=1e-12, atol=1e-12 * np.abs(allv).max())
+    np.testing.assert_allclose(merged[0, :, 2], m2, rtol=1e-10, atol=1e-10 * max(1.0, m2.max()))
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.floats(0.3, 3.0), st.floats(0.3, 4.0), st.floats(0.5, 4.0), st.floats(1e-4, 1.0),
+       st.integers(3, 7), st.integers(0, 2))
+def test_rates_recover_exact_power_laws(henry, alpha, beta, gamma, c0, n_levels, first):
+    """|E Y_l| = c0 2^(-alpha l), V_l = c0 2^(-beta l), s_l = 2^(gamma l) give
+    exactly (alpha, beta, gamma) from any first level; both sides agree."""
+    if n_levels - first < 2:
+        return
+    l = np.arange(n_levels)
+    means = list(c0 * 2.0 ** (-alpha * l))
+    V = list(c0 * 2.0 ** (-beta * l))
+    s = list(2.0 ** (gamma * l))
+    a, b, g = henry.mlmc_rates(means, V, s, first_level=first)
+    assert a == pytest.approx(alpha, rel=1e-9, abs=0) and b == pytest.approx(beta, rel=1e-9, abs=0)
+    assert g == pytest.approx(gamma, rel=1e-9, abs=0)
+    np.testing.assert_allclose((a, b, g), omlmc.rates(means, V, s, first_level=first), rtol=1e-12)
