@@ -82,3 +82,26 @@ def test_rates_recover_exact_power_laws(henry, alpha, beta, gamma, c0, n_levels,
     assert a == pytest.approx(alpha, rel=1e-9, abs=0) and b == pytest.approx(beta, rel=1e-9, abs=0)
     assert g == pytest.approx(gamma, rel=1e-9, abs=0)
     np.testing.assert_allclose((a, b, g), omlmc.rates(means, V, s, first_level=first), rtol=1e-12)
+
+
+@settings(max_examples=8, deadline=None)
+@given(st.floats(min_value=0.1, max_value=1.2), st.integers(min_value=1, max_value=64))
+def test_kl_basis_agrees_with_the_oracle_to_its_conditioning(henry, ell, terms):
+    """The library's KL basis (cyclic Jacobi) against the oracle's (LAPACK)
+    for any correlation length and number of terms.  Eigenvalues far below
+    the largest are fixed only to rounding of the largest, and so are their
+    modes, so the comparison is absolute in lam_max: the eigenvalues to
+    1e-13 lam_max, and the field contributions sqrt(lam_k) psi_k to
+    1e-9 sqrt(lam_max)."""
+    from oracle import henry as oh
+    from oracle import kl as okl
+    sl, modes = henry.kl_basis(0, kl_terms=terms, kl_corr_len=ell)
+    b = okl.KLBasis(n_terms=terms, ell=ell)
+    grid = oh.Grid.level(oh.Params(), 0)
+    xc = (np.arange(grid.nx) + 0.5) * grid.h
+    yc = (np.arange(grid.ny) + 0.5) * grid.h
+    lmax = b.lam.max()
+    assert np.abs(sl ** 2 - b.lam).max() <= 1e-13 * lmax
+    f_lib = sl[:, None, None] * modes
+    f_orc = np.sqrt(b.lam)[:, None, None] * b.modes(xc, yc)
+    assert np.abs(f_lib - f_orc).max() <= 1e-9 * np.sqrt(lmax)
