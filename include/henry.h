@@ -216,7 +216,9 @@ int henry_n_qoi(const henry_config* cfg);
 /* Create a handle for `cfg` (copied).  Allocates no device memory yet.
  * Errors: EINVAL on a NULL pointer, inconsistent grid sizes (nx0 = 2 ny0 with
  * ny0 a power of two >= 4, Lx = 2 Ly, max_level in [0, 8]), a finest level
- * past 2^30 cells per sample or 2^30 time steps, an unknown enum value, or
+ * past 2^30 cells per sample or 2^30 time steps, an unknown enum value, a
+ * floating-point setting that is NaN or infinite, a non-positive physical
+ * constant (Lx, Ly, T, rho0, rho1, mu, g, Dm, K_mean; 0 < phi_mean < 1) or
  * non-positive solver settings. */
 int henry_create(const henry_config* cfg, henry_handle** out);
 

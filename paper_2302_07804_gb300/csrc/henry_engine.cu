@@ -1306,6 +1306,18 @@ int check_step_args(henry_handle* h, int level, const double* xi, int n, const d
 // Configuration checks shared by henry_create and the allocation-free entry
 // point (which has no workspace_bytes budget: with_workspace false).
 int check_config(const henry_config& c, bool with_workspace) {
+  // every floating-point setting finite (a NaN would pass the comparisons below)
+  const double reals[] = {c.Lx, c.Ly, c.T, c.rho0, c.rho1, c.mu, c.g, c.Dm, c.phi_mean, c.K_mean, c.qin_mean,
+                          c.phi_amp, c.logK_amp, c.qin_amp, c.newton_atol, c.newton_dxtol, c.lin_rtol,
+                          c.newton_predictor, c.newton_dc_limit, c.kl_corr_len, c.kl_sigma_logK, c.kl_sigma_phi,
+                          c.phi_lo, c.phi_hi, c.adj_rtol};
+  for (double v : reals)
+    if (!std::isfinite(v)) return set_err(HENRY_EINVAL, "a floating-point setting is NaN or infinite");
+  if (with_workspace && !std::isfinite(c.workspace_bytes))
+    return set_err(HENRY_EINVAL, "workspace_bytes is NaN or infinite");
+  if (!(c.rho0 > 0) || !(c.rho1 > 0) || !(c.mu > 0) || !(c.g > 0) || !(c.Dm > 0) || !(c.K_mean > 0) ||
+      !(c.phi_mean > 0 && c.phi_mean < 1) || !(c.newton_atol >= 0) || !(c.newton_dxtol >= 0))
+    return set_err(HENRY_EINVAL, "physical constants must be positive (0 < phi_mean < 1), tolerances >= 0");
   if (c.ny0 < 4 || (c.ny0 & (c.ny0 - 1)) != 0 || (int64_t)c.nx0 != 2 * (int64_t)c.ny0)
     return set_err(HENRY_EINVAL, "grid must be nx0 = 2 ny0 with ny0 a power of two >= 4 (got %d x %d)", c.nx0, c.ny0);
   if (std::fabs(c.Lx - 2.0 * c.Ly) > 1e-12 * c.Lx || c.Ly <= 0)

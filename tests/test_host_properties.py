@@ -105,3 +105,54 @@ def test_kl_basis_agrees_with_the_oracle_to_its_conditioning(henry, ell, terms):
     f_lib = sl[:, None, None] * modes
     f_orc = np.sqrt(b.lam)[:, None, None] * b.modes(xc, yc)
     assert np.abs(f_lib - f_orc).max() <= 1e-9 * np.sqrt(lmax)
+
+
+ints = st.one_of(st.integers(min_value=-3, max_value=70), st.sampled_from([0, 1 << 20, 1 << 29, (1 << 31) - 1, -(1 << 31)]))
+reals = st.one_of(st.floats(allow_nan=True, allow_infinity=True, width=64), st.sampled_from([0.0, -1.0, 1e-300]))
+
+
+@settings(max_examples=300, deadline=None)
+@given(ny0=st.one_of(st.sampled_from([4, 8, 16, 32, 64]), ints), max_level=ints, steps0=ints, precision=ints,
+       coef_model=ints, qoi_set=ints, T=reals, lin_rtol=reals, Ly=st.sampled_from([1.0, 0.5, -1.0, 0.0]))
+def test_create_accepts_only_valid_configurations(henry, ny0, max_level, steps0, precision, coef_model, qoi_set, T,
+                                                   lin_rtol, Ly):
+    """henry_create on random configurations (host only; no device memory is
+    touched): it returns OK or EINVAL, never anything else, and a
+    configuration it accepts satisfies the documented rules."""
+    import ctypes
+    cfg = henry.default_config()
+    nx0 = 2 * ny0 if -(1 << 30) < ny0 < (1 << 30) else ny0
+    for k, v in dict(ny0=ny0, nx0=nx0, max_level=max_level, steps0=steps0, precision=precision,
+                     coef_model=coef_model, qoi_set=qoi_set, T=T, lin_rtol=lin_rtol, Ly=Ly, Lx=2 * Ly).items():
+        setattr(cfg, k, v)
+    h = ctypes.c_void_p()
+    rc = henry.lib().henry_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert rc in (henry.HENRY_OK, henry.HENRY_EINVAL)
+    if rc == henry.HENRY_OK:
+        henry.lib().henry_destroy(h)
+        assert ny0 >= 4 and ny0 & (ny0 - 1) == 0 and 0 <= max_level <= 8
+        assert ((2 * ny0) << max_level) * (ny0 << max_level) <= 1 << 30 and 0 < steps0 <= (1 << 30) >> max_level
+        assert precision in (henry.HENRY_FP64, henry.HENRY_MIXED) and 0 <= coef_model <= 2 and 0 <= qoi_set <= 3
+        assert math.isfinite(T) and T > 0 and math.isfinite(lin_rtol) and lin_rtol > 0 and Ly > 0
+    else:
+        assert henry.lib().henry_last_error()
+
+
+def test_create_rejects_nan_and_non_positive_physics(henry):
+    import ctypes
+    fields = ("Lx", "Ly", "T", "rho0", "rho1", "mu", "g", "Dm", "phi_mean", "K_mean", "qin_mean", "phi_amp",
+              "logK_amp", "qin_amp", "newton_atol", "newton_dxtol", "lin_rtol", "workspace_bytes",
+              "newton_predictor", "newton_dc_limit", "kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo",
+              "phi_hi", "adj_rtol")
+    for f in fields:
+        for bad in (math.nan, math.inf):
+            cfg = henry.default_config()
+            setattr(cfg, f, bad)
+            h = ctypes.c_void_p()
+            assert henry.lib().henry_create(ctypes.byref(cfg), ctypes.byref(h)) == henry.HENRY_EINVAL, (f, bad)
+    for f, bad in (("rho0", 0.0), ("mu", -1e-3), ("g", 0.0), ("Dm", 0.0), ("K_mean", 0.0), ("phi_mean", 1.0),
+                   ("newton_atol", -1.0)):
+        cfg = henry.default_config()
+        setattr(cfg, f, bad)
+        h = ctypes.c_void_p()
+        assert henry.lib().henry_create(ctypes.byref(cfg), ctypes.byref(h)) == henry.HENRY_EINVAL, (f, bad)
