@@ -1943,7 +1943,8 @@ int mlmc_rates(int n_levels, int first_level, const double* mean_Y, const double
 int mlmc_bias_test(int n_levels, const double* mean_Y, double alpha, double eps, double* bias_est,
                    int32_t* converged) {
   if (n_levels < 2 || !mean_Y) return set_err(HENRY_EINVAL, "need at least two levels");
-  if (!(alpha > 0.0) || !(eps > 0.0)) return set_err(HENRY_EINVAL, "alpha and eps must be positive");
+  if (!(alpha > 0.0) || !(eps > 0.0) || !std::isfinite(alpha) || !std::isfinite(eps))
+    return set_err(HENRY_EINVAL, "alpha and eps must be positive and finite");
   const double b = std::fabs(mean_Y[n_levels - 1]) / (std::exp2(alpha) - 1.0);
   if (!std::isfinite(b)) return set_err(HENRY_EINVAL, "mean_Y[%d] is not finite", n_levels - 1);
   if (bias_est) *bias_est = b;

@@ -144,7 +144,8 @@ def test_mlmc_rates_reject_bad_input(L):
             henry.mlmc_rates(*args[:3], first_level=args[3])
         assert e.value.code == henry.HENRY_EINVAL
     for args in (([1.0], 1.0, 1e-3), ([1.0, 0.5], 0.0, 1e-3), ([1.0, 0.5], 1.0, 0.0),
-                 ([1.0, float("nan")], 1.0, 1e-3)):
+                 ([1.0, float("nan")], 1.0, 1e-3), ([1.0, 0.5], float("inf"), 1e-3),
+                 ([1.0, 0.5], float("nan"), 1e-3), ([1.0, 0.5], 1.0, float("inf"))):
         with pytest.raises(henry.HenryError):
             henry.mlmc_bias_test(*args)
 
