@@ -22,7 +22,8 @@ Contents, each function citing the passage of arXiv 2302.07804 it follows:
   per grid vertex, Sec. 2.3 and Table tab:adaptiveTS_times), with the
   readings of its "consistent velocity" and partial upwinding stated in the
   module; the same equations, boundary conditions, time stepping and QoIs.
-  No CUDA counterpart yet: it fixes the target of that path.
+  Its CUDA counterpart so far is the assembly (``henry_vc_assemble``); the
+  oracle fixes the target of the rest of that path.
 * ``mg``      - the textbook definitions of the multigrid pieces the CUDA
   path uses (Galerkin coarse operator, red-black block Gauss-Seidel, V-cycle,
   right-preconditioned BiCGStab from the Templates book cited in Sec. 2.3).
