@@ -97,3 +97,48 @@ def test_host_build_of_the_kernel_math_matches_the_oracle(harness, level, xi, sp
     if qscale > 1:
         up = sum(int(np.sum(np.abs(F) * 2 > (vc.density(PRM, 0.5) * coef.phi * PRM.Dm))) for _, _, F, _ in fl)
         assert up > 0
+
+
+def _csr_from_blocks(J, grid):
+    import scipy.sparse as sp
+    ny1, nx1 = grid.ny + 1, grid.nx + 1
+    rows, cols, vals = [], [], []
+    Jg, Ig = np.meshgrid(np.arange(ny1), np.arange(nx1), indexing="ij")
+    for dj in (-1, 0, 1):
+        for di in (-1, 0, 1):
+            jn, inb = Jg + dj, Ig + di
+            ok = (jn >= 0) & (jn < ny1) & (inb >= 0) & (inb < nx1)
+            for eq in (0, 1):
+                for var in (0, 1):
+                    rows.append((2 * (Jg * nx1 + Ig) + eq)[ok])
+                    cols.append((2 * (jn * nx1 + inb) + var)[ok])
+                    vals.append(J[..., dj + 1, di + 1, eq, var][ok])
+    n = 2 * ny1 * nx1
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def test_scenario_solved_with_the_kernel_math_matches_the_oracle(harness):
+    """A whole level-0 scenario (20 implicit steps): Newton on the residual and
+    Jacobian of the host build of the kernel arithmetic, with sparse direct
+    solves, against the oracle's own solve; the QoIs agree to 1e-10."""
+    import scipy.sparse.linalg as spla
+    xi = [0.4, -0.6, 0.3]
+    grid = vc.Grid.level(PRM, 0)
+    coef = cc.coefficients(PRM, grid, xi)
+    p, c = vc.initial_state(PRM, grid)
+    sc = vc.residual_scale(PRM, grid)
+    for _ in range(grid.steps):
+        po, co = p, c
+        for it in range(PRM.newton_maxit):
+            R, J = host_assemble(harness, PRM, grid, coef, p, c, po, co)
+            if np.abs(R).max() / sc <= PRM.newton_atol:
+                break
+            dx = spla.spsolve(_csr_from_blocks(J, grid).tocsc(), -R.ravel()).reshape(R.shape)
+            p, c = p + dx[..., 0], c + dx[..., 1]
+        else:
+            pytest.fail("Newton did not converge")
+    q_kernel = vc.qoi(PRM, grid, coef, p, c)
+    q_oracle, ok = vc.solve_scenario(PRM, 0, xi)
+    assert ok
+    assert q_kernel[0] == pytest.approx(q_oracle[0], rel=1e-10, abs=0)
+    assert q_kernel[1] == pytest.approx(q_oracle[1], rel=0, abs=1e-10)
