@@ -156,3 +156,35 @@ def test_create_rejects_nan_and_non_positive_physics(henry):
         setattr(cfg, f, bad)
         h = ctypes.c_void_p()
         assert henry.lib().henry_create(ctypes.byref(cfg), ctypes.byref(h)) == henry.HENRY_EINVAL, (f, bad)
+
+
+anyf = st.floats(allow_nan=True, allow_infinity=True, width=64)
+
+
+@settings(max_examples=300, deadline=None)
+@given(st.lists(st.tuples(anyf, anyf, anyf), min_size=1, max_size=6), anyf, anyf, st.integers(-1, 6))
+def test_host_mlmc_functions_on_arbitrary_doubles(henry, rows, budget, alpha, first):
+    """mlmc_allocate, mlmc_rates and mlmc_bias_test on any doubles (NaN,
+    infinities, negatives, denormals): OK or EINVAL, and an OK result is
+    finite and in range."""
+    import ctypes
+    L = henry.lib()
+    n = len(rows)
+    mean = (ctypes.c_double * n)(*[r[0] for r in rows])
+    V = (ctypes.c_double * n)(*[r[1] for r in rows])
+    s = (ctypes.c_double * n)(*[r[2] for r in rows])
+    m = (ctypes.c_int64 * n)()
+    rc = L.mlmc_allocate(n, V, s, budget, m)
+    assert rc in (henry.HENRY_OK, henry.HENRY_EINVAL)
+    if rc == henry.HENRY_OK:
+        assert all(0 <= v < 9.0e18 for v in m)
+    a, b, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = L.mlmc_rates(n, first, mean, V, s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(g))
+    assert rc in (henry.HENRY_OK, henry.HENRY_EINVAL)
+    if rc == henry.HENRY_OK:
+        assert all(math.isfinite(x.value) for x in (a, b, g))
+    bias, ok = ctypes.c_double(), ctypes.c_int32()
+    rc = L.mlmc_bias_test(n, mean, alpha, budget, ctypes.byref(bias), ctypes.byref(ok))
+    assert rc in (henry.HENRY_OK, henry.HENRY_EINVAL)
+    if rc == henry.HENRY_OK:
+        assert math.isfinite(bias.value) and bias.value >= 0 and ok.value in (0, 1)
