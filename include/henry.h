@@ -150,6 +150,18 @@ typedef struct {
   int32_t tile_assembly; /* 1 (default): face-once assembly in tiles of 256 cells (whole rows up to 256 cells
                             wide, else 128 x 2 blocks), every face inside a tile evaluated once; 0: every
                             cell evaluates its four faces.  Same values up to rounding */
+  int32_t newton_residual_first; /* Newton iterations with this index (0 = the step's first residual) or later
+                                    evaluate the fine residual alone first and assemble the Jacobian only for
+                                    the samples that do not pass the residual test (default 2: after two
+                                    updates, when most samples have converged); < 0: always residual and
+                                    Jacobian together.  Same values either way */
+  int32_t mg_tail_cells; /* the V-cycle's coarse levels from the first one with at most this many cells per
+                            sample down to the coarsest run as one kernel, one CTA per sample with those
+                            levels' operators and vectors in shared memory (default 128: 16 x 8 cells and
+                            below); 0: every level as separate kernels.  Same values either way */
+  int32_t mg_tail_batch_cells; /* ... only while the batch times that level's cells per sample is at most this
+                                  (default 2^20; 0: no limit): large batches of small grids run those levels
+                                  as separate, large launches */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -174,9 +186,12 @@ void henry_paper_config(henry_config* cfg);
 /* Project autotuner.  Solver settings that change only how fast a solve
  * converges, never where (the FP64 Newton test decides): the Krylov tolerance,
  * the V-cycle's smoothing counts and, where the level's grid allows it, the
- * fused one-CTA-per-sample solver.  henry_autotune times every candidate -
- * lin_rtol in {1e-4, 1e-3, 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x
- * (fused small-grid solver on / off where eligible) - on n_trial samples
+ * fused one-CTA-per-sample solver; then, one at a time from the best so far,
+ * the fused multigrid tail (mg_tail_cells in {0, 128, 512}) and the
+ * residual-first Newton test (newton_residual_first in {-1, 1, 2}).
+ * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
+ * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
+ * off where eligible), then the two later stages - on n_trial samples
  * xi_dev[n_trial][n_xi] of `level` (with their coarse partners if
  * with_coarse), after one untimed warm-up, with CUDA events on `stream`, and
  * keeps the fastest candidate that solves every sample for that level of
@@ -190,6 +205,7 @@ typedef struct {
   double lin_rtol;
   int32_t nu1, nu2, fused_small_grids;
   double cell_steps_per_s; /* measured on the trial batch (0 for the configuration's own settings) */
+  int32_t mg_tail_cells, newton_residual_first; /* as in henry_config */
 } henry_tuning;
 int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
                    henry_tuning* best_out, void* stream);
@@ -336,6 +352,8 @@ int mlmc_bias_test(int n_levels, const double* mean_Y_host, double alpha, double
 
 /* a4. F_dev[n][ny][nx][2] = scaled residual (fluid mass, salt mass) and, if
  * J_dev is not NULL, J_dev[n][ny][nx][5][2][2] = scaled Jacobian blocks
+ * (J_dev NULL: the residual alone, by the residual-only kernel of the Newton
+ * test, bit-identical to the residual assembled with the Jacobian)
  * coupling each cell to (self, west, east, south, north) neighbour; block
  * [eq][var], eq 0 = fluid mass, 1 = salt; var 0 = p, 1 = c; zero across the
  * domain boundary.  In HENRY_MIXED the blocks are the FP32 copy the solver
@@ -373,8 +391,11 @@ int henry_linear_solve(henry_handle* h, int level, const double* xi_dev, int n, 
  * (value - boundary value) x rho0 h^2 / tau (p in units of rho0 g Ly).
  * J_dev (may be NULL) receives [n][ny+1][nx+1][3][3][2][2]: for each vertex
  * the 2x2 blocks d(R^m, R^s)/d(p, c) of the vertices (j+dj, i+di),
- * dj, di in {-1, 0, 1} (zero outside the grid).  Asynchronous on `stream`
- * (a stream-ordered scratch of n x 36 bytes). */
+ * dj, di in {-1, 0, 1} (zero outside the grid).  The coefficients are
+ * checked first: a sample whose xi gives phi outside (0, 1) or a non-finite
+ * K or q_in makes the call return HENRY_EINVAL, naming the first such sample,
+ * with nothing assembled.  Synchronises `stream` for that check (a
+ * stream-ordered scratch of n x 36 + 4 bytes). */
 int henry_vc_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
                       const double* state_old_dev, double* R_dev, double* J_dev, void* stream);
 
@@ -392,7 +413,8 @@ int henry_vc_assemble(henry_handle* h, int level, const double* xi_dev, int n, c
  * default configuration up to 64 level-0 samples in FP64 - otherwise
  * HENRY_EINVAL with a message giving the sizes.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress with that
- * device current): make that first call before any stream capture.  All
+ * device current), a set-up step: make that first call before any stream
+ * capture begins.  All
  * calls share the array and host counter words; calls that overlap on the GPU
  * or across host threads race.  Only the three-parameter model and the two
  * standard QoIs (qoi_set 0) are accepted (HENRY_EINVAL otherwise).
@@ -416,7 +438,10 @@ enum {
   HENRY_K_QOI = 9,               /* a2, a3, a11: coefficients, initial state, QoIs */
   HENRY_K_FUSED = 10,            /* a3-a11 for a small grid: the one-CTA-per-sample solver */
   HENRY_K_SMOOTH_COARSE = 11,    /* a7: the same half-sweeps on the coarser multigrid levels */
-  HENRY_K_COUNT = 12
+  HENRY_K_RESIDUAL = 12,         /* a4: fine-grid residual alone (the Newton test before a Jacobian is needed) */
+  HENRY_K_MG_TAIL = 13,          /* a7: the fused V-cycle below mg_tail_cells (sweeps, restrictions, coarsest
+                                    solve of those levels in one kernel) */
+  HENRY_K_COUNT = 14
 };
 
 /* Start (enable != 0: counters reset) or stop timing on this handle.  While

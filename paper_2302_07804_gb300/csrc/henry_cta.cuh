@@ -477,3 +477,103 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant
 }
 
 }  // namespace hk
+
+namespace hk {
+
+// ---------------------------------------------------------------------------
+// a7, fused multigrid tail: the part of a V-cycle below a coarse level kt,
+// i.e. the V(nu1, nu2) cycle that solves A_kt x_kt = b_kt approximately from
+// x_kt = 0, run by one CTA per sample with every tail level's operator and
+// vectors in shared memory.  The multi-kernel V-cycle launches ~9 kernels per
+// coarse level (sweeps, residual + restriction) on grids of 128 cells per
+// sample or fewer; here the sample's coarse operators are read from global
+// memory once per V-cycle and every phase of those levels costs a CTA barrier
+// instead of a kernel launch.  The arithmetic is cta_vcycle's, which is the
+// multi-kernel cycle's per cell and in the same order (sweep_cell,
+// restrict_cell, the coarsest 4 x 4 product), so the result is bit-identical
+// to the multi-kernel V-cycle's.
+
+// Shared-memory layout of a tail starting on an nx x ny grid: per level the
+// 6 block planes and the multigrid vectors x, b (level 0 of the layout is the
+// tail's first level kt), the coarsest inverse and a reduction buffer.
+__host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayout* L) {
+  const int b4 = 4 * tsize, v2 = 2 * tsize;
+  int o = 0, k = 0, nx = nx0, ny = ny0;
+  for (;;) {
+    if (k >= CTA_MAX_LEVELS) return false;
+    const int N = nx * ny;
+    L->nx[k] = nx;
+    L->ny[k] = ny;
+    L->J[k] = o; o = cta_align(o + 6 * b4 * N);
+    L->MX[k] = o; o = cta_align(o + v2 * N);
+    L->MB[k] = o; o = cta_align(o + v2 * N);
+    L->X[k] = L->XO[k] = -1;
+    if (nx <= 2 || ny <= 1) break;
+    nx >>= 1;
+    ny >>= 1;
+    ++k;
+  }
+  L->K = k;
+  L->r = L->rh = L->p = L->v = L->t = L->ph = L->dx = -1;
+  L->ainv = o; o = cta_align(o + 16 * tsize);
+  L->red = o; o = cta_align(o + 40 * 8);
+  L->bytes = o + 32;
+  return true;
+}
+
+// Global-memory operands of the tail, by tail level: the level's block planes
+// (6 planes of plane[k] blocks, a sample's N_k blocks at offset s N_k), the
+// right-hand side b and result x of the first level ([B][N_0] vectors), and
+// the coarsest inverses ([B][16]).
+struct TailArgs {
+  const void* J[CTA_MAX_LEVELS];
+  int64_t plane[CTA_MAX_LEVELS];
+  const void* b;
+  void* x;
+  const void* ainv;
+};
+
+// Copy n 16-byte words from global to shared memory (all threads of the CTA).
+__device__ __forceinline__ void cta_copy16(void* dst, const void* src, int n) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+constexpr int TAIL_MAX_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_MAX_THREADS) k_vcycle_tail(const __grid_constant__ CtaLayout L,
+                                                                  const __grid_constant__ TailArgs A, int B, int nu1,
+                                                                  int nu2, const int* __restrict__ active) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  extern __shared__ unsigned char smem_raw[];
+  const int s = blockIdx.x;
+  if (s >= B || !active[s]) return;
+  CtaSmem<T> S;
+  S.base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 31) & ~uintptr_t(31));
+  S.L = &L;
+  const int K = L.K;
+  // the sample's operators of every tail level: 6 contiguous runs of N_k blocks
+  for (int k = 0; k <= K; ++k) {
+    const int N = L.nx[k] * L.ny[k];
+    const int words = N * (int)sizeof(B4) / 16;
+    const B4* Jg = reinterpret_cast<const B4*>(A.J[k]) + (int64_t)s * N;
+    B4* Js = S.J(k);
+    for (int q = 0; q < 6; ++q) cta_copy16(Js + q * N, Jg + q * A.plane[k], words);
+  }
+  const int N0 = L.nx[0] * L.ny[0];
+  cta_copy16(S.MB(0), reinterpret_cast<const V2*>(A.b) + (int64_t)s * N0, N0 * (int)sizeof(V2) / 16);
+  {
+    const T* ai = reinterpret_cast<const T*>(A.ainv) + (int64_t)s * 16;
+    for (int i = threadIdx.x; i < 16; i += blockDim.x) S.ainv()[i] = ai[i];
+  }
+  __syncthreads();
+  cta_vcycle<T>(S, nu1, nu2, S.MB(0), S.MX(0));  // ends with a barrier
+  V2* xg = reinterpret_cast<V2*>(A.x) + (int64_t)s * N0;
+  const V2* xs = S.MX(0);
+  for (int i = threadIdx.x; i < N0; i += blockDim.x) xg[i] = xs[i];
+}
+
+}  // namespace hk

@@ -309,12 +309,13 @@ void prof_drain(henry_handle* H) {
 // whole rows per tile where they fit (nx <= TPB), else 128 x 2 blocks; the
 // per-cell form with tile_assembly = 0 (same arguments, same results up to
 // rounding).
-template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
-auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, FINE, FIELDS, DROP>) {
-  if (!c.tile_assembly) return &k_assemble<T, FINE, FIELDS, DROP>;
-  if (nx <= TPB) return &k_assemble_tile<T, FINE, FIELDS, DROP>;
-  if (nx % TILE_W == 0) return &k_assemble_tile2d<T, FINE, FIELDS, DROP>;  // N % TPB == 0 follows
-  return &k_assemble<T, FINE, FIELDS, DROP>;
+// JAC = false: the fine residual alone (same values as with JAC = true).
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
+auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, FINE, FIELDS, DROP, JAC>) {
+  if (!c.tile_assembly) return &k_assemble<T, FINE, FIELDS, DROP, JAC>;
+  if (nx <= TPB) return &k_assemble_tile<T, FINE, FIELDS, DROP, JAC>;
+  if (nx % TILE_W == 0) return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC>;  // N % TPB == 0 follows
+  return &k_assemble<T, FINE, FIELDS, DROP, JAC>;
 }
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
 int qoi_count(const henry_config& c) {
@@ -390,6 +391,33 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   return L->bytes <= optin;
 }
 
+// The device's opt-in shared memory per CTA (cached per device; 0 on error).
+int smem_optin() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  int optin = g_smem_optin[dev].load(std::memory_order_relaxed);
+  if (!optin) {
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    g_smem_optin[dev].store(optin, std::memory_order_relaxed);
+  }
+  return optin;
+}
+
+// Let the fused multigrid tail kernel use up to the opt-in shared memory
+// (once per device and precision; outside any stream capture).
+template <typename T>
+int ensure_tail_attr() {
+  static std::atomic<int> done[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_err(HENRY_EINVAL, "device %d outside [0, 64)", dev);
+  if (done[dev].load(std::memory_order_relaxed)) return HENRY_OK;
+  const int optin = smem_optin();
+  if (optin > 0) CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  done[dev].store(1, std::memory_order_relaxed);
+  return HENRY_OK;
+}
+
 template <typename T>
 std::map<int, Group<T>>& groups(henry_handle* h);
 template <>
@@ -426,6 +454,10 @@ int get_group(henry_handle* H, int level, int B, Group<T>** out, bool light = fa
   g.mem = mem;
   g.bytes = bytes;
   g.carve(mem, B, lg.nx, lg.ny, lg.h, light, has_fields(H->cfg));
+  if (!light) {
+    const int rc = ensure_tail_attr<T>();
+    if (rc) return rc;
+  }
   g.level = level;
   g.Bcap = B;
   *out = &g;
@@ -573,6 +605,24 @@ int restrict_states(henry_handle* H, Group<T>& G, int B, bool old, const int* ac
   return HENRY_OK;
 }
 
+// First multigrid level of the fused tail: the first coarse level (k >= 1)
+// with at most mg_tail_cells cells per sample, if the tail below it has at
+// least two levels, its shared-memory layout fits and the batch is small
+// enough (B x cells of that level <= mg_tail_batch_cells; larger batches keep
+// those levels as separate kernels, which then are large launches and fill
+// the FP64 pipe better than the tail's partly idle warps); -1: no tail.
+template <typename T>
+int tail_level(const henry_config& c, const Group<T>& G, int B, CtaLayout* L) {
+  if (c.mg_tail_cells <= 0) return -1;
+  for (int k = 1; k < G.K; ++k) {
+    if (G.lv[k].N > c.mg_tail_cells) continue;
+    if (c.mg_tail_batch_cells > 0 && (double)B * G.lv[k].N > (double)c.mg_tail_batch_cells) return -1;
+    if (!tail_layout(G.lv[k].nx, G.lv[k].ny, (int)sizeof(T), L) || L->bytes > smem_optin()) return -1;
+    return k;
+  }
+  return -1;
+}
+
 // One V(nu1, nu2) cycle: x0 = M^{-1} b0 on the fine level (active = lin_active).
 template <typename T>
 int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, typename VT<T>::v2* x0,
@@ -583,7 +633,10 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
   const int* act = G.lin_active;
   const double na = H->nact;
   const double b4 = sizeof(B4), v2 = sizeof(V2);
-  for (int k = 0; k < G.K; ++k) {
+  CtaLayout TL;
+  const int kt = tail_level<T>(H->cfg, G, B, &TL);
+  const int kend = kt > 0 ? kt : G.K;  // levels 0 .. kend - 1 run as separate kernels
+  for (int k = 0; k < kend; ++k) {
     Level& L = G.lv[k];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
@@ -616,14 +669,37 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     }
     CKL();
   }
-  {
+  if (kt > 0) {  // levels kt .. K: one CTA per sample in shared memory
+    TailArgs A;
+    std::memset(&A, 0, sizeof A);
+    double tb = 2.0 * G.lv[kt].N * v2 + 16.0 * sizeof(T), tf = 0.0;
+    for (int k = kt; k <= G.K; ++k) {
+      const Level& L = G.lv[k];
+      A.J[k - kt] = L.J;
+      A.plane[k - kt] = L.plane;
+      tb += 6.0 * L.N * b4;
+      if (k < G.K)
+        tf += (nu1 > 0 ? sweep_flops(L.nx, L.ny, 0) + (2 * nu1 - 1) * sweep_flops(L.nx, L.ny, 1) +
+                             restrict_flops(L.nx, L.ny)
+                       : 0.0) +
+              2 * nu2 * sweep_flops(L.nx, L.ny, 1) + (nu2 > 0 ? L.N : 0);
+    }
+    A.b = G.lv[kt].mgb;
+    A.x = G.lv[kt].mgx;
+    A.ainv = G.Ainv;
+    const int thr = std::min(TAIL_MAX_THREADS, std::max(32, ((G.lv[kt].N / 2 + 31) / 32) * 32));
+    launch(H, st, HENRY_K_MG_TAIL, na * tb, na * (tf + 32.0), [&] {
+      k_vcycle_tail<T><<<B, thr, TL.bytes, st>>>(TL, A, B, nu1, nu2, act);
+    });
+    CKL();
+  } else {
     Level& Lc = G.lv[G.K];
     launch(H, st, HENRY_K_COARSE_SOLVE, na * (16.0 * sizeof(T) + 4 * v2), [&] {
       k_coarse_solve<T><<<nblk(B, 64), 64, 0, st>>>(B, G.Ainv, (const V2*)Lc.mgb, (V2*)Lc.mgx, act);
     });
     CKL();
   }
-  for (int k = G.K - 1; k >= 0; --k) {
+  for (int k = kend - 1; k >= 0; --k) {
     Level& L = G.lv[k];
     Level& Lc = G.lv[k + 1];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
@@ -830,19 +906,41 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
   CKL();
   int rc = restrict_states<T>(H, G, B, true, G.newton_active, st);
   if (rc) return rc;
+  const double vt = lg.h * lg.h * inv_tau * inv_s;
+  // Fine residual and Jacobian (JAC), or the residual alone, of the samples
+  // with newton_active set; F and the per-CTA max |F| into pmax.
+  auto assemble_fine = [&](bool jac) {
+    if (jac)
+      launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
+        if (L.cc)
+          assemble_kernel<T, true, true>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+              ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, (B4*)L.J,
+              L.plane, pmax, L.cc, L.fc);
+        else
+          assemble_kernel<T, true>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+                                                                      vt, inv_s, L.x, L.xo, G.newton_active, G.F,
+                                                                      (B4*)L.J, L.plane, pmax, nullptr, nullptr);
+      });
+    else
+      launch(H, st, HENRY_K_RESIDUAL, (double)H->nact * N * 48.0, [&] {
+        if (L.cc)
+          assemble_kernel<T, true, true, false, false>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+              ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, nullptr,
+              L.plane, pmax, L.cc, L.fc);
+        else
+          assemble_kernel<T, true, false, false, false>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+              ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, nullptr,
+              L.plane, pmax, nullptr, nullptr);
+      });
+  };
   for (int it = 0; it <= c.newton_maxit; ++it) {
+    // From iteration newton_residual_first on, a sample is most likely
+    // converged: its residual is evaluated alone first, and the Jacobian is
+    // assembled only for the samples that go on iterating (the residual is
+    // recomputed with it, bit-identically).
+    const bool res_first = c.newton_residual_first >= 0 && it >= c.newton_residual_first;
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
-    launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
-      if (L.cc)
-        assemble_kernel<T, true, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                             lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                             G.newton_active, G.F, (B4*)L.J, L.plane, pmax, L.cc,
-                                                             L.fc);
-      else
-        assemble_kernel<T, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
-                                                       lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
-                                                       G.newton_active, G.F, (B4*)L.J, L.plane, pmax, nullptr, nullptr);
-    });
+    assemble_fine(!res_first);
     launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
       k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
                                                        G.newton_active, G.lin_active, G.newton_it, G.status,
@@ -854,6 +952,10 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     if (rc) return rc;
     if (n_act == 0) break;
     H->nact = n_act;
+    if (res_first) {
+      assemble_fine(true);
+      CKL();
+    }
     if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
       rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
       if (rc) return rc;
@@ -912,6 +1014,12 @@ __global__ void k_merge_status(int n, const int* __restrict__ a, int32_t* __rest
   else if (out[i] == 0) out[i] = v;
 }
 
+// *first = the smallest sample index with a non-zero status (untouched if none).
+__global__ void k_first_bad(int n, const int* __restrict__ status, int* __restrict__ first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && status[i] != 0) atomicMin(first, i);
+}
+
 // The whole scenario solve of B samples with the fused one-CTA-per-sample
 // kernel (coefficients and status set).
 template <typename T>
@@ -959,6 +1067,8 @@ struct TuningScope {
     h->cfg.nu1 = f->second.nu1;
     h->cfg.nu2 = f->second.nu2;
     h->cfg.fused_small_grids = f->second.fused_small_grids;
+    h->cfg.mg_tail_cells = f->second.mg_tail_cells;
+    h->cfg.newton_residual_first = f->second.newton_residual_first;
   }
   ~TuningScope() { H->cfg = saved; }
 };
@@ -1017,14 +1127,29 @@ int setup_from_states(henry_handle* H, int level, const double* xi, int n, const
   return HENRY_OK;
 }
 
+// jac = false: the fine residual alone, with the kernel of the Newton
+// test's residual-first evaluations.
 template <typename T>
-int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t st) {
+int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t st, bool jac = true) {
   typedef typename VT<T>::b4 B4;
   const henry_config& c = H->cfg;
   const LevelGeom lg = geom(c, G.level);
   const double inv_tau = 1.0 / lg.tau;
   const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h * inv_tau);
   Level& L = G.lv[0];
+  if (!jac) {
+    double* pm = G.part + P_MAX * (int64_t)n * G.nct;
+    if (L.cc)
+      assemble_kernel<T, true, true, false, false>(c, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+          phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+          G.newton_active, G.F, nullptr, L.plane, pm, L.cc, L.fc);
+    else
+      assemble_kernel<T, true, false, false, false>(c, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+          phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
+          G.newton_active, G.F, nullptr, L.plane, pm, nullptr, nullptr);
+    CKL();
+    return HENRY_OK;
+  }
   if (L.cc)
     assemble_kernel<T, true, true>(H->cfg, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
         phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
@@ -1243,7 +1368,7 @@ int step_entry(henry_handle* H, int which, int level, const double* xi, int n, c
   if (rc) return rc;
   Level& L = G->lv[0];
   const int64_t n0 = (int64_t)n * L.N;
-  rc = assemble_all<T>(H, *G, n, which >= 2, st);
+  rc = assemble_all<T>(H, *G, n, which >= 2, st, which != 0 || out2 != nullptr);
   if (rc) return rc;
   switch (which) {
     case 0:  // assemble
@@ -1378,6 +1503,9 @@ void henry_default_config(henry_config* c) {
   c->cuda_graphs = 1;
   c->qoi_set = HENRY_QOI_STANDARD;
   c->tile_assembly = 1;
+  c->newton_residual_first = 2;
+  c->mg_tail_cells = 128;
+  c->mg_tail_batch_cells = 1 << 20;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -1407,8 +1535,9 @@ int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
     h->tuned.erase(level);
     return HENRY_OK;
   }
-  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0)
-    return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d)", t->lin_rtol, t->nu1, t->nu2);
+  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < 0)
+    return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d, mg_tail_cells %d)", t->lin_rtol, t->nu1,
+                   t->nu2, t->mg_tail_cells);
   h->tuned[level] = *t;
   return HENRY_OK;
 }
@@ -1425,6 +1554,8 @@ int henry_get_tuning(henry_handle* h, int level, henry_tuning* out) {
     out->nu1 = h->cfg.nu1;
     out->nu2 = h->cfg.nu2;
     out->fused_small_grids = h->cfg.fused_small_grids;
+    out->mg_tail_cells = h->cfg.mg_tail_cells;
+    out->newton_residual_first = h->cfg.newton_residual_first;
   }
   return HENRY_OK;
 }
@@ -1464,6 +1595,8 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         t.nu1 = nu[0];
         t.nu2 = nu[1];
         t.fused_small_grids = can_fuse ? (fz == 0 ? 0 : 1) : c.fused_small_grids;
+        t.mg_tail_cells = c.mg_tail_cells;
+        t.newton_residual_first = c.newton_residual_first;
         cands.push_back(t);
       }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1485,7 +1618,9 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
   h->tuned.erase(level);
   int best = -1;
   double best_rate = 0.0;
-  for (int i = -1; i < (int)cands.size() && !rc; ++i) {  // i = -1: warm-up (workspaces, graphs)
+  // Times candidate i (i = -1: the untimed warm-up that sets up workspaces
+  // and graphs); keeps the fastest that solves every sample.
+  auto trial = [&](int i) {
     if (i >= 0) h->tuned[level] = cands[i];
     cudaEventRecord(e0, st);
     rc = henry_level_batch_solve(h, level, with_coarse, xi_dev, n_trial, qf, with_coarse ? qc : nullptr, sd, nullptr,
@@ -1493,9 +1628,9 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
     cudaEventRecord(e1, st);
     if (rc == HENRY_ENOCONV) {  // a candidate that loses samples is not a candidate
       rc = HENRY_OK;
-      continue;
+      return;
     }
-    if (rc) break;
+    if (rc) return;
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -1505,6 +1640,31 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         best_rate = cands[i].cell_steps_per_s;
         best = i;
       }
+    }
+  };
+  // Stage 1: Krylov tolerance x smoothing counts x fused small-grid solver.
+  const int n1 = (int)cands.size();
+  for (int i = -1; i < n1 && !rc; ++i) trial(i);
+  // Stages 2 and 3, one setting at a time from the best so far: the fused
+  // multigrid tail (off, from 16 x 8, from 32 x 16 cells) and the
+  // residual-first Newton test (never, from iteration 1, from 2).
+  if (!rc && best >= 0 && !cands[best].fused_small_grids) {
+    const int tails[3] = {0, 128, 512};
+    for (int v : tails) {
+      if (v == cands[best].mg_tail_cells || rc) continue;
+      henry_tuning t = cands[best];
+      t.mg_tail_cells = v;
+      cands.push_back(t);
+      trial((int)cands.size() - 1);
+    }
+    const int rfs[3] = {-1, 1, 2};
+    const int b2 = best;
+    for (int v : rfs) {
+      if (v == cands[b2].newton_residual_first || rc) continue;
+      henry_tuning t = cands[b2];
+      t.newton_residual_first = v;
+      cands.push_back(t);
+      trial((int)cands.size() - 1);
     }
   }
   h->tuned.erase(level);
@@ -2005,14 +2165,33 @@ int henry_vc_assemble(henry_handle* h, int level, const double* xi_dev, int n, c
   const VcParams P{lg.nx, lg.ny, lg.h, lg.tau, c.rho0, c.rho1 - c.rho0, c.rho1, c.g, c.Ly};
   const size_t cbytes = sizeof(Coef) * (size_t)n;
   char* mem = nullptr;
-  if (cudaMallocAsync((void**)&mem, cbytes + sizeof(int) * (size_t)n, st) != cudaSuccess) {
+  if (cudaMallocAsync((void**)&mem, cbytes + sizeof(int) * ((size_t)n + 1), st) != cudaSuccess) {
     cudaGetLastError();
     return set_err(HENRY_ENOMEM, "cudaMallocAsync for %d samples' coefficients failed", n);
   }
   Coef* coef = (Coef*)mem;
   int* status = (int*)(mem + cbytes);
+  int* first_bad = status + n;
   const CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
-  k_coefficients<<<nblk(n, 128), 128, 0, st>>>(m, n, xi_dev, coef, status);
+  // Coefficients first, checked on the host: a sample whose xi gives phi
+  // outside (0, 1) or a non-finite K or q_in is refused (EINVAL, naming the
+  // first such sample) before anything is assembled from it.
+  rc = ensure_pinned(h);
+  if (!rc) {
+    k_coefficients<<<nblk(n, 128), 128, 0, st>>>(m, n, xi_dev, coef, status);
+    cudaMemsetAsync(first_bad, 0x7f, sizeof(int), st);
+    k_first_bad<<<nblk(n, 128), 128, 0, st>>>(n, status, first_bad);
+    rc = read_counter(h, first_bad, st, &h->host_counter[1]);
+  }
+  if (!rc && h->host_counter[1] < n) {
+    const int bad = h->host_counter[1];
+    cudaFreeAsync(mem, st);
+    return set_err(HENRY_EINVAL, "sample %d: its inputs give phi outside (0, 1) or a non-finite K or q_in", bad);
+  }
+  if (rc) {
+    cudaFreeAsync(mem, st);
+    return rc;
+  }
   const int64_t total = (int64_t)n * (lg.nx + 1) * (lg.ny + 1);
   k_vc_assemble<<<nblk(total), TPB, 0, st>>>(P, n, coef, state_dev, state_old_dev, R_dev, J_dev);
   const cudaError_t e = cudaGetLastError();
@@ -2082,6 +2261,7 @@ int static_solve(henry_handle* H, int level, int with_coarse, const double* xi, 
                  int32_t* status, cudaStream_t st) {
   char* base = nullptr;
   int rc = static_scratch_ptr(&base);
+  if (!rc) rc = ensure_tail_attr<T>();
   if (rc) return rc;
   const LevelGeom gf = geom(H->cfg, level);
   Group<T> Gf, Gc;

@@ -176,7 +176,7 @@ __device__ __forceinline__ B4 mkblk(double a00, double a01, double a10, double a
 // Land (ix = 0) and seaside (ix = nx - 1) boundary terms of one cell, added
 // to its scaled residuals and centre block (assemble_cell and the tile
 // assembly share them).
-template <typename T, typename S, bool DROP>
+template <typename T, typename S, bool DROP, bool JAC = true>
 __device__ __forceinline__ void boundary_terms(const Phys& ph, double qin, double inv_s, S kmu, S PD, int nx, int ix,
                                                int iy, S hS, S ihS, S rhoP, S pP, S cP, S& Rm, S& Rs, T& C00,
                                                T& C01, T& C10, T& C11) {
@@ -188,7 +188,7 @@ __device__ __forceinline__ void boundary_terms(const Phys& ph, double qin, doubl
     const bool up = Fl >= (S)0;
     Rm += Fl;
     Rs += fma_(Fl, up ? cP : (S)0, (S)2 * rb * PD * cP);
-    C11 += (up ? (T)Fl : (T)0) + PDP_T * (T)fma_(drho, cP, (S)2 * rb);
+    if constexpr (JAC) C11 += (up ? (T)Fl : (T)0) + PDP_T * (T)fma_(drho, cP, (S)2 * rb);
   }
   if (ix == nx - 1) {  // seaside: hydrostatic brine pressure, c_b = 1
     const S yP = ((S)iy + (S)0.5) * hS;
@@ -201,12 +201,14 @@ __device__ __forceinline__ void boundary_terms(const Phys& ph, double qin, doubl
     const S dif = PD * ((S)1 - cP);
     Rm += Fr;
     Rs += fma_(Fr, cup, -(S)2 * rb * dif);
-    const T dFdp = (T)2 * (T)rb * kmuP_T;
-    const T dFdc = DROP ? (T)0 : hdT * (T)q * hT;
-    C00 += dFdp;
-    C01 += dFdc;
-    C10 = fma_(dFdp, (T)cup, C10);
-    C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDP_T));
+    if constexpr (JAC) {
+      const T dFdp = (T)2 * (T)rb * kmuP_T;
+      const T dFdc = DROP ? (T)0 : hdT * (T)q * hT;
+      C00 += dFdp;
+      C01 += dFdc;
+      C10 = fma_(dFdp, (T)cup, C10);
+      C11 += fma_(dFdc, (T)cup, (up ? (T)Fr : (T)0) - ((T)drho * (T)dif - (T)2 * (T)rb * PDP_T));
+    }
   }
 }
 
@@ -229,11 +231,14 @@ struct CellSys {
 // FIELDS: per-cell coefficients instead of the sample's scalars: cc[st] =
 // (phi, K/mu) of the cell and fc[st] = (K/mu, phi Dm) harmonic means on its
 // east face (.x, .y) and north face (.z, .w), zero across the boundary.
+// JAC = false: the residual alone (no derivative terms; the residual's
+// arithmetic is the same code, so it is bit-identical to the JAC = true
+// form's).
 // DROP: the fallback preconditioner operator - the Jacobian without the
 // derivatives of the face densities with respect to c (dF/dc = 0 in both
 // rows), an operator whose diagonal blocks stay definite where density
 // contrasts over heterogeneous K make point-block Gauss-Seidel diverge.
-template <typename T, typename S, bool FIELDS = false, bool DROP = false>
+template <typename T, typename S, bool FIELDS = false, bool DROP = false, bool JAC = true>
 __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, int nx, int ny, double h, double inv_h,
                                               double vt_s, double inv_s, const double2* xs, const double2* xos,
                                               int st, int ix, int iy, CellSys<T, S>& o,
@@ -288,6 +293,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     const S dif = PD_f * (cN - cP);
     Rm += Ff;
     Rs += fma_(Ff, cup, -rhof * dif);
+    if constexpr (!JAC) continue;
     // derivatives of (F, G) w.r.t. the unknowns of P and of the neighbour
     const T rhofT = (T)rhof, cupT = (T)cup, FfT = (T)Ff, difT = (T)dif;
     const T dFdp = rhofT * kmuT;
@@ -303,7 +309,7 @@ __device__ __forceinline__ void assemble_cell(const Phys& ph, const Coef& cf, in
     o.Nb[k][2] = -dFdp * cupT;
     o.Nb[k][3] = fma_(dFdc, cupT, (up ? (T)0 : FfT) - dGdifN);
   }
-  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C00, C01, C10,
+  boundary_terms<T, S, DROP, JAC>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C00, C01, C10,
                              C11);
   o.fm = Rm;
   o.fs = Rs;
@@ -324,7 +330,7 @@ __device__ __forceinline__ void store_blocks(typename VT<T>::b4* J, int64_t ps, 
 
 // One thread per cell; FINE: CTAs never straddle samples (N % TPB == 0) and
 // write the per-CTA max |F| (inf for non-finite) to rmax_part[s][ct].
-template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
 __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
                                                   double h, double inv_h, double vt_s, double inv_s,
                                                   const double2* __restrict__ x, const double2* __restrict__ xo,
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
   xy_of(st, nx, ix, iy);
   const int64_t base = e - st;
   CellSys<T, S> o;
-  assemble_cell<T, S, FIELDS, DROP>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o,
+  assemble_cell<T, S, FIELDS, DROP, JAC>(ph, coef[s], nx, ny, h, inv_h, vt_s, inv_s, x + base, xo + base, st, ix, iy, o,
                               FIELDS ? cc + base : nullptr, FIELDS ? fc + base : nullptr);
   if (FINE) {
     const double fm = (double)o.fm, fs = (double)o.fs;
@@ -361,7 +367,9 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
       rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
     }
   }
-  if (J) store_blocks<T>(J, plane, e, o.C, o.Nb);
+  if constexpr (JAC) {
+    if (J) store_blocks<T>(J, plane, e, o.C, o.Nb);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -372,16 +380,24 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
 // evaluates every interior face from both sides): the same arithmetic from
 // L's side, upwinding included (at the tie F = 0 the upwind value is L's,
 // the same tie-break as assemble_cell's from L's side).
-template <typename T, typename S>
+template <typename T, typename S, bool JAC = true>
 struct FaceData {
   S F, G;   // fluxes L -> R (scaled)
   T aL[4];  // d(F, G)/d(p_L, c_L): dF/dp, dF/dc, dG/dp, dG/dc
   T aR[4];  // d(F, G)/d(p_R, c_R)
 };
+// Residual-only evaluation (JAC = false): the fluxes alone.
+template <typename T, typename S>
+struct FaceData<T, S, false> {
+  S F, G;
+};
 
-template <typename T, typename S, bool DROP>
+// JAC = false: the fluxes only, with exactly the arithmetic of the JAC =
+// true form (the derivative terms come after F and G and feed nothing back),
+// so both forms give bit-identical residuals.
+template <typename T, typename S, bool DROP, bool JAC = true>
 __device__ __forceinline__ void face_eval(const Phys& ph, S kmu_f, S PD_f, S sg, S hS, S ihS, double2 xL, double2 xR,
-                                          FaceData<T, S>& f) {
+                                          FaceData<T, S, JAC>& f) {
   const S drho = (S)ph.drho, rho0 = (S)ph.rho0;
   const S pL = (S)xL.x, cL = (S)xL.y, pR = (S)xR.x, cR = (S)xR.y;
   const S rhoL = rho0 + drho * cL, rhoR = rho0 + drho * cR;
@@ -393,6 +409,8 @@ __device__ __forceinline__ void face_eval(const Phys& ph, S kmu_f, S PD_f, S sg,
   const S dif = PD_f * (cR - cL);
   f.F = Ff;
   f.G = fma_(Ff, cup, -rhof * dif);
+  if constexpr (!JAC) return;
+  else {
   const T kmuT = (T)kmu_f, PDT = (T)PD_f, hT = (T)hS, hdT = (T)(0.5 * ph.drho);
   const T rhofT = (T)rhof, cupT = (T)cup, FfT = (T)Ff, difT = (T)dif;
   const T dFdp = rhofT * kmuT;
@@ -407,28 +425,33 @@ __device__ __forceinline__ void face_eval(const Phys& ph, S kmu_f, S PD_f, S sg,
   f.aR[1] = dFdc;
   f.aR[2] = -dFdp * cupT;
   f.aR[3] = fma_(dFdc, cupT, (up ? (T)0 : FfT) - dGdifR);
+  }
 }
 
 // The residual and Jacobian of one cell from its faces' data (sgn = +1: the
 // cell is the face's L, -1: its R; k = 0 W, 1 E, 2 S, 3 N).
-template <typename T, typename S>
-__device__ __forceinline__ void add_face(const FaceData<T, S>& f, bool cell_is_L, int k, S& Rm, S& Rs, T C[4],
+template <typename T, typename S, bool JAC = true>
+__device__ __forceinline__ void add_face(const FaceData<T, S, JAC>& f, bool cell_is_L, int k, S& Rm, S& Rs, T C[4],
                                          T Nb[4][4]) {
   if (cell_is_L) {
     Rm += f.F;
     Rs += f.G;
+    if constexpr (JAC) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      C[j] += f.aL[j];
-      Nb[k][j] = f.aR[j];
+      for (int j = 0; j < 4; ++j) {
+        C[j] += f.aL[j];
+        Nb[k][j] = f.aR[j];
+      }
     }
   } else {
     Rm -= f.F;
     Rs -= f.G;
+    if constexpr (JAC) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      C[j] -= f.aR[j];
-      Nb[k][j] = -f.aL[j];
+      for (int j = 0; j < 4; ++j) {
+        C[j] -= f.aR[j];
+        Nb[k][j] = -f.aL[j];
+      }
     }
   }
 }
@@ -441,7 +464,7 @@ __device__ __forceinline__ void add_face(const FaceData<T, S>& f, bool cell_is_L
 // its accumulation and boundary terms, and stores F, the blocks and C^-1
 // like k_assemble (same arguments; FINE: N % TPB == 0, one sample per CTA).
 // Shared memory: 2 x TPB faces (40 KB in FP64).
-template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
 __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __restrict__ coef, int B, int nx, int ny,
                                                        double h, double inv_h, double vt_s, double inv_s,
                                                        const double2* __restrict__ x, const double2* __restrict__ xo,
@@ -451,7 +474,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
                                                        const double2* __restrict__ cc = nullptr,
                                                        const double4_32a* __restrict__ fc = nullptr) {
   typedef typename std::conditional<FINE, double, T>::type S;
-  __shared__ FaceData<T, S> fE[TPB], fN[TPB];
+  __shared__ FaceData<T, S, JAC> fE[TPB], fN[TPB];
   __shared__ double sh[40];
   const int N = nx * ny;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -490,7 +513,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
         kf = (S)(q.x * inv_s);
         pf = (S)(q.y * inv_s);
       }
-      face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
+      face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
     }
     if (iy + 1 < ny) {  // north face, P = L
       S kf = kmu, pf = PD;
@@ -499,7 +522,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
         kf = (S)(q.z * inv_s);
         pf = (S)(q.w * inv_s);
       }
-      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
+      face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
     }
   }
   __syncthreads();
@@ -516,11 +539,11 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
   T Nb[4][4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = (T)0;
-  if (ix > 0) add_face<T, S>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);                     // W: P = R
-  if (ix + 1 < nx) add_face<T, S>(fE[slot], true, 1, Rm, Rs, C, Nb);                     // E: P = L
+  if (ix > 0) add_face<T, S, JAC>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);                     // W: P = R
+  if (ix + 1 < nx) add_face<T, S, JAC>(fE[slot], true, 1, Rm, Rs, C, Nb);                     // E: P = L
   if (iy > 0) {  // S: P = R
     if (r > 0) {
-      add_face<T, S>(fN[slot - nx], false, 2, Rm, Rs, C, Nb);
+      add_face<T, S, JAC>(fN[slot - nx], false, 2, Rm, Rs, C, Nb);
     } else {  // the lower cell is in another tile: evaluate the face here
       const int sb = st_of(ix, iy - 1, nx);
       S kf = kmu, pf = PD;
@@ -529,13 +552,13 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
         kf = (S)(q.z * inv_s);
         pf = (S)(q.w * inv_s);
       }
-      FaceData<T, S> fb;
-      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
-      add_face<T, S>(fb, false, 2, Rm, Rs, C, Nb);
+      FaceData<T, S, JAC> fb;
+      face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
+      add_face<T, S, JAC>(fb, false, 2, Rm, Rs, C, Nb);
     }
   }
-  if (iy + 1 < ny) add_face<T, S>(fN[slot], true, 3, Rm, Rs, C, Nb);                     // N: P = L
-  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
+  if (iy + 1 < ny) add_face<T, S, JAC>(fN[slot], true, 3, Rm, Rs, C, Nb);                     // N: P = L
+  boundary_terms<T, S, DROP, JAC>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
                              C[3]);
   if (FINE) {
     const double fm = (double)Rm, fs = (double)Rs;
@@ -548,7 +571,9 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
       rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
     }
   }
-  if (J) store_blocks<T>(J, plane, e, C, Nb);
+  if constexpr (JAC) {
+    if (J) store_blocks<T>(J, plane, e, C, Nb);
+  }
 }
 
 // Tile assembly for grids wider than TPB cells: a CTA covers a TW x (TPB /
@@ -559,7 +584,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
 // About 2.5 face evaluations per cell.  The per-tile max |F| goes to slot
 // (tile index) of the sample's N / TPB partials.
 constexpr int TILE_W = 128;
-template <typename T, bool FINE, bool FIELDS = false, bool DROP = false>
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
 __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __restrict__ coef, int B, int nx,
                                                          int ny, double h, double inv_h, double vt_s, double inv_s,
                                                          const double2* __restrict__ x, const double2* __restrict__ xo,
@@ -570,7 +595,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __
                                                          const double4_32a* __restrict__ fc = nullptr) {
   typedef typename std::conditional<FINE, double, T>::type S;
   constexpr int TH = TPB / TILE_W;
-  __shared__ FaceData<T, S> fE[TPB], fN[TPB];
+  __shared__ FaceData<T, S, JAC> fE[TPB], fN[TPB];
   __shared__ double sh[40];
   const int N = nx * ny;
   const int tiles = N / TPB;  // per sample
@@ -609,12 +634,12 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __
   if (ix + 1 < nx) {  // east face, P = L
     S kf, pf;
     face_coef(st, false, kf, pf);
-    face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
+    face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)0, hS, ihS, xP, x[base + st_of(ix + 1, iy, nx)], fE[slot]);
   }
   if (iy + 1 < ny) {  // north face, P = L
     S kf, pf;
     face_coef(st, true, kf, pf);
-    face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
+    face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)ph.g, hS, ihS, xP, x[base + st_of(ix, iy + 1, nx)], fN[slot]);
   }
   __syncthreads();
   const double2 xO = xo[base + st];
@@ -631,31 +656,31 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __
   for (int k = 0; k < 4; ++k) Nb[k][0] = Nb[k][1] = Nb[k][2] = Nb[k][3] = (T)0;
   if (ix > 0) {  // W: P = R
     if (tx > 0) {
-      add_face<T, S>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);
+      add_face<T, S, JAC>(fE[slot - 1], false, 0, Rm, Rs, C, Nb);
     } else {
       const int sw = st_of(ix - 1, iy, nx);
       S kf, pf;
       face_coef(sw, false, kf, pf);
-      FaceData<T, S> fw;
-      face_eval<T, S, DROP>(ph, kf, pf, (S)0, hS, ihS, x[base + sw], xP, fw);
-      add_face<T, S>(fw, false, 0, Rm, Rs, C, Nb);
+      FaceData<T, S, JAC> fw;
+      face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)0, hS, ihS, x[base + sw], xP, fw);
+      add_face<T, S, JAC>(fw, false, 0, Rm, Rs, C, Nb);
     }
   }
-  if (ix + 1 < nx) add_face<T, S>(fE[slot], true, 1, Rm, Rs, C, Nb);  // E: P = L
+  if (ix + 1 < nx) add_face<T, S, JAC>(fE[slot], true, 1, Rm, Rs, C, Nb);  // E: P = L
   if (iy > 0) {  // S: P = R
     if (ty > 0) {
-      add_face<T, S>(fN[slot - TILE_W], false, 2, Rm, Rs, C, Nb);
+      add_face<T, S, JAC>(fN[slot - TILE_W], false, 2, Rm, Rs, C, Nb);
     } else {
       const int sb = st_of(ix, iy - 1, nx);
       S kf, pf;
       face_coef(sb, true, kf, pf);
-      FaceData<T, S> fb;
-      face_eval<T, S, DROP>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
-      add_face<T, S>(fb, false, 2, Rm, Rs, C, Nb);
+      FaceData<T, S, JAC> fb;
+      face_eval<T, S, DROP, JAC>(ph, kf, pf, (S)ph.g, hS, ihS, x[base + sb], xP, fb);
+      add_face<T, S, JAC>(fb, false, 2, Rm, Rs, C, Nb);
     }
   }
-  if (iy + 1 < ny) add_face<T, S>(fN[slot], true, 3, Rm, Rs, C, Nb);  // N: P = L
-  boundary_terms<T, S, DROP>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
+  if (iy + 1 < ny) add_face<T, S, JAC>(fN[slot], true, 3, Rm, Rs, C, Nb);  // N: P = L
+  boundary_terms<T, S, DROP, JAC>(ph, cf.qin, inv_s, kmu, PD, nx, ix, iy, hS, ihS, rhoP, pP, cP, Rm, Rs, C[0], C[1], C[2],
                              C[3]);
   const int64_t e = base + st;
   if (FINE) {
@@ -666,7 +691,9 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __
     const double bm = block_reduce<true>(loc, sh);
     if (threadIdx.x == 0) rmax_part[(int64_t)s * tiles + tile] = bm;
   }
-  if (J) store_blocks<T>(J, plane, e, C, Nb);
+  if constexpr (JAC) {
+    if (J) store_blocks<T>(J, plane, e, C, Nb);
+  }
 }
 
 // Coarse states: mean of the 2x2 children (both the iterate and the old state).

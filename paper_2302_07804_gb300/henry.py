@@ -29,7 +29,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_paper_config", "henry_kl_basis", "henry_autotune", "henry_get_tuning",
            "henry_set_tuning", "henry_vc_assemble")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
-                  "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse")
+                  "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse", "residual", "mg_tail")
 
 
 class HenryConfig(ctypes.Structure):
@@ -45,7 +45,8 @@ class HenryConfig(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("kl_corr_len", "kl_sigma_logK", "kl_sigma_phi", "phi_lo", "phi_hi")] + \
                [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32), ("adj_rtol", ctypes.c_double),
                 ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32),
-                ("tile_assembly", ctypes.c_int32)]
+                ("tile_assembly", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
+                ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -69,7 +70,8 @@ _lib = None
 class HenryTuning(ctypes.Structure):
     """henry_tuning: a level's solver settings chosen by henry_autotune."""
     _fields_ = [("lin_rtol", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
-                ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double)]
+                ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double),
+                ("mg_tail_cells", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

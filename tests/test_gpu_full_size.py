@@ -45,7 +45,7 @@ def test_level0_bench_batch_sampled_against_oracle(hl, precision):
     ref, ok = ohenry.solve_scenarios(PRM, 0, xi[picks].cpu().numpy())
     assert ok.all()
     np.testing.assert_allclose(qn[picks, 0], ref[:, 0], rtol=1e-10, atol=0)
-    np.testing.assert_allclose(qn[picks, 1], ref[:, 1], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(qn[picks, 1], ref[:, 1], rtol=1e-10, atol=1e-14)
     s.close()
 
 
@@ -62,5 +62,5 @@ def test_largest_grid_properties(hl):
     assert np.all((f64[:, 1] >= -1e-12) & (f64[:, 1] <= 1 + 1e-12)) and np.all(f64[:, 0] > 0)
     assert np.abs(f64[:, 1] - c64[:, 1]).max() < 0.01
     np.testing.assert_allclose(f32[:, 0], f64[:, 0], rtol=1e-10, atol=0)
-    np.testing.assert_allclose(f32[:, 1], f64[:, 1], rtol=0, atol=1e-10)
-    np.testing.assert_allclose(c32[:, 1], c64[:, 1], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(f32[:, 1], f64[:, 1], rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(c32[:, 1], c64[:, 1], rtol=1e-10, atol=1e-14)

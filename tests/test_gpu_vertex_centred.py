@@ -70,3 +70,21 @@ def test_vc_assembly_rejects_field_models(hl):
         s.vc_assemble(0, xi, st, st)
     assert e.value.code == hl.HENRY_EINVAL
     s.close()
+
+
+def test_vc_assembly_rejects_inputs_outside_the_model(hl):
+    """xi1 = -6 gives phi = 0.35 (1 - 1.2) < 0: the call refuses the batch and
+    names the sample instead of assembling from a negative porosity."""
+    s = hl.Solver()
+    ny, nx = s.grid(0)
+    xi = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    xi[1, 0] = -6.0
+    st = torch.zeros((3, ny + 1, nx + 1, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(hl.HenryError) as e:
+        s.vc_assemble(0, xi, st, st)
+    assert e.value.code == hl.HENRY_EINVAL and "sample 1" in str(e.value)
+    xi[1, 0] = 0.0
+    R, _ = s.vc_assemble(0, xi, st, st, with_jacobian=False)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(R).all())
+    s.close()
