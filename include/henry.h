@@ -99,6 +99,23 @@ enum { HENRY_MODEL_UNIFORM3 = 0, HENRY_MODEL_KL = 1, HENRY_MODEL_TWO_LAYER = 2 }
  *   paper's Q_FW(t) curves and crossing times (Sec. 4); the last one is [2]. */
 enum { HENRY_QOI_STANDARD = 0, HENRY_QOI_PAPER = 1, HENRY_QOI_PAPER_FIELD = 2, HENRY_QOI_PAPER_SERIES = 3 };
 
+/* Discretisations (henry_config.scheme).
+ * CELL (default): cell-centred finite volumes with upwind advection, the
+ *   configuration's scheme (states [n][ny][nx][2] in the per-step calls).
+ * VERTEX: the paper's own vertex-centred finite volumes (Sec. 2.3): (p, c)
+ *   at the (ny + 1) x (nx + 1) grid vertices, n_l = 2 (nx + 1)(ny + 1)
+ *   unknowns as in Table tab:adaptiveTS_times, a "consistent velocity" and
+ *   partial upwinding (the readings are stated in henry_vc.cuh); Newton with
+ *   BiCGStab preconditioned by a V-cycle on vertex-nested grids (four-colour
+ *   2x2-block Gauss-Seidel, full-weighting restriction, bilinear
+ *   prolongation, rediscretised coarse operators, a dense solve on the 2 x 1
+ *   element grid).  QoIs: the lumped salt mass and c at the vertex (1.5,
+ *   0.25).  Three-parameter model and the standard QoIs only; per-step
+ *   states are [n][ny + 1][nx + 1][2], henry_assemble's blocks
+ *   [n][ny + 1][nx + 1][9][2][2] (neighbour (dj, di) at (dj + 1) 3 + di + 1).
+ *   Not available in henry_adjoint and henry_level_batch_solve_static. */
+enum { HENRY_SCHEME_CELL = 0, HENRY_SCHEME_VERTEX = 1 };
+
 /* Coarse-grid operators of the multigrid hierarchy. */
 enum { HENRY_COARSE_REDISCRETISE = 0, HENRY_COARSE_GALERKIN = 1 };
 
@@ -162,6 +179,7 @@ typedef struct {
   int32_t mg_tail_batch_cells; /* ... only while the batch times that level's cells per sample is at most this
                                   (default 2^20; 0: no limit): large batches of small grids run those levels
                                   as separate, large launches */
+  int32_t scheme; /* HENRY_SCHEME_CELL (default) or HENRY_SCHEME_VERTEX */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -188,7 +206,7 @@ void henry_paper_config(henry_config* cfg);
  * the V-cycle's smoothing counts and, where the level's grid allows it, the
  * fused one-CTA-per-sample solver; then, one at a time from the best so far,
  * the fused multigrid tail (mg_tail_cells in {0, 128, 512}) and the
- * residual-first Newton test (newton_residual_first in {-1, 1, 2}).
+ * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}).
  * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
  * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
  * off where eligible), then the two later stages - on n_trial samples
@@ -343,6 +361,18 @@ int mlmc_rates(int n_levels, int first_level, const double* mean_Y_host, const d
  * or eps <= 0, non-finite mean).  Host only, synchronous. */
 int mlmc_bias_test(int n_levels, const double* mean_Y_host, double alpha, double eps, double* bias_est,
                    int32_t* converged);
+
+/* The same bias test with E[Y_L] from the fitted weak error model rather
+ * than the level-L sample mean alone (on the finest levels that mean rests
+ * on a handful of samples and its noise decides the test): log2 |mean_Y_l|
+ * = a - alpha l fitted by least squares over l = first_level .. L (L =
+ * n_levels - 1); alpha = max(fitted slope, alpha_min) (*alpha_out), a
+ * refitted for that alpha; *bias_est = 2^(a - alpha L) / (2^alpha - 1);
+ * *converged = (bias_est <= eps / sqrt 2).  Outputs may be NULL.  Errors:
+ * EINVAL (fewer than two levels from first_level, a zero or non-finite
+ * mean, alpha_min or eps <= 0).  Host only, synchronous. */
+int mlmc_bias_test_fit(int n_levels, int first_level, const double* mean_Y_host, double alpha_min, double eps,
+                       double* alpha_out, double* bias_est, int32_t* converged);
 
 /* ---- Per-step entry points: one step of the solve on given states, for
  * checking each step on its own.  Each evaluates the coefficients of

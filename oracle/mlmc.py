@@ -89,3 +89,18 @@ def bias_test(mean_Y, alpha, eps):
     Returns (estimate, passed)."""
     b = abs(float(mean_Y[-1])) / (2.0 ** alpha - 1.0)
     return b, b <= eps / math.sqrt(2.0)
+
+
+def bias_test_fit(mean_Y, eps, first_level=1, alpha_min=0.5):
+    """The same remaining-bias estimate with E[Y_L] taken from the fitted weak
+    error model instead of the level-L sample mean alone: log2 |E[Y_l]| =
+    a - alpha l fitted by least squares (numpy polyfit) over l = first_level
+    .. L; alpha = max(fitted slope, alpha_min), a refitted for that alpha
+    (mean of log2 |E[Y_l]| + alpha l); E[Y_L] ~ 2^(a - alpha L), bias =
+    E[Y_L] / (2^alpha - 1).  Returns (bias, passed, alpha)."""
+    lev = np.arange(first_level, len(mean_Y))
+    y = np.log2(np.abs(np.asarray(mean_Y, dtype=np.float64)[first_level:]))
+    alpha = max(-np.polyfit(lev, y, 1)[0], alpha_min)
+    a = float(np.mean(y + alpha * lev))
+    b = float(2.0 ** (a - alpha * lev[-1]) / (2.0 ** alpha - 1.0))
+    return b, bool(b <= eps / math.sqrt(2.0)), float(alpha)

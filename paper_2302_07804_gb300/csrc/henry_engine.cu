@@ -35,6 +35,7 @@
 #include "henry_kl.cuh"
 #include "henry_adjoint.cuh"
 #include "henry_vc.cuh"
+#include "henry_vc_solve.cuh"
 
 using namespace hk;
 
@@ -188,6 +189,88 @@ struct Group {
   }
 };
 
+// The workspace of a batch of B samples of the vertex-centred scheme at one
+// MLMC level (henry_vc_solve.cuh gives the layout): per multigrid level the
+// states (fine: Newton iterate and old state; coarse: injected), 10 block
+// planes and the multigrid vectors x, b and a residual; on the fine level
+// (stride padded to whole 256-entry blocks) F and the Krylov vectors; the
+// per-sample scalars and partial sums.  One cudaMalloc, zeroed once (the
+// padding entries of every fine vector stay zero).
+template <typename T>
+struct VcGroup {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  struct Lv {
+    int nx, ny, NV, stride;
+    int64_t plane;
+    double h;
+    double2 *x, *xo;
+    void* J;
+    void *mgx, *mgb, *mgr;
+  };
+  int level = -1, Bcap = 0, K = 0, nct = 0;
+  char* mem = nullptr;
+  size_t bytes = 0;
+  std::vector<Lv> lv;
+  double2* F = nullptr;
+  V2 *r, *rh, *p, *v, *s, *t, *ph, *sh, *dx;
+  Coef* coef;
+  double *part, *theta, *fin;
+  int *newton_active, *lin_active, *newton_it, *status, *iters, *counter;
+  unsigned long long* totals;
+  LinScal* sc;
+  T* Ainv;
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> gexec;  // (B, nu1, nu2)
+  void drop_graphs() {
+    for (auto& kv : gexec) cudaGraphExecDestroy(kv.second);
+    gexec.clear();
+  }
+  size_t carve(char* base, int B, int nx0, int ny0, double h0) {
+    Carver c{base, 0};
+    std::vector<Lv> L;
+    int nx = nx0, ny = ny0;
+    double h = h0;
+    for (;;) {
+      Lv l;
+      l.nx = nx; l.ny = ny; l.NV = (nx + 1) * (ny + 1); l.h = h;
+      l.stride = L.empty() ? ((l.NV + TPB - 1) / TPB) * TPB : l.NV;
+      l.plane = (int64_t)B * l.stride;
+      l.x = c.take<double2>(sizeof(double2) * l.plane);
+      l.xo = c.take<double2>(sizeof(double2) * l.plane);
+      l.J = c.take<B4>(sizeof(B4) * 10 * l.plane);
+      l.mgx = L.empty() ? nullptr : c.take<V2>(sizeof(V2) * l.plane);
+      l.mgb = L.empty() ? nullptr : c.take<V2>(sizeof(V2) * l.plane);
+      l.mgr = c.take<V2>(sizeof(V2) * l.plane);
+      L.push_back(l);
+      if (nx <= 2 || ny <= 1) break;
+      nx /= 2; ny /= 2; h *= 2.0;
+    }
+    const int64_t n0 = L[0].plane;
+    F = c.take<double2>(sizeof(double2) * n0);
+    V2** vecs[9] = {&r, &rh, &p, &v, &s, &t, &ph, &sh, &dx};
+    for (auto vp : vecs) *vp = c.take<V2>(sizeof(V2) * n0);
+    coef = c.take<Coef>(sizeof(Coef) * B);
+    nct = L[0].stride / TPB;
+    part = c.take<double>(sizeof(double) * NPART * (size_t)B * nct);
+    newton_active = c.take<int>(sizeof(int) * B);
+    lin_active = c.take<int>(sizeof(int) * B);
+    newton_it = c.take<int>(sizeof(int) * B);
+    status = c.take<int>(sizeof(int) * B);
+    iters = c.take<int>(sizeof(int) * B);
+    theta = c.take<double>(sizeof(double) * B);
+    fin = c.take<double>(sizeof(double) * NPART * (size_t)B);
+    counter = c.take<int>(sizeof(int) * 4);
+    totals = c.take<unsigned long long>(sizeof(unsigned long long) * 4);
+    sc = c.take<LinScal>(sizeof(LinScal) * B);
+    Ainv = c.take<T>(sizeof(T) * VC_COARSE_N * VC_COARSE_N * (size_t)B);
+    if (base) {
+      lv = L;
+      K = (int)L.size() - 1;
+    }
+    return c.off + 256;
+  }
+};
+
 }  // namespace
 
 // Per-kernel-class timing with CUDA events (off by default): each profiled
@@ -225,6 +308,8 @@ struct henry_handle {
   std::map<int, KLTables> kl_tables;  // by MLMC level
   std::map<int, Group<double>> g64;
   std::map<int, Group<float>> g32;
+  std::map<int, VcGroup<double>> vg64;  // vertex-centred scheme
+  std::map<int, VcGroup<float>> vg32;
   int* host_counter = nullptr;  // pinned
   unsigned long long* host_totals = nullptr;
   Prof prof;
@@ -377,7 +462,9 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   // 1 (default): only with FP32 linear algebra, where it measured faster; on
   // GB300 the FP64 variant (one CTA per SM for lack of shared memory) is
   // FP64-latency bound and slower than the multi-kernel path.  2: always.
-  if (c.fused_small_grids <= 0 || has_fields(c) || c.qoi_set != HENRY_QOI_STANDARD) return false;
+  if (c.fused_small_grids <= 0 || has_fields(c) || c.qoi_set != HENRY_QOI_STANDARD ||
+      c.scheme != HENRY_SCHEME_CELL)
+    return false;
   if (c.fused_small_grids == 1 && sizeof(T) != sizeof(float)) return false;
   const LevelGeom lg = geom(c, level);
   if (!cta_layout(lg.nx, lg.ny, (int)sizeof(T), L)) return false;
@@ -1056,6 +1143,470 @@ int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, d
   return HENRY_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The vertex-centred scheme (henry_vc.cuh, henry_vc_solve.cuh): the same
+// Newton / BiCGStab / V-cycle structure as the cell-centred path, on the
+// vertex grid, with the BiCGStab and Newton vector kernels shared (they see
+// a sample's fine vectors as `stride` entries, padding included).
+
+template <typename T>
+std::map<int, VcGroup<T>>& vgroups(henry_handle* h);
+template <>
+std::map<int, VcGroup<double>>& vgroups<double>(henry_handle* h) { return h->vg64; }
+template <>
+std::map<int, VcGroup<float>>& vgroups<float>(henry_handle* h) { return h->vg32; }
+
+template <typename T>
+size_t vc_bytes_per_sample(const henry_config& c, int level) {
+  VcGroup<T> g;
+  const LevelGeom lg = geom(c, level);
+  return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h);
+}
+
+template <typename T>
+int vc_get_group(henry_handle* H, int level, int B, VcGroup<T>** out) {
+  int rc0 = ensure_pinned(H);
+  if (rc0) return rc0;
+  VcGroup<T>& g = vgroups<T>(H)[level];
+  if (g.mem && g.Bcap >= B) {
+    *out = &g;
+    return HENRY_OK;
+  }
+  if (g.mem) {
+    CK(cudaDeviceSynchronize());
+    g.drop_graphs();
+    CK(cudaFree(g.mem));
+    g.mem = nullptr;
+  }
+  const LevelGeom lg = geom(H->cfg, level);
+  const size_t bytes = g.carve(nullptr, B, lg.nx, lg.ny, lg.h);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(HENRY_ENOMEM, "cudaMalloc of %zu bytes for %d vertex-centred samples at level %d failed", bytes,
+                   B, level);
+  }
+  CK(cudaMemset(mem, 0, bytes));  // padding entries stay zero from here on
+  g.mem = mem;
+  g.bytes = bytes;
+  g.carve(mem, B, lg.nx, lg.ny, lg.h);
+  g.level = level;
+  g.Bcap = B;
+  *out = &g;
+  return HENRY_OK;
+}
+
+template <typename T>
+VcParams vc_params(const henry_config& c, const typename VcGroup<T>::Lv& L, double tau) {
+  return VcParams{L.nx, L.ny, L.h, tau, c.rho0, c.rho1 - c.rho0, c.rho1, c.g, c.Ly};
+}
+template <typename T>
+VcLevelArgs vc_args(const typename VcGroup<T>::Lv& L) {
+  return VcLevelArgs{L.nx, L.ny, L.stride, L.plane};
+}
+
+// States of the coarse levels by injection, level by level (old: the old state).
+template <typename T>
+int vc_inject(henry_handle* H, VcGroup<T>& G, int B, bool old, const int* active, cudaStream_t st) {
+  for (int k = 1; k <= G.K; ++k) {
+    auto& Lf = G.lv[k - 1];
+    auto& Lc = G.lv[k];
+    launch(H, st, HENRY_K_STATE_RESTRICT, (double)H->nact * Lc.NV * 32.0, [&] {
+      k_vc_inject<<<nblk((int64_t)B * Lc.NV), TPB, 0, st>>>(B, Lc.nx, Lc.ny, Lf.stride, Lc.stride,
+                                                             old ? Lf.xo : Lf.x, old ? Lc.xo : Lc.x, active);
+    });
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// Coarse operators rediscretised at the injected states (call vc_inject for
+// the iterate first) and the coarsest inverse, for the samples with lin_active.
+template <typename T>
+int vc_coarse_ops(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_s, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  for (int k = 1; k <= G.K; ++k) {
+    auto& L = G.lv[k];
+    launch(H, st, HENRY_K_COARSE_OPS, (double)H->nact * L.NV * (32.0 + 10.0 * sizeof(B4)), [&] {
+      k_vc_assemble_st<T, false><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
+          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.lin_active, nullptr,
+          (B4*)L.J, nullptr);
+    });
+    CKL();
+  }
+  auto& Lc = G.lv[G.K];
+  launch(H, st, HENRY_K_COARSE_OPS, (double)H->nact * (9.0 * 6 * sizeof(B4) + 144.0 * sizeof(T)), [&] {
+    k_vc_coarse_inverse<T><<<nblk(B, 64), 64, 0, st>>>(B, vc_args<T>(Lc), (const B4*)Lc.J, G.Ainv, G.lin_active);
+  });
+  CKL();
+  return HENRY_OK;
+}
+
+// One V(nu1, nu2) cycle on the vertex hierarchy: x0 = M^{-1} b0 (fine level,
+// active = lin_active).  Colours (ci, cj) in the order 0 (0,0), 1 (1,0),
+// 2 (0,1), 3 (1,1) before the coarse correction and 3..0 after it.
+template <typename T>
+int vc_vcycle(henry_handle* H, VcGroup<T>& G, int B, const typename VT<T>::v2* b0, typename VT<T>::v2* x0,
+              cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  const int nu1 = H->cfg.nu1, nu2 = H->cfg.nu2;
+  const int* act = G.lin_active;
+  const double na = H->nact;
+  const double b4 = sizeof(B4), v2 = sizeof(V2);
+  static const int CI[4] = {0, 1, 0, 1}, CJ[4] = {0, 0, 1, 1};
+  auto sweep = [&](int k, int col, const V2* b, V2* x) {
+    auto& L = G.lv[k];
+    const VcLevelArgs A = vc_args<T>(L);
+    const int nv = vc_colour_rows(L.ny + 1, CJ[col]) * vc_colour_cols(L.nx + 1, CI[col]);
+    launch(H, st, k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE, na * nv * (9 * b4 + 3 * v2),
+           na * nv * (8 * 8.0 + 6.0), [&] {
+             k_vc_sweep<T, 1><<<nblk((int64_t)B * nv), TPB, 0, st>>>(B, A, CI[col], CJ[col], (const B4*)L.J, b, x,
+                                                                     act);
+           });
+  };
+  for (int k = 0; k < G.K; ++k) {
+    auto& L = G.lv[k];
+    auto& Lc = G.lv[k + 1];
+    const VcLevelArgs A = vc_args<T>(L), Ac = vc_args<T>(Lc);
+    const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
+    V2* x = k == 0 ? x0 : (V2*)L.mgx;
+    const int sm = k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE;
+    if (nu1 > 0) {
+      launch(H, st, sm, na * L.NV * (0.25 * (b4 + v2) + v2), na * L.NV * 1.5, [&] {
+        k_vc_sweep<T, 0><<<nblk((int64_t)B * L.NV), TPB, 0, st>>>(B, A, 0, 0, (const B4*)L.J, b, x, act);
+      });
+      for (int col = 1; col < 4; ++col) sweep(k, col, b, x);
+      for (int i = 1; i < nu1; ++i)
+        for (int col = 0; col < 4; ++col) sweep(k, col, b, x);
+    } else {
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.NV * v2, [&] {
+        k_vc_sweep<T, 2><<<nblk((int64_t)B * L.NV), TPB, 0, st>>>(B, A, 0, 0, (const B4*)L.J, b, x, act);
+      });
+    }
+    launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.NV * (9 * b4 + 3 * v2) + na * Lc.NV * v2,
+           na * L.NV * 74.0, [&] {
+             k_vc_residual<T><<<nblk((int64_t)B * L.NV), TPB, 0, st>>>(B, A, (const B4*)L.J, b, x, (V2*)L.mgr, act);
+             k_vc_restrict<T><<<nblk((int64_t)B * Lc.NV), TPB, 0, st>>>(B, A, Ac, (const V2*)L.mgr, (V2*)Lc.mgb,
+                                                                        act);
+           });
+    CKL();
+  }
+  {
+    auto& Lc = G.lv[G.K];
+    launch(H, st, HENRY_K_COARSE_SOLVE, na * (144.0 * sizeof(T) + 24 * v2), [&] {
+      k_vc_coarse_solve<T><<<nblk(B, 64), 64, 0, st>>>(B, vc_args<T>(Lc), G.Ainv, (const V2*)Lc.mgb, (V2*)Lc.mgx,
+                                                       act);
+    });
+    CKL();
+  }
+  for (int k = G.K - 1; k >= 0; --k) {
+    auto& L = G.lv[k];
+    auto& Lc = G.lv[k + 1];
+    const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
+    V2* x = k == 0 ? x0 : (V2*)L.mgx;
+    launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * (L.NV * 2.0 * v2 + Lc.NV * v2), [&] {
+      k_vc_prolong_add<T><<<nblk((int64_t)B * L.NV), TPB, 0, st>>>(B, vc_args<T>(L), vc_args<T>(Lc), x,
+                                                                   (const V2*)Lc.mgx, act);
+    });
+    for (int i = 0; i < nu2; ++i)
+      for (int col = 3; col >= 0; --col) sweep(k, col, b, x);
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// BiCGStab on the fine vertex grid for the samples with lin_active set;
+// right-hand side -F, solution in G.dx (linear_solve's kernels and order).
+template <typename T>
+int vc_linear_solve(henry_handle* H, VcGroup<T>& G, int B, cudaStream_t st, double rtol = -1.0, int maxit = -1) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  auto& L = G.lv[0];
+  const int N = L.stride;
+  const VcLevelArgs A = vc_args<T>(L);
+  const unsigned g = nblk((int64_t)B * N);
+  const double b4 = sizeof(B4), v2 = sizeof(V2);
+  launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (16 + 5 * v2), [&] {
+    k_bicg_init<T><<<g, TPB, 0, st>>>(B, N, G.F, G.r, G.rh, G.p, G.v, G.dx, G.part, G.lin_active);
+  });
+  CKL();
+  double* fin = (H->cfg.finalize_nct > 0 && G.nct >= H->cfg.finalize_nct) ? G.fin : nullptr;
+  auto finalize = [&](int a, int b, cudaStream_t ss) {
+    if (!fin) return;
+    launch(H, ss, HENRY_K_KRYLOV, (double)B * G.nct * 16.0,
+           [&] { k_finalize<<<nblk((int64_t)B * 32, 128), 128, 0, ss>>>(B, G.nct, G.part, a, b, fin); });
+  };
+  finalize(P_RR, P_RN, st);
+  const double rt = rtol > 0.0 ? rtol : H->cfg.lin_rtol;
+  const int mi = maxit > 0 ? maxit : H->cfg.lin_maxit;
+  const double rtol2 = rt * rt;
+  auto body = [&](int n_act, cudaStream_t ss) -> int {
+    const double nc = (double)n_act * L.NV;
+    int rc = vc_vcycle<T>(H, G, B, G.p, G.ph, ss);
+    if (rc) return rc;
+    launch(H, ss, HENRY_K_SPMV, nc * (9 * b4 + 3 * v2), nc * (9 * 8.0 + 4.0), [&] {
+      k_vc_spmv<T, 1><<<g, TPB, 0, ss>>>(B, A, (const B4*)L.J, G.ph, G.v, G.rh, G.part, P_RV, 0, G.lin_active);
+    });
+    finalize(P_RV, -1, ss);
+    launch(H, ss, HENRY_K_KRYLOV, nc * 3 * v2,
+           [&] { k_bicg_s<T><<<g, TPB, 0, ss>>>(B, N, G.r, G.v, G.s, G.part, G.sc, G.lin_active, fin); });
+    CKL();
+    rc = vc_vcycle<T>(H, G, B, G.s, G.sh, ss);
+    if (rc) return rc;
+    launch(H, ss, HENRY_K_SPMV, nc * (9 * b4 + 3 * v2), nc * (9 * 8.0 + 8.0), [&] {
+      k_vc_spmv<T, 2><<<g, TPB, 0, ss>>>(B, A, (const B4*)L.J, G.sh, G.t, G.s, G.part, P_TS, P_TT, G.lin_active);
+    });
+    finalize(P_TS, P_TT, ss);
+    launch(H, ss, HENRY_K_KRYLOV, nc * 8 * v2, [&] {
+      k_bicg_update<T><<<g, TPB, 0, ss>>>(B, N, G.dx, G.ph, G.sh, G.s, G.t, G.rh, G.r, G.part, G.sc, G.lin_active,
+                                           fin);
+    });
+    finalize(P_RR, P_RN, ss);
+    CKL();
+    return HENRY_OK;
+  };
+  const bool use_graph = H->cfg.cuda_graphs && !H->prof.on;
+  auto run_graph = [&]() -> int {
+    const auto key = std::make_tuple(B, H->cfg.nu1, H->cfg.nu2);
+    auto f = G.gexec.find(key);
+    if (f == G.gexec.end()) {
+      if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = body(B, H->cap_stream);
+      const cudaError_t e = cudaStreamEndCapture(H->cap_stream, &gr);
+      if (rc) {
+        if (e == cudaSuccess && gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e != cudaSuccess) return set_err(HENRY_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t e2 = cudaGraphInstantiate(&ex, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e2 != cudaSuccess) return set_err(HENRY_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e2));
+      f = G.gexec.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(f->second, st));
+    return HENRY_OK;
+  };
+  for (int it = 0; it <= mi; ++it) {
+    CK(cudaMemsetAsync(G.counter + 1, 0, sizeof(int), st));
+    launch(H, st, HENRY_K_KRYLOV, (double)H->nact * N * (it == 0 ? 2 : 4) * v2, [&] {
+      k_bicg_p<T><<<g, TPB, 0, st>>>(B, N, it, mi, rtol2, G.r, G.p, G.v, G.part, G.sc, G.lin_active, G.iters,
+                                      G.status, G.counter + 1, G.totals + 1, fin);
+    });
+    CKL();
+    int n_act = 0;
+    int rc = read_counter(H, G.counter + 1, st, &n_act);
+    if (rc) return rc;
+    if (n_act == 0) break;
+    H->nact = n_act;
+    rc = use_graph ? run_graph() : body(n_act, st);
+    if (rc) return rc;
+  }
+  return HENRY_OK;
+}
+
+// Fine residual and Jacobian (scaled by inv_s) of the samples with
+// newton_active set, with the per-CTA max |F| into P_MAX.
+template <typename T>
+int vc_assemble_fine(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_s, cudaStream_t st) {
+  typedef typename VT<T>::b4 B4;
+  auto& L = G.lv[0];
+  launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * L.NV * (48.0 + 10.0 * sizeof(B4)), [&] {
+    k_vc_assemble_st<T, true><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
+        vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
+        (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
+  });
+  CKL();
+  return HENRY_OK;
+}
+
+// One implicit-Euler step of the vertex-centred scheme (implicit_step's
+// Newton iteration and tests).
+template <typename T>
+int vc_implicit_step(henry_handle* H, VcGroup<T>& G, int B, int step, cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  auto& L = G.lv[0];
+  const int N = L.stride;
+  const int64_t n0 = (int64_t)B * N;
+  const double inv_s = 1.0 / (c.rho0 * lg.h * lg.h / lg.tau);
+  const double inv_pref = 1.0 / (c.rho0 * c.g * c.Ly);
+  double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
+  H->nact = B;
+  launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
+    if (step > 0 && c.newton_predictor > 0.0)
+      k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
+    else
+      k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
+  });
+  CKL();
+  int rc = vc_inject<T>(H, G, B, true, G.newton_active, st);
+  if (rc) return rc;
+  for (int it = 0; it <= c.newton_maxit; ++it) {
+    CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
+    rc = vc_assemble_fine<T>(H, G, B, lg.tau, inv_s, st);
+    if (rc) return rc;
+    launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
+      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+                                                       G.newton_active, G.lin_active, G.newton_it, G.status,
+                                                       G.counter, G.totals);
+    });
+    CKL();
+    int n_act = 0;
+    rc = read_counter(H, G.counter, st, &n_act);
+    if (rc) return rc;
+    if (n_act == 0) break;
+    H->nact = n_act;
+    rc = vc_inject<T>(H, G, B, false, G.lin_active, st);
+    if (!rc) rc = vc_coarse_ops<T>(H, G, B, lg.tau, inv_s, st);
+    if (!rc) rc = vc_linear_solve<T>(H, G, B, st);
+    if (rc) return rc;
+    H->nact = n_act;
+    launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
+      double* pdc = G.part + P_DC * (int64_t)B * G.nct;
+      k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
+      k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
+      k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
+      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
+    });
+    CKL();
+  }
+  return HENRY_OK;
+}
+
+// Full scenario solves of B samples of the vertex-centred scheme whose
+// coefficients and status are set; QoIs [B][2] (salt mass, c at (1.5, 0.25)).
+template <typename T>
+int vc_solve_group(henry_handle* H, VcGroup<T>& G, int B, double* qoi, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  const LevelGeom lg = geom(c, G.level);
+  auto& L = G.lv[0];
+  CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
+  H->nact = B;
+  launch(H, st, HENRY_K_QOI, (double)B * L.stride * 16, [&] {
+    k_vc_init_state<<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(B, L.nx, L.ny, L.stride, lg.h, c.rho0 * c.g,
+                                                                c.rho1 * c.g, c.Ly, L.x);
+  });
+  CKL();
+  for (int step = 0; step < lg.steps; ++step) {
+    const int rc = vc_implicit_step<T>(H, G, B, step, st);
+    if (rc) return rc;
+  }
+  const int ip = (int)std::lround(1.5 / lg.h), jp = (int)std::lround(0.25 / lg.h);
+  launch(H, st, HENRY_K_QOI, (double)B * L.NV * 16, [&] {
+    k_vc_qoi<<<B, TPB, 0, st>>>(B, L.nx, L.ny, L.stride, lg.h, c.rho0, c.rho1 - c.rho0, ip, jp, G.coef, L.x,
+                                G.status, qoi);
+  });
+  CKL();
+  return HENRY_OK;
+}
+
+template <typename T>
+int vc_set_coefficients(henry_handle* H, VcGroup<T>& G, const double* xi, int B, cudaStream_t st) {
+  const henry_config& c = H->cfg;
+  const CoefModel m{c.phi_mean, c.K_mean, c.qin_mean, c.phi_amp, c.logK_amp, c.qin_amp, c.mu, c.Dm};
+  launch(H, st, HENRY_K_QOI, (double)B * (24 + 32 + 4),
+         [&] { k_coefficients<<<nblk(B, 128), 128, 0, st>>>(m, B, xi, G.coef, G.status); });
+  CKL();
+  return HENRY_OK;
+}
+
+template <typename T>
+int vc_batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status,
+                         bool first, henry_stats* stats, cudaStream_t st) {
+  const LevelGeom lg = geom(H->cfg, level);
+  const double per = (double)vc_bytes_per_sample<T>(H->cfg, level);
+  const int Bmax = (int)std::max(1.0, std::min(std::floor(H->cfg.workspace_bytes / per), 1.0e6));
+  for (int off = 0; off < n; off += Bmax) {
+    const int B = std::min(Bmax, n - off);
+    VcGroup<T>* G = nullptr;
+    int rc = vc_get_group<T>(H, level, std::min(Bmax, n), &G);
+    if (!rc) rc = vc_set_coefficients<T>(H, *G, xi + 3 * (int64_t)off, B, st);
+    if (!rc) rc = vc_solve_group<T>(H, *G, B, qoi + 2 * (int64_t)off, st);
+    if (rc) return rc;
+    k_merge_status<<<nblk(B, 128), 128, 0, st>>>(B, G->status, status + off, first ? 1 : 0);
+    CKL();
+    if (stats) {
+      CK(cudaMemcpyAsync(H->host_totals, G->totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      stats->newton_iters += H->host_totals[0];
+      stats->linear_iters += H->host_totals[1];
+      stats->newton_solves += (int64_t)B * lg.steps;
+      stats->cell_steps += (double)B * lg.nx * lg.ny * lg.steps;
+    }
+  }
+  return HENRY_OK;
+}
+
+// Per-step entry points of the vertex-centred scheme (states in natural
+// vertex order [n][ny + 1][nx + 1][2]); the cell-centred step_entry's cases.
+template <typename T>
+int vc_step_entry(henry_handle* H, int which, int level, const double* xi, int n, const double* state,
+                  const double* state_old, const double* in, double* out, double* out2, int32_t* iters,
+                  cudaStream_t st) {
+  typedef typename VT<T>::v2 V2;
+  typedef typename VT<T>::b4 B4;
+  VcGroup<T>* Gp = nullptr;
+  int rc = vc_get_group<T>(H, level, n, &Gp);
+  if (rc) return rc;
+  VcGroup<T>& G = *Gp;
+  H->nact = n;
+  rc = vc_set_coefficients<T>(H, G, xi, n, st);
+  if (rc) return rc;
+  auto& L = G.lv[0];
+  const int64_t nv = (int64_t)n * L.NV;
+  const LevelGeom lg = geom(H->cfg, level);
+  const double inv_s = 1.0 / (H->cfg.rho0 * lg.h * lg.h / lg.tau);
+  k_vc_to_storage<double2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const double2*)state, L.x);
+  k_vc_to_storage<double2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const double2*)state_old, L.xo);
+  k_step_flags<<<nblk(n, 128), 128, 0, st>>>(n, G.status, G.newton_active, G.newton_it);
+  CK(cudaMemcpyAsync(G.lin_active, G.newton_active, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  CKL();
+  rc = vc_assemble_fine<T>(H, G, n, lg.tau, inv_s, st);
+  if (!rc && which >= 2) {
+    rc = vc_inject<T>(H, G, n, true, G.lin_active, st);
+    if (!rc) rc = vc_inject<T>(H, G, n, false, G.lin_active, st);
+    if (!rc) rc = vc_coarse_ops<T>(H, G, n, lg.tau, inv_s, st);
+  }
+  if (rc) return rc;
+  switch (which) {
+    case 0:
+      k_vc_from_storage<double2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, G.F, (double2*)out);
+      if (out2) k_vc_blocks_out<B4><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const B4*)L.J, L.plane, out2);
+      break;
+    case 1:
+      k_vc_to_storage<V2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const double2*)in, G.p);
+      k_vc_spmv<T, 0><<<nblk((int64_t)n * L.stride), TPB, 0, st>>>(n, vc_args<T>(L), (const B4*)L.J, G.p, G.v,
+                                                                    nullptr, nullptr, 0, 0, G.lin_active);
+      k_vc_from_storage<V2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, G.v, (double2*)out);
+      break;
+    case 2:
+      k_vc_to_storage<V2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const double2*)in, G.p);
+      CKL();
+      rc = vc_vcycle<T>(H, G, n, G.p, G.ph, st);
+      if (rc) return rc;
+      k_vc_from_storage<V2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, G.ph, (double2*)out);
+      break;
+    case 3:
+      k_vc_to_storage<double2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, (const double2*)in, G.F);
+      k_scale_d2<<<nblk((int64_t)n * L.stride), TPB, 0, st>>>((int64_t)n * L.stride, -1.0, G.F);
+      CKL();
+      CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
+      rc = vc_linear_solve<T>(H, G, n, st);
+      if (rc) return rc;
+      k_vc_from_storage<V2><<<nblk(nv), TPB, 0, st>>>(n, L.nx, L.ny, L.stride, G.dx, (double2*)out);
+      if (iters) CK(cudaMemcpyAsync(iters, G.iters, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+      break;
+  }
+  CKL();
+  return HENRY_OK;
+}
+
 // The level's autotuned settings (henry_autotune) in force for one scope.
 struct TuningScope {
   henry_handle* H;
@@ -1462,6 +2013,10 @@ int check_config(const henry_config& c, bool with_workspace) {
   if (c.coef_model < HENRY_MODEL_UNIFORM3 || c.coef_model > HENRY_MODEL_TWO_LAYER)
     return set_err(HENRY_EINVAL, "bad coef_model");
   if (c.qoi_set < HENRY_QOI_STANDARD || c.qoi_set > HENRY_QOI_PAPER_SERIES) return set_err(HENRY_EINVAL, "bad qoi_set");
+  if (c.scheme != HENRY_SCHEME_CELL && c.scheme != HENRY_SCHEME_VERTEX) return set_err(HENRY_EINVAL, "bad scheme");
+  if (c.scheme == HENRY_SCHEME_VERTEX && (c.coef_model != HENRY_MODEL_UNIFORM3 || c.qoi_set != HENRY_QOI_STANDARD))
+    return set_err(HENRY_EINVAL,
+                   "the vertex-centred scheme solves the three-parameter model with the two standard QoIs");
   if (c.coef_model == HENRY_MODEL_KL &&
       (c.kl_terms < 1 || c.kl_terms > 256 || !(c.kl_corr_len > 0) || !(c.phi_lo > 0) || !(c.phi_hi < 1) ||
        !(c.phi_lo < c.phi_hi)))
@@ -1506,6 +2061,7 @@ void henry_default_config(henry_config* c) {
   c->newton_residual_first = 2;
   c->mg_tail_cells = 128;
   c->mg_tail_batch_cells = 1 << 20;
+  c->scheme = HENRY_SCHEME_CELL;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -1657,7 +2213,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       cands.push_back(t);
       trial((int)cands.size() - 1);
     }
-    const int rfs[3] = {-1, 1, 2};
+    const int rfs[4] = {-1, 2, 3, 4};
     const int b2 = best;
     for (int v : rfs) {
       if (v == cands[b2].newton_residual_first || rc) continue;
@@ -1744,6 +2300,14 @@ void henry_destroy(henry_handle* h) {
     if (kv.second.mem) cudaFree(kv.second.mem);
   }
   for (auto& kv : h->g32) {
+    kv.second.drop_graphs();
+    if (kv.second.mem) cudaFree(kv.second.mem);
+  }
+  for (auto& kv : h->vg64) {
+    kv.second.drop_graphs();
+    if (kv.second.mem) cudaFree(kv.second.mem);
+  }
+  for (auto& kv : h->vg32) {
     kv.second.drop_graphs();
     if (kv.second.mem) cudaFree(kv.second.mem);
   }
@@ -1981,14 +2545,15 @@ int henry_level_batch_solve(henry_handle* h, int level, int with_coarse, const d
   std::memset(&local, 0, sizeof local);
   henry_stats* stp = stats_host ? &local : nullptr;
   int rc;
+  const bool vc = h->cfg.scheme == HENRY_SCHEME_VERTEX;
   if (h->cfg.precision == HENRY_MIXED) {
-    rc = batch_solve_level<float>(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
-    if (!rc && with_coarse)
-      rc = batch_solve_level<float>(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
+    auto solve = vc ? &vc_batch_solve_level<float> : &batch_solve_level<float>;
+    rc = solve(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
+    if (!rc && with_coarse) rc = solve(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
   } else {
-    rc = batch_solve_level<double>(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
-    if (!rc && with_coarse)
-      rc = batch_solve_level<double>(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
+    auto solve = vc ? &vc_batch_solve_level<double> : &batch_solve_level<double>;
+    rc = solve(h, level, xi_dev, n, qoi_fine_dev, status_dev, true, stp, st);
+    if (!rc && with_coarse) rc = solve(h, level - 1, xi_dev, n, qoi_coarse_dev, status_dev, false, stp, st);
   }
   if (rc) return rc;
   // count failed samples (synchronises)
@@ -2014,6 +2579,8 @@ int henry_adjoint(henry_handle* h, int level, const double* xi_dev, int n, const
     return set_err(HENRY_EINVAL, "NULL device pointer");
   if (checkpoint_every <= 0) return set_err(HENRY_EINVAL, "checkpoint_every = %d must be positive", checkpoint_every);
   if (!(h->cfg.adj_rtol > 0.0) || h->cfg.adj_maxit <= 0) return set_err(HENRY_EINVAL, "bad adj_rtol / adj_maxit");
+  if (h->cfg.scheme != HENRY_SCHEME_CELL)
+    return set_err(HENRY_EINVAL, "the discrete adjoint is built for the cell-centred scheme only");
   cudaStream_t st = (cudaStream_t)stream;
   int rc = adjoint_level(h, level, xi_dev, n, qoi_weights_dev, grad_dev, qoi_dev, checkpoint_every, status_dev, st);
   if (rc) return rc;
@@ -2112,12 +2679,47 @@ int mlmc_bias_test(int n_levels, const double* mean_Y, double alpha, double eps,
   return HENRY_OK;
 }
 
+int mlmc_bias_test_fit(int n_levels, int first_level, const double* mean_Y, double alpha_min, double eps,
+                       double* alpha_out, double* bias_est, int32_t* converged) {
+  if (!mean_Y || n_levels <= 0 || first_level < 0 || n_levels - first_level < 2)
+    return set_err(HENRY_EINVAL, "need at least two levels from first_level (n_levels %d, first_level %d)",
+                   n_levels, first_level);
+  if (!(alpha_min > 0.0) || !(eps > 0.0) || !std::isfinite(alpha_min) || !std::isfinite(eps))
+    return set_err(HENRY_EINVAL, "alpha_min and eps must be positive and finite");
+  const int n = n_levels - first_level;
+  std::vector<double> l(n), y(n);
+  for (int i = 0; i < n; ++i) {
+    const double v = std::fabs(mean_Y[first_level + i]);
+    if (!(v > 0.0) || !std::isfinite(v))
+      return set_err(HENRY_EINVAL, "level %d: mean %g must be finite and nonzero", first_level + i,
+                     mean_Y[first_level + i]);
+    l[i] = first_level + i;
+    y[i] = std::log2(v);
+  }
+  const double alpha = std::max(-ls_slope(n, l.data(), y.data()), alpha_min);
+  double a = 0.0;  // intercept of the fit with that slope
+  for (int i = 0; i < n; ++i) a += y[i] + alpha * l[i];
+  a /= n;
+  const double b = std::exp2(a - alpha * (n_levels - 1)) / (std::exp2(alpha) - 1.0);
+  if (!std::isfinite(b)) return set_err(HENRY_EINVAL, "bias estimate is not finite");
+  if (alpha_out) *alpha_out = alpha;
+  if (bias_est) *bias_est = b;
+  if (converged) *converged = b <= eps / std::sqrt(2.0) ? 1 : 0;
+  return HENRY_OK;
+}
+
 #define STEP_DISPATCH(which, in, out, out2, iters)                                                              \
-  (h->cfg.precision == HENRY_MIXED                                                                             \
-       ? step_entry<float>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,        \
-                           (cudaStream_t)stream)                                                               \
-       : step_entry<double>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,       \
-                            (cudaStream_t)stream))
+  (h->cfg.scheme == HENRY_SCHEME_VERTEX                                                                        \
+       ? (h->cfg.precision == HENRY_MIXED                                                                      \
+              ? vc_step_entry<float>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters, \
+                                     (cudaStream_t)stream)                                                     \
+              : vc_step_entry<double>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2,     \
+                                      iters, (cudaStream_t)stream))                                            \
+       : (h->cfg.precision == HENRY_MIXED                                                                      \
+              ? step_entry<float>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters,  \
+                                  (cudaStream_t)stream)                                                        \
+              : step_entry<double>(h, which, level, xi_dev, n, state_dev, state_old_dev, in, out, out2, iters, \
+                                   (cudaStream_t)stream)))
 
 int henry_assemble(henry_handle* h, int level, const double* xi_dev, int n, const double* state_dev,
                    const double* state_old_dev, double* F_dev, double* J_dev, void* stream) {
@@ -2307,8 +2909,9 @@ extern "C" int henry_level_batch_solve_static(const henry_config* cfg, int level
   if (!cfg) return set_err(HENRY_EINVAL, "cfg is NULL");
   int rc = static_check_config(*cfg);
   if (rc) return rc;
-  if (cfg->coef_model != HENRY_MODEL_UNIFORM3)
-    return set_err(HENRY_EINVAL, "the static-scratch solve supports the three-parameter model only");
+  if (cfg->coef_model != HENRY_MODEL_UNIFORM3 || cfg->scheme != HENRY_SCHEME_CELL)
+    return set_err(HENRY_EINVAL,
+                   "the static-scratch solve supports the three-parameter model on the cell-centred scheme only");
   if (level < 0 || level > cfg->max_level) return set_err(HENRY_EINVAL, "level %d outside [0, %d]", level, cfg->max_level);
   if (n <= 0) return set_err(HENRY_EINVAL, "n = %d must be positive", n);
   if (!xi_dev || !qoi_fine_dev || !status_dev) return set_err(HENRY_EINVAL, "NULL device pointer");

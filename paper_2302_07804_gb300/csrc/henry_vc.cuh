@@ -146,19 +146,26 @@ __host__ __device__ inline void vc_face(const VcParams& P, const VcCoef& C, cons
   *G = vd_sub(vd_mul(*F, cf), vd_scale(vd_mul(Dc, dc), 0.5 * P.h));
 }
 
+// Vertex (j, i) -> index of its (p, c) pair in a sample's state array.
+struct VcNaturalIndex {  // [ny + 1][nx + 1] row-major
+  int nx1;
+  __host__ __device__ int operator()(int j, int i) const { return j * nx1 + i; }
+};
+
 // Residual (R^m, R^s) of vertex (j, i) of one sample and, if J is not NULL,
 // its Jacobian row blocks J[(dj + 1) * 3 + (di + 1)][eq][var] with respect to
 // (p, c) of vertex (j + dj, i + di) (36 doubles; zero for neighbours outside
-// the grid).  x, xo: the sample's states, [ny + 1][nx + 1][2] (p, c).
-__host__ __device__ inline void vc_vertex(const VcParams& P, const VcCoef& C, const double* x, const double* xo,
-                                          int j, int i, double* R, double* J) {
-  const int nx1 = P.nx + 1;
+// the grid).  x, xo: the sample's states, pairs (p, c) at idx(j, i)
+// (vc_vertex: natural order [ny + 1][nx + 1][2]).
+template <typename IDX>
+__host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C, const double* x, const double* xo,
+                                             int j, int i, double* R, double* J, IDX idx) {
   double Rm = 0.0, Rs = 0.0;
   double Jm[9][2], Js[9][2];
   for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
 
   // lumped storage
-  const double cv = x[2 * (j * nx1 + i) + 1], cvo = xo[2 * (j * nx1 + i) + 1];
+  const double cv = x[2 * idx(j, i) + 1], cvo = xo[2 * idx(j, i) + 1];
   const double rho = P.rho0 + P.drho * cv, rho_o = P.rho0 + P.drho * cvo;
   const int nel = (i > 0 && j > 0) + (i < P.nx && j > 0) + (i > 0 && j < P.ny) + (i < P.nx && j < P.ny);
   const double w = C.phi * nel * (0.25 * P.h * P.h);
@@ -173,7 +180,7 @@ __host__ __device__ inline void vc_vertex(const VcParams& P, const VcCoef& C, co
     if (ey < 0 || ey >= P.ny || ex < 0 || ex >= P.nx) continue;
     VcDual p[4], c[4], r[4];
     for (int k = 0; k < 4; ++k) {
-      const int vk = (ey + (k >> 1)) * nx1 + ex + (k & 1);
+      const int vk = idx(ey + (k >> 1), ex + (k & 1));
       p[k] = vd_zero();
       p[k].v = x[2 * vk];
       p[k].d[k] = 1.0;
@@ -211,7 +218,7 @@ __host__ __device__ inline void vc_vertex(const VcParams& P, const VcCoef& C, co
   if (i == P.nx) {
     const double pb = P.rho1 * P.g * (P.Ly - j * P.h);
     const double pscale = P.rho0 * P.g * P.Ly;
-    Rm = sc * (x[2 * (j * nx1 + i)] - pb) / pscale;
+    Rm = sc * (x[2 * idx(j, i)] - pb) / pscale;
     Rs = sc * (cv - 1.0);
     for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
     Jm[4][0] = sc / pscale;
@@ -232,4 +239,9 @@ __host__ __device__ inline void vc_vertex(const VcParams& P, const VcCoef& C, co
       J[q * 4 + 3] = Js[q][1];
     }
   }
+}
+
+__host__ __device__ inline void vc_vertex(const VcParams& P, const VcCoef& C, const double* x, const double* xo,
+                                          int j, int i, double* R, double* J) {
+  vc_vertex_at(P, C, x, xo, j, i, R, J, VcNaturalIndex{P.nx + 1});
 }

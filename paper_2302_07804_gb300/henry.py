@@ -17,6 +17,7 @@ HENRY_OK, HENRY_EINVAL, HENRY_ECUDA, HENRY_ENOMEM, HENRY_ENOCONV, HENRY_ELIMIT =
 HENRY_SAMPLE_OK, HENRY_SAMPLE_NEWTON, HENRY_SAMPLE_LINEAR, HENRY_SAMPLE_NONFINITE = range(4)
 HENRY_FP64, HENRY_MIXED = 0, 1
 HENRY_COARSE_REDISCRETISE, HENRY_COARSE_GALERKIN = 0, 1
+HENRY_SCHEME_CELL, HENRY_SCHEME_VERTEX = 0, 1
 HENRY_MODEL_UNIFORM3, HENRY_MODEL_KL, HENRY_MODEL_TWO_LAYER = 0, 1, 2
 HENRY_QOI_STANDARD, HENRY_QOI_PAPER, HENRY_QOI_PAPER_FIELD, HENRY_QOI_PAPER_SERIES = 0, 1, 2, 3
 N_QOI = 2
@@ -27,7 +28,7 @@ EXPORTS = ("henry_default_config", "henry_create", "henry_destroy", "henry_last_
            "henry_apply_jacobian", "henry_precondition", "henry_linear_solve", "henry_profile",
            "henry_profile_read", "henry_level_batch_solve_static", "henry_batch_solve_mixed", "mlmc_rates", "mlmc_bias_test", "henry_adjoint", "henry_n_qoi",
            "henry_paper_config", "henry_kl_basis", "henry_autotune", "henry_get_tuning",
-           "henry_set_tuning", "henry_vc_assemble")
+           "henry_set_tuning", "henry_vc_assemble", "mlmc_bias_test_fit")
 KERNEL_CLASSES = ("assemble", "coarse_ops", "state_restrict", "smooth", "residual_restrict", "coarse_solve",
                   "spmv", "krylov", "newton", "qoi", "fused", "smooth_coarse", "residual", "mg_tail")
 
@@ -46,7 +47,8 @@ class HenryConfig(ctypes.Structure):
                [("lin_retry", ctypes.c_int32), ("finalize_nct", ctypes.c_int32), ("adj_rtol", ctypes.c_double),
                 ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32),
                 ("tile_assembly", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
-                ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32)]
+                ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32),
+                ("scheme", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -108,6 +110,8 @@ def lib():
         L.mlmc_rates.argtypes = [I, I, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
                                  ctypes.POINTER(D), ctypes.POINTER(D)]
         L.mlmc_bias_test.argtypes = [I, ctypes.POINTER(D), D, D, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int32)]
+        L.mlmc_bias_test_fit.argtypes = [I, I, ctypes.POINTER(D), D, D, ctypes.POINTER(D), ctypes.POINTER(D),
+                                         ctypes.POINTER(ctypes.c_int32)]
         L.henry_assemble.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_apply_jacobian.argtypes = [P, I, P, I, P, P, P, P, P]
         L.henry_precondition.argtypes = [P, I, P, I, P, P, P, P, P]
@@ -273,6 +277,16 @@ def mlmc_bias_test(mean_Y, alpha, eps):
     return b.value, bool(ok.value)
 
 
+def mlmc_bias_test_fit(mean_Y, eps, first_level=1, alpha_min=0.5):
+    """(bias estimate from the fitted weak error model, passed, alpha) (host; mlmc_bias_test_fit)."""
+    n = len(mean_Y)
+    arr = (ctypes.c_double * n)(*[float(v) for v in mean_Y])
+    a, b, ok = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().mlmc_bias_test_fit(n, first_level, arr, float(alpha_min), float(eps), ctypes.byref(a),
+                                    ctypes.byref(b), ctypes.byref(ok)))
+    return b.value, bool(ok.value), a.value
+
+
 def level_batch_solve_static(cfg, level, xi, with_coarse=False, stream=None, allow_failures=False):
     """henry_level_batch_solve_static: the batch solve with the library's
     compiled-in device workspace (no device allocation by the library); for
@@ -335,6 +349,12 @@ class Solver:
 
     def grid(self, level):
         return (self.cfg.ny0 << level, self.cfg.nx0 << level)
+
+    def state_shape(self, level):
+        """(rows, columns) of a per-step state: cells, or vertices for the
+        vertex-centred scheme."""
+        ny, nx = self.grid(level)
+        return (ny + 1, nx + 1) if self.cfg.scheme == HENRY_SCHEME_VERTEX else (ny, nx)
 
     def level_batch_solve(self, level, xi, with_coarse=False, stream=None, allow_failures=False, out=None):
         """Returns (qoi_fine[n][2], qoi_coarse[n][2] or None, status[n] int32, stats dict)."""
@@ -405,7 +425,7 @@ class Solver:
         return t.as_dict()
 
     def _states(self, level, xi, state, state_old):
-        ny, nx = self.grid(level)
+        ny, nx = self.state_shape(level)
         n = state.shape[0]
         _dev_f64(xi, (n, self.n_xi), "xi")
         _dev_f64(state, (n, ny, nx, 2), "state")
@@ -414,8 +434,9 @@ class Solver:
 
     def assemble(self, level, xi, state, state_old, with_jacobian=True, stream=None):
         n, ny, nx = self._states(level, xi, state, state_old)
+        nb = 9 if self.cfg.scheme == HENRY_SCHEME_VERTEX else 5
         F = torch.empty((n, ny, nx, 2), dtype=torch.float64, device=state.device)
-        J = torch.empty((n, ny, nx, 5, 2, 2), dtype=torch.float64, device=state.device) if with_jacobian else None
+        J = torch.empty((n, ny, nx, nb, 2, 2), dtype=torch.float64, device=state.device) if with_jacobian else None
         _check(lib().henry_assemble(self._h, level, _ptr(xi), n, _ptr(state), _ptr(state_old), _ptr(F), _ptr(J),
                                     _stream(stream)))
         return F, J

@@ -53,3 +53,10 @@ def random_vectors(tag, n, ny, nx):
 def uniform_xi(tag, n, n_xi=3):
     """n points uniform on [-1, 1]^n_xi (for tests that pass xi in directly)."""
     return rng(tag).uniform(-1.0, 1.0, size=(n, n_xi))
+
+
+def kl_inputs(tag, n, terms=32):
+    """n inputs of the KL random-field model: 2 x terms standard normals
+    (theta_K, theta_phi) and one uniform on [-1, 1] (xi3), shaped (n, 2 terms + 1)."""
+    gen = rng(tag)
+    return np.concatenate([gen.standard_normal((n, 2 * terms)), gen.uniform(-1.0, 1.0, (n, 1))], axis=1)

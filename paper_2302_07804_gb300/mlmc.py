@@ -194,13 +194,19 @@ def run_mlmc(solver, eps=1e-3, max_level=3, pilot=(1000, 200, 50, 20), seed=None
 
 
 def run_mlmc_adaptive(solver, eps=1e-3, L_start=2, L_max=None, pilot=(1000, 200, 50, 20, 10, 10, 10, 10, 10),
-                      seed=None, qoi=1, cost="model", alpha_min=0.5, log=None):
+                      seed=None, qoi=1, cost="model", alpha_min=0.5, log=None, bias="last"):
     """MLMC with the finest level chosen by the bias test (Sec. 3: Eq. (MSE)
     splits eps^2 into eps^2 / 2 for the variance and eps^2 / 2 for the
     squared bias).  Levels 0 .. L_start are allocated as in run_mlmc; the weak
     rate alpha is fitted over levels 1 .. L (mlmc_rates, at least alpha_min),
-    and level L + 1 is added while the bias test fails and L < L_max.  The
-    result of the last run_mlmc pass carries L, the rates and the bias test."""
+    and level L + 1 is added while the bias test fails and L < L_max.
+    bias = "last": E[Y_L] is the level-L sample mean (mlmc_bias_test);
+    "fit": E[Y_L] from the fitted weak error model (mlmc_bias_test_fit).  The
+    result of the last run_mlmc pass carries L, the rates and the bias test
+    (both estimates)."""
+    if bias not in ("last", "fit"):
+        raise ValueError("bias must be 'last' or 'fit'")
+    rule = bias
     L_max = solver.cfg.max_level if L_max is None else L_max
     if L_start < 2 or L_start > L_max:
         raise ValueError("need 2 <= L_start <= L_max to fit the weak rate over levels 1 .. L")
@@ -215,11 +221,14 @@ def run_mlmc_adaptive(solver, eps=1e-3, L_start=2, L_max=None, pilot=(1000, 200,
         s = [level_cost_model(solver.cfg, l) for l in range(L + 1)]
         alpha, beta, gamma_d = henry.mlmc_rates(means, var, s, first_level=1)
         alpha_used = max(alpha, alpha_min)
-        bias, ok = henry.mlmc_bias_test(means, alpha_used, eps)
+        bias_last, ok_last = henry.mlmc_bias_test(means, alpha_used, eps)
+        bias_fit, ok_fit, _ = henry.mlmc_bias_test_fit(means, eps, first_level=1, alpha_min=alpha_min)
+        bias_est, ok = (bias_fit, ok_fit) if rule == "fit" else (bias_last, ok_last)
         if log:
-            log("L=%d alpha=%.3f beta=%.3f gamma_d=%.3f bias=%.3g ok=%s" % (L, alpha, beta, gamma_d, bias, ok))
+            log("L=%d alpha=%.3f beta=%.3f gamma_d=%.3f bias=%.3g ok=%s" % (L, alpha, beta, gamma_d, bias_est, ok))
         res.update({"L": L, "alpha": alpha, "alpha_used": alpha_used, "beta": beta, "gamma_d": gamma_d,
-                    "bias_est": bias, "bias_ok": ok, "wall_seconds": time.perf_counter() - t0,
+                    "bias_est": bias_est, "bias_ok": ok, "bias_rule": rule, "bias_est_last": bias_last,
+                    "bias_est_fit": bias_fit, "wall_seconds": time.perf_counter() - t0,
                     "cell_steps": sum(st.cell_steps for st in state)})
         if ok or L >= L_max:
             return res

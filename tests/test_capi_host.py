@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from conftest import ROOT, golden_rows
@@ -257,3 +258,28 @@ def test_binding_checks_tensors_before_passing_pointers(L):
                    torch.zeros((4, 16, 32, 2), dtype=torch.float64))
     assert "xi: expected shape (4, 65)" in str(e.value)
     s.close()
+
+
+def test_fitted_bias_test_matches_the_oracle(L):
+    """mlmc_bias_test_fit against oracle.mlmc.bias_test_fit on noisy power
+    laws (the bench's bias test), and its argument checks."""
+    from oracle import mlmc as omlmc
+    from paper_2302_07804_gb300 import henry
+    gen = np.random.default_rng(11)
+    for trial in range(20):
+        L_ = int(gen.integers(2, 7))
+        alpha = float(gen.uniform(0.3, 2.0))
+        means = [0.45] + [0.01 * 2.0 ** (-alpha * l) * (1 + 0.3 * gen.standard_normal()) * gen.choice([-1, 1])
+                          for l in range(1, L_ + 1)]
+        eps = float(gen.uniform(1e-4, 1e-2))
+        b, ok, a = henry.mlmc_bias_test_fit(means, eps)
+        bo, oko, ao = omlmc.bias_test_fit(means, eps)
+        assert a == pytest.approx(ao, rel=1e-12) and b == pytest.approx(bo, rel=1e-10) and ok == oko
+    D = ctypes.c_double
+    arr = (D * 3)(0.4, 0.0, 0.01)
+    assert L.mlmc_bias_test_fit(3, 1, arr, 0.5, 1e-3, None, None, None) == henry.HENRY_EINVAL
+    arr = (D * 3)(0.4, 0.02, 0.01)
+    assert L.mlmc_bias_test_fit(3, 2, arr, 0.5, 1e-3, None, None, None) == henry.HENRY_EINVAL
+    assert L.mlmc_bias_test_fit(3, 1, arr, 0.0, 1e-3, None, None, None) == henry.HENRY_EINVAL
+    assert L.mlmc_bias_test_fit(3, 1, arr, 0.5, 1e-3, None, None, None) == henry.HENRY_OK
+

@@ -86,3 +86,19 @@ def test_two_layer_porosity_at_paper_xi_star():
     # layers: the lower one (y < -0.75 in the paper's coordinates) is scaled by 1 + 0.2 xi1
     ratio = c.phi[0, 5] / henry.coefficients_two_layer(prm, grid, [0.0, -0.7257, -0.9616]).phi[0, 5]
     assert np.isfinite(ratio)
+
+
+def test_stored_kl_workload_qois_are_the_oracles():
+    """tests/golden/kl_workload_oracle_qoi.txt (read by the bench) holds the
+    oracle's QoIs of the KL workload's sampled scenarios: recompute the
+    level-0 ones from the same seeded inputs."""
+    from conftest import golden_rows
+    from oracle import henry as oh
+    from paper_2302_07804_gb300 import inputs
+    rows = [r for r in golden_rows("kl_workload_oracle_qoi.txt") if r[0] == "0"]
+    assert len(rows) == 2
+    for lv, i, mass, c in rows:
+        th = inputs.kl_inputs(500 + int(lv), 3264)[int(i)]
+        q, ok = oh.solve_scenario(oh.Params(), int(lv), th, model="kl")
+        assert ok
+        assert q[0] == float(mass) and q[1] == float(c)

@@ -243,6 +243,27 @@ def test_bias_test_is_the_geometric_tail():
         assert mlmc.bias_test(means, alpha, math.sqrt(2.0) * tail * 1.001)[1] is True
 
 
+def test_fitted_bias_test_recovers_the_tail_and_smooths_noise():
+    """The fitted variant: on exact power laws (level 0 off the line, as the
+    level-0 mean is g_0 itself) it returns the exact geometric tail and the
+    exact alpha; with multiplicative noise on the means it stays within the
+    noise's spread of the tail, and a slope below alpha_min is floored."""
+    c, L = 0.01, 5
+    for alpha in (0.7, 1.0, 1.6):
+        means = [0.45] + [c * 2.0 ** (-alpha * l) for l in range(1, L + 1)]
+        tail = sum(c * 2.0 ** (-alpha * l) for l in range(L + 1, 400))
+        b, ok, a = mlmc.bias_test_fit(means, 1.0)
+        assert a == pytest.approx(alpha, rel=1e-12) and b == pytest.approx(tail, rel=1e-10)
+        assert mlmc.bias_test_fit(means, math.sqrt(2.0) * tail * 0.999)[1] is False
+        assert mlmc.bias_test_fit(means, math.sqrt(2.0) * tail * 1.001)[1] is True
+    gen = np.random.default_rng(5)
+    means = [0.45] + [c * 2.0 ** (-l) * (1 + 0.2 * gen.standard_normal()) for l in range(1, L + 1)]
+    b, _, a = mlmc.bias_test_fit(means, 1.0)
+    assert 0.7 < a < 1.3 and 0.5 * c * 2.0 ** -L < b < 2.0 * c * 2.0 ** -L
+    flat = [0.45] + [c] * L
+    assert mlmc.bias_test_fit(flat, 1.0, alpha_min=0.5)[2] == 0.5
+
+
 def test_mlmc_with_independent_samples_agrees_with_plain_mc():
     """Eq. (A) with independent samples on each level (level 0: 40 samples,
     level 1: 12 fine/coarse pairs) estimates E[g_1]; plain Monte Carlo on
