@@ -180,6 +180,10 @@ typedef struct {
                                   (default 2^20; 0: no limit): large batches of small grids run those levels
                                   as separate, large launches */
   int32_t scheme; /* HENRY_SCHEME_CELL (default) or HENRY_SCHEME_VERTEX */
+  int32_t newton_jacobian_every; /* cell-centred scheme: Newton assembles the Jacobian and the coarse operators at
+                                    iterations 0, k, 2k, ... of a time step and reuses them in between (chord
+                                    Newton; k = 1, the default: every iteration).  The FP64 residual test
+                                    decides convergence either way, so the converged states agree to it */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -206,7 +210,8 @@ void henry_paper_config(henry_config* cfg);
  * the V-cycle's smoothing counts and, where the level's grid allows it, the
  * fused one-CTA-per-sample solver; then, one at a time from the best so far,
  * the fused multigrid tail (mg_tail_cells in {0, 128, 512}) and the
- * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}).
+ * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}) and
+ * chord Newton (newton_jacobian_every in {1, 2, 3}, cell-centred scheme).
  * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
  * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
  * off where eligible), then the two later stages - on n_trial samples
@@ -223,7 +228,7 @@ typedef struct {
   double lin_rtol;
   int32_t nu1, nu2, fused_small_grids;
   double cell_steps_per_s; /* measured on the trial batch (0 for the configuration's own settings) */
-  int32_t mg_tail_cells, newton_residual_first; /* as in henry_config */
+  int32_t mg_tail_cells, newton_residual_first, newton_jacobian_every; /* as in henry_config */
 } henry_tuning;
 int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
                    henry_tuning* best_out, void* stream);

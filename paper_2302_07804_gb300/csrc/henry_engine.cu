@@ -941,7 +941,8 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
 // coarse, while the Krylov matvec keeps the exact Jacobian.  The coarse
 // operators of the retried samples are rebuilt by the next Newton iteration.
 template <typename T>
-int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st) {
+int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, double inv_s, cudaStream_t st,
+                       int* retried = nullptr) {
   typedef typename VT<T>::b4 B4;
   const henry_config& c = H->cfg;
   const LevelGeom lg = geom(c, G.level);
@@ -952,6 +953,7 @@ int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, doub
   int n_retry = 0;
   int rc = read_counter(H, G.counter + 2, st, &n_retry);
   if (rc) return rc;
+  if (retried) *retried = n_retry;
   if (n_retry == 0) return HENRY_OK;
   H->nact = n_retry;
   double* pscratch = G.part + P_MAX * (int64_t)B * G.nct;
@@ -1020,12 +1022,21 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
               L.plane, pmax, nullptr, nullptr);
       });
   };
+  // Chord Newton (newton_jacobian_every = k > 1): the Jacobian and the
+  // coarse operators are assembled at iterations 0, k, 2k, ... of the step
+  // (and after a fallback-preconditioner retry, which rebuilt coarse
+  // operators for its samples); the other iterations evaluate the residual
+  // alone and reuse them.  The FP64 residual test still decides convergence.
+  const int jac_every = std::max(1, c.newton_jacobian_every);
+  int last_jac = -1;
+  bool force_jac = false;
   for (int it = 0; it <= c.newton_maxit; ++it) {
+    const bool jac_now = force_jac || last_jac < 0 || it - last_jac >= jac_every;
     // From iteration newton_residual_first on, a sample is most likely
     // converged: its residual is evaluated alone first, and the Jacobian is
     // assembled only for the samples that go on iterating (the residual is
     // recomputed with it, bit-identically).
-    const bool res_first = c.newton_residual_first >= 0 && it >= c.newton_residual_first;
+    const bool res_first = !jac_now || (c.newton_residual_first >= 0 && it >= c.newton_residual_first);
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
     assemble_fine(!res_first);
     launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
@@ -1039,21 +1050,27 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     if (rc) return rc;
     if (n_act == 0) break;
     H->nact = n_act;
-    if (res_first) {
-      assemble_fine(true);
-      CKL();
-    }
-    if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
-      rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
+    if (jac_now) {
+      if (res_first) {
+        assemble_fine(true);
+        CKL();
+      }
+      if (c.coarse_op == HENRY_COARSE_REDISCRETISE) {
+        rc = restrict_states<T>(H, G, B, false, G.lin_active, st);
+        if (rc) return rc;
+      }
+      rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
       if (rc) return rc;
+      last_jac = it;
+      force_jac = false;
     }
-    rc = build_coarse_ops<T>(H, G, B, inv_tau, inv_s, st);
-    if (rc) return rc;
     rc = linear_solve<T>(H, G, B, st);
     if (rc) return rc;
     if (G.Jp && c.lin_retry) {  // fallback preconditioner for the samples whose solve failed
-      rc = retry_linear_solve<T>(H, G, B, inv_tau, inv_s, st);
+      int retried = 0;
+      rc = retry_linear_solve<T>(H, G, B, inv_tau, inv_s, st, &retried);
       if (rc) return rc;
+      if (retried) force_jac = true;
     }
     H->nact = n_act;
     launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
@@ -1620,6 +1637,7 @@ struct TuningScope {
     h->cfg.fused_small_grids = f->second.fused_small_grids;
     h->cfg.mg_tail_cells = f->second.mg_tail_cells;
     h->cfg.newton_residual_first = f->second.newton_residual_first;
+    h->cfg.newton_jacobian_every = std::max(1, f->second.newton_jacobian_every);
   }
   ~TuningScope() { H->cfg = saved; }
 };
@@ -2023,7 +2041,8 @@ int check_config(const henry_config& c, bool with_workspace) {
     return set_err(HENRY_EINVAL, "bad random-field settings");
   if (c.steps0 <= 0 || c.T <= 0 || c.newton_maxit <= 0 || c.lin_maxit <= 0 || c.nu1 < 0 || c.nu2 < 0 ||
       c.lin_rtol <= 0 || (with_workspace && c.workspace_bytes <= 0) ||
-      !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) || !(c.newton_dc_limit >= 0.0))
+      !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) || !(c.newton_dc_limit >= 0.0) ||
+      c.newton_jacobian_every < 1)
     return set_err(HENRY_EINVAL, "bad solver settings");
   return HENRY_OK;
 }
@@ -2059,6 +2078,7 @@ void henry_default_config(henry_config* c) {
   c->qoi_set = HENRY_QOI_STANDARD;
   c->tile_assembly = 1;
   c->newton_residual_first = 2;
+  c->newton_jacobian_every = 1;
   c->mg_tail_cells = 128;
   c->mg_tail_batch_cells = 1 << 20;
   c->scheme = HENRY_SCHEME_CELL;
@@ -2091,7 +2111,8 @@ int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
     h->tuned.erase(level);
     return HENRY_OK;
   }
-  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < 0)
+  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < 0 ||
+      t->newton_jacobian_every < 1)
     return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d, mg_tail_cells %d)", t->lin_rtol, t->nu1,
                    t->nu2, t->mg_tail_cells);
   h->tuned[level] = *t;
@@ -2112,6 +2133,7 @@ int henry_get_tuning(henry_handle* h, int level, henry_tuning* out) {
     out->fused_small_grids = h->cfg.fused_small_grids;
     out->mg_tail_cells = h->cfg.mg_tail_cells;
     out->newton_residual_first = h->cfg.newton_residual_first;
+    out->newton_jacobian_every = h->cfg.newton_jacobian_every;
   }
   return HENRY_OK;
 }
@@ -2153,6 +2175,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         t.fused_small_grids = can_fuse ? (fz == 0 ? 0 : 1) : c.fused_small_grids;
         t.mg_tail_cells = c.mg_tail_cells;
         t.newton_residual_first = c.newton_residual_first;
+        t.newton_jacobian_every = c.newton_jacobian_every;
         cands.push_back(t);
       }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2221,6 +2244,16 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       t.newton_residual_first = v;
       cands.push_back(t);
       trial((int)cands.size() - 1);
+    }
+    if (c.scheme == HENRY_SCHEME_CELL) {  // chord Newton: the Jacobian every 1, 2 or 3 iterations
+      const int b3 = best;
+      for (int v : {1, 2, 3}) {
+        if (v == cands[b3].newton_jacobian_every || rc) continue;
+        henry_tuning t = cands[b3];
+        t.newton_jacobian_every = v;
+        cands.push_back(t);
+        trial((int)cands.size() - 1);
+      }
     }
   }
   h->tuned.erase(level);

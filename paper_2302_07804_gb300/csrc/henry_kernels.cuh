@@ -101,6 +101,55 @@ __device__ __forceinline__ double block_reduce(double v, double* sh) {
   __syncthreads();
   return sh[32];
 }
+// The same sum with fewer FP64 instructions: a shared-memory tree (halving
+// the active threads each stage) down to one warp, then shuffles.  The FP64
+// pipe (2 FMA units per SM on GB300) bounds the Krylov and SpMV kernels, and
+// block_reduce's shuffle stage runs its adds in every warp: 5 per warp, 45
+// warp instructions per 256-thread CTA, against 12 here.  sh: blockDim.x + 1
+// doubles; blockDim.x a power of two >= 64.  Deterministic order.
+__device__ __forceinline__ double block_sum_tree(double v, double* sh) {
+  const int t = threadIdx.x, n = blockDim.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int s = n >> 1; s >= 32; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+  if (t < 32) {
+    double u = warp_sum(sh[t]);
+    if (t == 0) sh[n] = u;
+  }
+  __syncthreads();
+  return sh[n];
+}
+// CTA-wide max of non-negative doubles without NaNs (+inf allowed) on the
+// integer pipes: for such values the IEEE-754 bit patterns order like the
+// values, so the max of the 64-bit patterns is the max of the values (the
+// same result as block_reduce<true>, with no FP64 instruction).
+__device__ __forceinline__ double block_max_nonneg(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, u, o);
+    u = x > u ? x : u;
+  }
+  unsigned long long* su = reinterpret_cast<unsigned long long*>(sh);
+  __syncthreads();
+  if (lane == 0) su[w] = u;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long x = lane < nw ? su[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = y > x ? y : x;
+    }
+    if (lane == 0) su[32] = x;
+  }
+  __syncthreads();
+  return __longlong_as_double((long long)su[32]);
+}
 // Sum of a sample's nct partials, computed identically by every CTA of the
 // sample (fixed order), returned to every thread.
 __device__ __forceinline__ double sample_sum(const double* __restrict__ p, int nct, double* sh) {
@@ -361,7 +410,7 @@ __global__ void __launch_bounds__(TPB) k_assemble(Phys ph, const Coef* __restric
     if (F) F[e] = make_double2(fm, fs);
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
-    const double bm = block_reduce<true>(loc, sh);
+    const double bm = block_max_nonneg(loc, sh);
     if (threadIdx.x == 0) {
       const int nct = N / TPB;
       rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
@@ -565,7 +614,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
     if (F) F[e] = make_double2(fm, fs);
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
-    const double bm = block_reduce<true>(loc, sh);
+    const double bm = block_max_nonneg(loc, sh);
     if (threadIdx.x == 0) {
       const int nct = N / TPB;
       rmax_part[(int64_t)s * nct + (st / TPB)] = bm;
@@ -688,7 +737,7 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __
     if (F) F[e] = make_double2(fm, fs);
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;  // NaN or inf
-    const double bm = block_reduce<true>(loc, sh);
+    const double bm = block_max_nonneg(loc, sh);
     if (threadIdx.x == 0) rmax_part[(int64_t)s * tiles + tile] = bm;
   }
   if constexpr (JAC) {
@@ -1001,7 +1050,7 @@ __global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typen
                                               const typename VT<T>::v2* __restrict__ w1, double* __restrict__ part,
                                               int slot1, int slot2, const int* __restrict__ active) {
   typedef typename VT<T>::v2 V2;
-  __shared__ double sh[40];
+  __shared__ double sh[TPB + 1];
   const int N = nx * ny, nct = N / TPB;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int s = (int)(e / N);
@@ -1015,9 +1064,9 @@ __global__ void __launch_bounds__(TPB) k_spmv(int B, int nx, int ny, const typen
   if (NDOT >= 1 && part) {
     // per-cell products in T, widened once for the FP64 CTA reduction
     const V2 ww = w1[e];
-    const double d1 = block_reduce<false>((double)fma_(ww.x, yy.x, ww.y * yy.y), sh);
+    const double d1 = block_sum_tree((double)fma_(ww.x, yy.x, ww.y * yy.y), sh);
     double d2 = 0.0;
-    if (NDOT == 2) d2 = block_reduce<false>((double)fma_(yy.x, yy.x, yy.y * yy.y), sh);
+    if (NDOT == 2) d2 = block_sum_tree((double)fma_(yy.x, yy.x, yy.y * yy.y), sh);
     if (threadIdx.x == 0) {
       const int64_t pi = (int64_t)s * nct + st / TPB, stride = (int64_t)B * nct;
       part[slot1 * stride + pi] = d1;
@@ -1039,7 +1088,7 @@ __global__ void __launch_bounds__(TPB) k_bicg_init(int B, int N, const double2* 
                                                    typename VT<T>::v2* __restrict__ dx, double* __restrict__ part,
                                                    const int* __restrict__ active) {
   typedef typename VT<T>::v2 V2;
-  __shared__ double sh[40];
+  __shared__ double sh[TPB + 1];
   const int nct = N / TPB;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int s = (int)(e / N);
@@ -1052,7 +1101,7 @@ __global__ void __launch_bounds__(TPB) k_bicg_init(int B, int N, const double2* 
   p[e] = z;
   v[e] = z;
   dx[e] = z;
-  const double bs = block_reduce<false>((double)fma_(rr.x, rr.x, rr.y * rr.y), sh);
+  const double bs = block_sum_tree((double)fma_(rr.x, rr.x, rr.y * rr.y), sh);
   if (threadIdx.x == 0) {
     const int64_t pi = (int64_t)s * nct + (e - (int64_t)s * N) / TPB, stride = (int64_t)B * nct;
     part[P_RR * stride + pi] = bs;
@@ -1084,31 +1133,45 @@ __global__ void __launch_bounds__(TPB) k_bicg_p(int B, int N, int it, int maxit,
   const int64_t stride = (int64_t)B * nct;
   const double rho = sample_sum_or_fin(part, fin, P_RR, stride, s, nct, sh);
   const double rn2 = sample_sum_or_fin(part, fin, P_RN, stride, s, nct, sh);
-  const double bn2 = (it == 0) ? rn2 : sc[s].bnorm2;
-  const bool finite = (rn2 <= 1.0e300) && (rho == rho);
-  if (!finite || rn2 <= rtol2 * bn2 || it >= maxit) {
-    // A sample that reaches maxit keeps its last iterate (inexact Newton
-    // step; Newton's own test decides); a non-finite one fails.
-    if (threadIdx.x == 0 && ct == 0) {
-      lin_active[s] = 0;
-      iters[s] = !finite ? -2 : ((rn2 <= rtol2 * bn2) ? it : -1);
-      atomicAdd(lin_total, (unsigned long long)it);
+  // The test and the Krylov scalars once per CTA, by thread 0 (an FP64
+  // division is a long FP64-pipe sequence, and every thread would compute
+  // the same values); bc = (stop code, beta, omega).
+  __shared__ double bc[3];
+  if (threadIdx.x == 0) {
+    const double bn2 = (it == 0) ? rn2 : sc[s].bnorm2;
+    const bool finite = (rn2 <= 1.0e300) && (rho == rho);
+    const bool conv = rn2 <= rtol2 * bn2;
+    bc[0] = (!finite || conv || it >= maxit) ? (!finite ? -2.0 : (conv ? (double)it : -1.0)) : -3.0;
+    if (bc[0] != -3.0) {
+      // A sample that reaches maxit keeps its last iterate (inexact Newton
+      // step; Newton's own test decides); a non-finite one fails.
+      if (ct == 0) {
+        lin_active[s] = 0;
+        iters[s] = (int)bc[0];
+        atomicAdd(lin_total, (unsigned long long)it);
+      }
+    } else {
+      if (ct == 0) {
+        atomicAdd(n_active, 1);
+        if (it == 0) sc[s].bnorm2 = bn2;
+      }
+      if (it > 0) {
+        const LinScal q = sc[s];
+        bc[1] = (rho / q.rho) * (q.alpha / q.omega);
+        bc[2] = q.omega;
+      }
     }
-    return;
   }
-  if (threadIdx.x == 0 && ct == 0) {
-    atomicAdd(n_active, 1);
-    if (it == 0) sc[s].bnorm2 = bn2;
-  }
+  __syncthreads();
+  if (bc[0] != -3.0) return;
   const V2 rr = r[e];
   if (it == 0) {
     p[e] = rr;
     return;
   }
-  const LinScal q = sc[s];
-  const double beta = (rho / q.rho) * (q.alpha / q.omega);
+  const double beta = bc[1], omega = bc[2];
   const V2 pp = p[e], vv = v[e];
-  const T bt = (T)beta, om = (T)q.omega;
+  const T bt = (T)beta, om = (T)omega;
   p[e] = mk2<V2>(rr.x + bt * (pp.x - om * vv.x), rr.y + bt * (pp.y - om * vv.y));
 }
 
@@ -1129,7 +1192,10 @@ __global__ void __launch_bounds__(TPB) k_bicg_s(int B, int N, const typename VT<
   const int64_t stride = (int64_t)B * nct;
   const double rho = sample_sum_or_fin(part, fin, P_RR, stride, s, nct, sh);
   const double rv = sample_sum_or_fin(part, fin, P_RV, stride, s, nct, sh);
-  const double alpha = rho / rv;
+  __shared__ double bc;
+  if (threadIdx.x == 0) bc = rho / rv;  // once per CTA
+  __syncthreads();
+  const double alpha = bc;
   if (threadIdx.x == 0 && ct == 0) {
     sc[s].rho = rho;
     sc[s].alpha = alpha;
@@ -1152,7 +1218,7 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
                                                      LinScal* __restrict__ sc, const int* __restrict__ lin_active,
                                                      const double* __restrict__ fin) {
   typedef typename VT<T>::v2 V2;
-  __shared__ double sh[40];
+  __shared__ double sh[TPB + 1];
   const int nct = N / TPB;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int s = (int)(e / N);
@@ -1161,7 +1227,10 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
   const int64_t stride = (int64_t)B * nct;
   const double ts = sample_sum_or_fin(part, fin, P_TS, stride, s, nct, sh);
   const double tt = sample_sum_or_fin(part, fin, P_TT, stride, s, nct, sh);
-  const double omega = (tt > 0.0) ? ts / tt : 0.0;
+  __shared__ double bc;
+  if (threadIdx.x == 0) bc = (tt > 0.0) ? ts / tt : 0.0;  // once per CTA
+  __syncthreads();
+  const double omega = bc;
   const double alpha = sc[s].alpha;
   if (threadIdx.x == 0 && ct == 0) sc[s].omega = omega;
   const T a = (T)alpha, w = (T)omega;
@@ -1169,8 +1238,8 @@ __global__ void __launch_bounds__(TPB) k_bicg_update(int B, int N, typename VT<T
   dx[e] = mk2<V2>(x0.x + a * p0.x + w * s0.x, x0.y + a * p0.y + w * s0.y);
   const V2 rn = mk2<V2>(sv0.x - w * t0.x, sv0.y - w * t0.y);
   r[e] = rn;
-  const double d1 = block_reduce<false>((double)fma_(rh0.x, rn.x, rh0.y * rn.y), sh);
-  const double d2 = block_reduce<false>((double)fma_(rn.x, rn.x, rn.y * rn.y), sh);
+  const double d1 = block_sum_tree((double)fma_(rh0.x, rn.x, rh0.y * rn.y), sh);
+  const double d2 = block_sum_tree((double)fma_(rn.x, rn.x, rn.y * rn.y), sh);
   if (threadIdx.x == 0) {
     const int64_t pi = (int64_t)s * nct + ct;
     part[P_RR * stride + pi] = d1;
@@ -1238,8 +1307,8 @@ __global__ void __launch_bounds__(TPB) k_newton_step_max(int B, int N, double in
   double loc = fmax(fabs((double)d.x) * inv_pref, dc);
   if (!(loc <= 1.0e300)) loc = INFINITY;
   if (!(dc <= 1.0e300)) dc = INFINITY;
-  const double m = block_reduce<true>(loc, sh);
-  const double mc = block_reduce<true>(dc, sh);
+  const double m = block_max_nonneg(loc, sh);
+  const double mc = block_max_nonneg(dc, sh);
   if (threadIdx.x == 0) {
     const int64_t i = (int64_t)s * nct + (e - (int64_t)s * N) / TPB;
     dmax_part[i] = m;

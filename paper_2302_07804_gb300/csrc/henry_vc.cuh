@@ -30,9 +30,10 @@
 //    the corners); y = 0, Ly: no flux (Sec. 2.1).  A Dirichlet equation is
 //    (value - boundary value) x rho0 h^2/tau, with p in units of rho0 g Ly.
 //
-// Derivatives are forward-mode: every quantity of an element carries its
-// derivatives with respect to the element's 8 unknowns (p0..p3, c0..c3).
-// Upwind choices are taken on the values.
+// Derivatives are exact: each face's fluxes are differentiated by hand with
+// respect to the element's 8 unknowns (p0..p3, c0..c3), the chain rule
+// written out for the bilinear gradients, the interpolated densities and the
+// partial-upwind share.  Upwind choices are taken on the values.
 //
 // The functions are plain arithmetic with __host__ __device__ qualifiers, so
 // the same code also compiles as host C++.
@@ -53,97 +54,70 @@ struct VcCoef {
   double phi, kmu, PD, qin;  // porosity, K / mu, phi Dm, inflow velocity
 };
 
-// A value with its derivatives with respect to the element's unknowns
-// (slot k: p of corner k; slot 4 + k: c of corner k).
-struct VcDual {
-  double v;
-  double d[8];
-};
-
-__host__ __device__ inline VcDual vd_zero() {
-  VcDual r;
-  r.v = 0.0;
-  for (int k = 0; k < 8; ++k) r.d[k] = 0.0;
-  return r;
-}
-
-__host__ __device__ inline VcDual vd_add(const VcDual& a, const VcDual& b) {
-  VcDual r;
-  r.v = a.v + b.v;
-  for (int k = 0; k < 8; ++k) r.d[k] = a.d[k] + b.d[k];
-  return r;
-}
-
-__host__ __device__ inline VcDual vd_sub(const VcDual& a, const VcDual& b) {
-  VcDual r;
-  r.v = a.v - b.v;
-  for (int k = 0; k < 8; ++k) r.d[k] = a.d[k] - b.d[k];
-  return r;
-}
-
-__host__ __device__ inline VcDual vd_scale(const VcDual& a, double s) {
-  VcDual r;
-  r.v = a.v * s;
-  for (int k = 0; k < 8; ++k) r.d[k] = a.d[k] * s;
-  return r;
-}
-
-__host__ __device__ inline VcDual vd_mul(const VcDual& a, const VcDual& b) {
-  VcDual r;
-  r.v = a.v * b.v;
-  for (int k = 0; k < 8; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-  return r;
-}
-
-__host__ __device__ inline VcDual vd_div(const VcDual& a, const VcDual& b) {
-  VcDual r;
-  r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
-  for (int k = 0; k < 8; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
-  return r;
-}
-
-// w0 u0 + w1 u1 + w2 u2 + w3 u3
-__host__ __device__ inline VcDual vd_lin4(const VcDual* u, double w0, double w1, double w2, double w3) {
-  VcDual r = vd_scale(u[0], w0);
-  r = vd_add(r, vd_scale(u[1], w1));
-  r = vd_add(r, vd_scale(u[2], w2));
-  return vd_add(r, vd_scale(u[3], w3));
-}
-
 // Mass and salt flux through face f of an element, from its corner a to its
-// corner b, given the corners' p, c and rho.
-__host__ __device__ inline void vc_face(const VcParams& P, const VcCoef& C, const VcDual* p, const VcDual* c,
-                                        const VcDual* rho, int f, VcDual* F, VcDual* G) {
+// corner b, and their derivatives with respect to the element's unknowns
+// (slot k: p of corner k, slot 4 + k: c of corner k), given the corners'
+// p and c; ih = 1 / h.  (Divisions are few: on GPUs with few FP64 units a
+// division is a long sequence of FP64 instructions.)
+__host__ __device__ inline void vc_face(const VcParams& P, const VcCoef& C, const double* p, const double* c, int f,
+                                        double ih, double& F, double* dF, double& G, double* dG) {
   const int a = (f == 1) ? 2 : ((f == 3) ? 1 : 0);
   const int b = (f == 0) ? 1 : ((f == 2) ? 2 : 3);
   const double xi = (f == 2) ? 0.25 : ((f == 3) ? 0.75 : 0.5);
   const double eta = (f == 0) ? 0.25 : ((f == 1) ? 0.75 : 0.5);
-  const double ih = 1.0 / P.h;
-  VcDual dp, dc, grav;
+  const double hh = 0.5 * P.h;
+  // gradient weights (normal component, 1/h included), bilinear weights at
+  // the face point, weights of the gravity density (y faces only)
+  double gw[4], w[4], rg[4];
   if (f < 2) {  // normal +x
-    dp = vd_scale(vd_lin4(p, -(1.0 - eta), 1.0 - eta, -eta, eta), ih);
-    dc = vd_scale(vd_lin4(c, -(1.0 - eta), 1.0 - eta, -eta, eta), ih);
-    grav = vd_zero();
+    gw[0] = -(1.0 - eta) * ih; gw[1] = (1.0 - eta) * ih; gw[2] = -eta * ih; gw[3] = eta * ih;
+    rg[0] = rg[1] = rg[2] = rg[3] = 0.0;
   } else {  // normal +y
-    dp = vd_scale(vd_lin4(p, -(1.0 - xi), -xi, 1.0 - xi, xi), ih);
-    dc = vd_scale(vd_lin4(c, -(1.0 - xi), -xi, 1.0 - xi, xi), ih);
-    grav = vd_scale(vd_lin4(rho, 0.5 * (1.0 - xi), 0.5 * xi, 0.5 * (1.0 - xi), 0.5 * xi), P.g);
+    gw[0] = -(1.0 - xi) * ih; gw[1] = -xi * ih; gw[2] = (1.0 - xi) * ih; gw[3] = xi * ih;
+    rg[0] = rg[2] = 0.5 * (1.0 - xi); rg[1] = rg[3] = 0.5 * xi;
   }
-  const VcDual qn = vd_scale(vd_add(dp, grav), -C.kmu);
-  const VcDual rho_ip = vd_lin4(rho, (1.0 - xi) * (1.0 - eta), xi * (1.0 - eta), (1.0 - xi) * eta, xi * eta);
-  *F = vd_scale(vd_mul(rho_ip, qn), 0.5 * P.h);
-  const VcDual Dc = vd_scale(rho_ip, C.PD);
-  const bool pos = F->v >= 0.0;
-  const VcDual absF = pos ? *F : vd_scale(*F, -1.0);
-  VcDual s = vd_zero();
-  if (Dc.v < 2.0 * absF.v) {
-    s = vd_sub(vd_zero(), vd_div(Dc, vd_scale(absF, 2.0)));
-    s.v += 1.0;
+  w[0] = (1.0 - xi) * (1.0 - eta); w[1] = xi * (1.0 - eta); w[2] = (1.0 - xi) * eta; w[3] = xi * eta;
+  double dp = 0.0, dc = 0.0, grav = 0.0, rip = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const double rho = P.rho0 + P.drho * c[k];
+    dp += gw[k] * p[k];
+    dc += gw[k] * c[k];
+    grav += rg[k] * rho;
+    rip += w[k] * rho;
   }
-  const double sg = pos ? 1.0 : -1.0;
-  const VcDual cf = vd_add(vd_scale(vd_add(c[a], c[b]), 0.5), vd_scale(vd_mul(s, vd_sub(c[a], c[b])), 0.5 * sg));
-  *G = vd_sub(vd_mul(*F, cf), vd_scale(vd_mul(Dc, dc), 0.5 * P.h));
+  grav *= P.g;
+  const double qn = -C.kmu * (dp + grav);
+  F = rip * qn * hh;
+  double dDc[8], ddc[8];
+  for (int k = 0; k < 4; ++k) {
+    dF[k] = rip * (-C.kmu * gw[k]) * hh;                                    // d/dp_k
+    dF[4 + k] = (w[k] * P.drho * qn + rip * (-C.kmu * P.g * rg[k] * P.drho)) * hh;  // d/dc_k
+    dDc[k] = 0.0;
+    dDc[4 + k] = w[k] * P.drho * C.PD;
+    ddc[k] = 0.0;
+    ddc[4 + k] = gw[k];
+  }
+  const double Dc = rip * C.PD;
+  // partial upwind share s = max(0, 1 - Dc / (2 |F|)), its sign from F
+  const bool pos = F >= 0.0;
+  const double sg = pos ? 1.0 : -1.0, A = pos ? F : -F;
+  double s = 0.0, ds[8];
+  for (int j = 0; j < 8; ++j) ds[j] = 0.0;
+  if (Dc < 2.0 * A) {
+    const double i2A = 0.5 / A;  // 1 / (2 |F|)
+    s = 1.0 - Dc * i2A;
+    const double u = Dc * sg * (2.0 * i2A);  // Dc sgn(F) / |F|
+    for (int j = 0; j < 8; ++j) ds[j] = (u * dF[j] - dDc[j]) * i2A;
+  }
+  const double cab = c[a] - c[b];
+  const double cf = 0.5 * (c[a] + c[b]) + 0.5 * sg * s * cab;
+  G = F * cf - Dc * dc * hh;
+  for (int j = 0; j < 8; ++j) {
+    double dcf = 0.5 * sg * cab * ds[j];
+    if (j == 4 + a) dcf += 0.5 + 0.5 * sg * s;
+    if (j == 4 + b) dcf += 0.5 - 0.5 * sg * s;
+    dG[j] = dF[j] * cf + F * dcf - (dDc[j] * dc + Dc * ddc[j]) * hh;
+  }
 }
 
 // Vertex (j, i) -> index of its (p, c) pair in a sample's state array.
@@ -168,44 +142,38 @@ __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C,
   const double cv = x[2 * idx(j, i) + 1], cvo = xo[2 * idx(j, i) + 1];
   const double rho = P.rho0 + P.drho * cv, rho_o = P.rho0 + P.drho * cvo;
   const int nel = (i > 0 && j > 0) + (i < P.nx && j > 0) + (i > 0 && j < P.ny) + (i < P.nx && j < P.ny);
-  const double w = C.phi * nel * (0.25 * P.h * P.h);
-  Rm += w * (rho - rho_o) / P.tau;
-  Jm[4][1] += w * P.drho / P.tau;
-  Rs += w * (rho * cv - rho_o * cvo) / P.tau;
-  Js[4][1] += w * (rho + P.drho * cv) / P.tau;
+  const double wt = C.phi * nel * (0.25 * P.h * P.h) / P.tau;  // lumped phi |CV| / tau
+  const double ih = 1.0 / P.h;
+  Rm += wt * (rho - rho_o);
+  Jm[4][1] += wt * P.drho;
+  Rs += wt * (rho * cv - rho_o * cvo);
+  Js[4][1] += wt * (rho + P.drho * cv);
 
   // the faces of the (up to four) elements this vertex is a corner of
   for (int kv = 0; kv < 4; ++kv) {
     const int ey = j - (kv >> 1), ex = i - (kv & 1);
     if (ey < 0 || ey >= P.ny || ex < 0 || ex >= P.nx) continue;
-    VcDual p[4], c[4], r[4];
+    double p[4], c[4];
     for (int k = 0; k < 4; ++k) {
       const int vk = idx(ey + (k >> 1), ex + (k & 1));
-      p[k] = vd_zero();
-      p[k].v = x[2 * vk];
-      p[k].d[k] = 1.0;
-      c[k] = vd_zero();
-      c[k].v = x[2 * vk + 1];
-      c[k].d[4 + k] = 1.0;
-      r[k] = vd_zero();
-      r[k].v = P.rho0 + P.drho * c[k].v;
-      r[k].d[4 + k] = P.drho;
+      p[k] = x[2 * vk];
+      c[k] = x[2 * vk + 1];
     }
     for (int f = 0; f < 4; ++f) {
       const int a = (f == 1) ? 2 : ((f == 3) ? 1 : 0);
       const int b = (f == 0) ? 1 : ((f == 2) ? 2 : 3);
       if (a != kv && b != kv) continue;
-      VcDual F, G;
-      vc_face(P, C, p, c, r, f, &F, &G);
+      double F, G, dF[8], dG[8];
+      vc_face(P, C, p, c, f, ih, F, dF, G, dG);
       const double sgn = (a == kv) ? 1.0 : -1.0;  // out of this vertex's volume
-      Rm += sgn * F.v;
-      Rs += sgn * G.v;
+      Rm += sgn * F;
+      Rs += sgn * G;
       for (int k = 0; k < 4; ++k) {
         const int q = (ey + (k >> 1) - j + 1) * 3 + (ex + (k & 1) - i + 1);
-        Jm[q][0] += sgn * F.d[k];
-        Jm[q][1] += sgn * F.d[4 + k];
-        Js[q][0] += sgn * G.d[k];
-        Js[q][1] += sgn * G.d[4 + k];
+        Jm[q][0] += sgn * dF[k];
+        Jm[q][1] += sgn * dF[4 + k];
+        Js[q][0] += sgn * dG[k];
+        Js[q][1] += sgn * dG[4 + k];
       }
     }
   }

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
     F[e] = make_double2(fm, fs);
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;
-    const double bm = block_reduce<true>(loc, sh);
+    const double bm = block_max_nonneg(loc, sh);
     if (threadIdx.x == 0) rmax_part[(int64_t)s * (stride / TPB) + st / TPB] = bm;
   }
   if (J) {
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(TPB) k_vc_spmv(int B, VcLevelArgs L, const typ
                                                  const typename VT<T>::v2* __restrict__ w1, double* __restrict__ part,
                                                  int slot1, int slot2, const int* __restrict__ active) {
   typedef typename VT<T>::v2 V2;
-  __shared__ double sh[40];
+  __shared__ double sh[TPB + 1];
   const int nxv = L.nx + 1, nyv = L.ny + 1, NV = nxv * nyv, nct = L.stride / TPB;
   const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const int s = (int)(e / L.stride);
@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(TPB) k_vc_spmv(int B, VcLevelArgs L, const typ
   y[e] = yy;
   if (NDOT >= 1 && part) {
     const V2 ww = w1[e];
-    const double d1 = block_reduce<false>((double)fma_(ww.x, yy.x, ww.y * yy.y), sh);
+    const double d1 = block_sum_tree((double)fma_(ww.x, yy.x, ww.y * yy.y), sh);
     double d2 = 0.0;
-    if (NDOT == 2) d2 = block_reduce<false>((double)fma_(yy.x, yy.x, yy.y * yy.y), sh);
+    if (NDOT == 2) d2 = block_sum_tree((double)fma_(yy.x, yy.x, yy.y * yy.y), sh);
     if (threadIdx.x == 0) {
       const int64_t pi = (int64_t)s * nct + st / TPB, stride = (int64_t)B * nct;
       part[slot1 * stride + pi] = d1;

@@ -48,7 +48,7 @@ class HenryConfig(ctypes.Structure):
                 ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32),
                 ("tile_assembly", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
                 ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32),
-                ("scheme", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("newton_jacobian_every", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -73,7 +73,8 @@ class HenryTuning(ctypes.Structure):
     """henry_tuning: a level's solver settings chosen by henry_autotune."""
     _fields_ = [("lin_rtol", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double),
-                ("mg_tail_cells", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32)]
+                ("mg_tail_cells", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
+                ("newton_jacobian_every", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -217,7 +217,7 @@ def test_autotune_arguments_return_einval(L):
     assert L.henry_autotune(s._h, 9, 0, P(16), 4, ctypes.byref(t), None) == henry.HENRY_EINVAL
     # without tuning, a level's settings are the configuration's
     assert s.tuning(2) == {"lin_rtol": 1e-4, "nu1": 2, "nu2": 2, "fused_small_grids": 1, "cell_steps_per_s": 0.0,
-                           "mg_tail_cells": 128, "newton_residual_first": 2}
+                           "mg_tail_cells": 128, "newton_residual_first": 2, "newton_jacobian_every": 1}
     bad = dict(s.tuning(2), mg_tail_cells=-1)
     with pytest.raises(henry.HenryError):
         s.set_tuning(2, bad)

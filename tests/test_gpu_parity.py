@@ -468,3 +468,21 @@ def test_fused_multigrid_tail_is_bit_identical(hl, precision):
         s.close()
     assert torch.equal(q[0][0], q[1][0]) and torch.equal(q[0][1], q[1][1]) and torch.equal(q[0][2], q[1][2])
     assert q[0][3] == q[1][3]
+
+
+@pytest.mark.parametrize("every,precision", [(2, 0), (3, 0), (2, 1)])
+def test_chord_newton_reaches_the_oracle_solution(hl, every, precision):
+    """Chord Newton (the Jacobian and coarse operators re-assembled every
+    k-th iteration of a step, the residual alone in between) converges to the
+    same discrete solution: level-1 solves with coarse partners against the
+    oracle at relative 1e-10, FP64 and mixed precision (multi-kernel path)."""
+    s = hl.Solver(newton_jacobian_every=every, precision=precision, fused_small_grids=0)
+    xi = hl.sample_xi(inputs.SEED, 1, 4600, 3)
+    qf, qc, st, stats = s.level_batch_solve(1, xi, with_coarse=True)
+    assert int(st.abs().sum()) == 0
+    x = xi.cpu().numpy()
+    ref1, _ = ohenry.solve_scenarios(PRM, 1, x)
+    ref0, _ = ohenry.solve_scenarios(PRM, 0, x)
+    _qoi_check(qf.cpu().numpy(), ref1)
+    _qoi_check(qc.cpu().numpy(), ref0)
+    s.close()
