@@ -14,7 +14,10 @@ also carries the e2e figure (host xi in pinned memory copied in, QoIs and
 sums copied out every step), the roofline of the dominant kernel class (from
 the library's CUDA-event kernel timer over one extra step), the clocks seen
 during the timed region, the oracle's CPU throughput on a bounded sample,
-and the MLMC time to RMSE 1e-3 for FP64 and mixed precision.
+the MLMC time to RMSE 1e-3 for FP64 and mixed precision with the bias test
+(levels added from L = 3) and to the variance budget alone at L = 3, and the
+other workloads: 4096 uneven scenarios over levels 0..5 (FP64; KL fields in
+mixed precision, against stored oracle QoIs) and the discrete adjoint.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -455,12 +458,14 @@ class Workload:
 UNEVEN_COUNTS = (3264, 656, 128, 32, 8, 8)  # 4096 scenarios, the shape of Eq. (M_ell) under the paper's (V_l, s_l)
 
 
-def uneven_workload(henry, torch, dev, kl, overrides=None):
+def uneven_workload(henry, torch, dev, kl, overrides=None, tuning=None):
     """4096 scenarios spread over levels 0..5 (32x16x20 .. 1024x512x640), all
     levels concurrently (one stream and handle each) in one
     henry_batch_solve_mixed call after an untimed warm-up call.  kl = False:
     FP64, three-parameter model; kl = True: KL random fields in mixed
     precision, with the QoI difference to FP64 GPU solves of the same inputs.
+    tuning: {level: henry_autotune settings} applied to those levels (the
+    MLMC step's, tuned on the same model and precision).
     Returns (line, per-level inputs, per-level mixed-precision QoIs)."""
     import numpy as np
     from paper_2302_07804_gb300 import inputs
@@ -477,6 +482,8 @@ def uneven_workload(henry, torch, dev, kl, overrides=None):
             xis.append(henry.sample_xi(inputs.SEED, l, 2 * 10 ** 7, m, device=dev))
     cs = sum(m * (cfg.nx0 << l) * (cfg.ny0 << l) * (cfg.steps0 << l) for l, m in enumerate(counts))
     W = Workload(henry, torch, dev, counts, prec, [xis], with_coarse=False, **kw)
+    for l, t in (tuning or {}).items():
+        W.solver.set_tuning(int(l), t)
     W.run(0)  # warm-up: workspaces and KL tables
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -489,6 +496,7 @@ def uneven_workload(henry, torch, dev, kl, overrides=None):
     line = {"workload": "uneven-4096-levels0-5" + ("-kl-mixed" if kl else "-fp64"), "metric": METRIC,
             "value": cs / sec, "unit": "cell-steps/s", "seconds": sec, "counts": counts, "cell_steps": cs,
             "failed_samples": W.fails, "clocks": clk.summary(), "iterations": W.iteration_means(),
+            "tuning": ({str(l): t for l, t in tuning.items()} if tuning else "configuration defaults"),
             "schedule": "one henry_batch_solve_mixed call: levels concurrent, one stream + child handle each"}
     q32 = [W.outs[l][0].clone() for l in range(len(counts))]
     if kl:
@@ -732,14 +740,16 @@ def mlmc_bias_checked(henry, mlmc, torch, inputs, t_start):
             out[key] = {"seconds": r["wall_seconds"], "L": r["L"], "bias_est": r["bias_est"],
                         "bias_ok": r["bias_ok"], "bias_est_last_level_mean": r["bias_est_last"],
                         "alpha": r["alpha"], "beta": r["beta"],
-                        "rmse_stat": r["rmse_stat"], "rmse_bound": math.sqrt(r["variance"] + r["bias_est"] ** 2),
+                        "rmse_stat": r["rmse_stat"], "rmse_bound": r["rmse_bound"], "rmse_ok": r["rmse_ok"],
                         "estimate": r["estimate"], "alloc": r["alloc"], "cell_steps": r["cell_steps"],
                         "samples": [p["n"] for p in r["levels"]]}
             s2.close()
     out["note"] = ("fresh handle per run (device workspace allocated inside); pilot %s; levels added from L = 3 "
                    "while E[Y_L] / (2^alpha - 1) > eps / sqrt 2, E[Y_L] from the weak-error fit over levels 1..L "
                    "(mlmc_bias_test_fit; the level-L sample mean alone rests on 4 samples at L = 5, its estimate "
-                   "is given beside); rmse_bound = sqrt(variance + bias_est^2)" % (list(ADAPTIVE_PILOT),))
+                   "is given beside); if the test still fails at L = 5 the variance gets the rest of the budget, "
+                   "eps^2 - bias^2 (Eq. MSE); rmse_bound = sqrt(variance + bias_est^2), rmse_ok = rmse_bound <= eps"
+                   % (list(ADAPTIVE_PILOT),))
     return out
 
 
@@ -905,7 +915,7 @@ def main():
         # precision, with the oracle on sampled scenarios) and the discrete adjoint of 1024 KL samples
         wl = {}
         if within_budget(t_start, wl, "uneven_fp64"):
-            wl["uneven_fp64"] = uneven_workload(henry, torch, dev, False)[0]
+            wl["uneven_fp64"] = uneven_workload(henry, torch, dev, False, tuning=tuning)[0]
         if within_budget(t_start, wl, "kl_mixed"):
             wl["kl_mixed"], _, kl_q = uneven_workload(henry, torch, dev, True)
             wl["kl_mixed"]["qoi_mixed_vs_oracle"] = kl_against_oracle(kl_q)

@@ -184,6 +184,9 @@ typedef struct {
                                     iterations 0, k, 2k, ... of a time step and reuses them in between (chord
                                     Newton; k = 1, the default: every iteration).  The FP64 residual test
                                     decides convergence either way, so the converged states agree to it */
+  int32_t level_priority; /* henry_batch_solve_mixed: 1 (default) runs finer levels on higher-priority
+                             streams (their solves are the pass's critical path); 0: equal priorities.
+                             Fixed when a level's stream is first created.  Same values either way */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */

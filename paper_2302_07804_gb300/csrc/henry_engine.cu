@@ -2079,6 +2079,7 @@ void henry_default_config(henry_config* c) {
   c->tile_assembly = 1;
   c->newton_residual_first = 2;
   c->newton_jacobian_every = 1;
+  c->level_priority = 1;
   c->mg_tail_cells = 128;
   c->mg_tail_batch_cells = 1 << 20;
   c->scheme = HENRY_SCHEME_CELL;
@@ -2227,7 +2228,14 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
   // Stages 2 and 3, one setting at a time from the best so far: the fused
   // multigrid tail (off, from 16 x 8, from 32 x 16 cells) and the
   // residual-first Newton test (never, from iteration 1, from 2).
-  if (!rc && best >= 0 && !cands[best].fused_small_grids) {
+  // (not when the fused small-grid solver won: it has its own in-kernel V-cycle and Newton loop)
+  bool fused_won = false;
+  if (best >= 0) {
+    henry_config cb = c;
+    cb.fused_small_grids = cands[best].fused_small_grids;
+    fused_won = c.precision == HENRY_MIXED ? fused_eligible<float>(cb, level, &CL) : fused_eligible<double>(cb, level, &CL);
+  }
+  if (!rc && best >= 0 && !fused_won) {
     const int tails[3] = {0, 128, 512};
     for (int v : tails) {
       if (v == cands[best].mg_tail_cells || rc) continue;
@@ -2445,8 +2453,16 @@ int henry_batch_solve_mixed(henry_handle* h, const int32_t* levels_host, int n, 
       const int rc = henry_create(&h->cfg, &k);
       if (rc) return rc;
       h->kids[l] = k;
+      // level_priority: finer levels (longer solves: the critical path of a
+      // pass) get higher stream priorities, so their kernels are scheduled
+      // first when the levels compete for SMs
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      const int prio = h->cfg.level_priority
+                           ? std::max(greatest, least - (l * (least - greatest)) / std::max(1, h->cfg.max_level))
+                           : least;
       cudaStream_t ls = nullptr;
-      CK(cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithPriority(&ls, cudaStreamNonBlocking, prio));
       h->kid_streams[l] = ls;
     }
     henry_handle* k = h->kids[l];

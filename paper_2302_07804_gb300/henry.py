@@ -48,7 +48,8 @@ class HenryConfig(ctypes.Structure):
                 ("adj_maxit", ctypes.c_int32), ("cuda_graphs", ctypes.c_int32), ("qoi_set", ctypes.c_int32),
                 ("tile_assembly", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
                 ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32),
-                ("scheme", ctypes.c_int32), ("newton_jacobian_every", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("newton_jacobian_every", ctypes.c_int32),
+                ("level_priority", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
