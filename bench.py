@@ -539,6 +539,40 @@ def kl_against_oracle(q32):
             "oracle": "FP64 Newton with sparse direct solves, stored in tests/golden/kl_workload_oracle_qoi.txt"}
 
 
+# The paper's own discretisation (vertex-centred FV): per level a batch of
+# scenarios of the configuration's physics; vertex-steps/s beside the
+# paper's ug4 runs (Table tab:adaptiveTS_times: one scenario on 32 cores of
+# a Shaheen II node, DOFs 2 (nx+1)(ny+1), its own physics variant and time
+# steps), as context only.
+VC_COUNTS = ((0, 4096), (1, 512), (2, 64), (3, 8))
+PAPER_VERTEX_STEPS_PER_S = {0: 9.2e4, 1: 1.97e5, 2: 3.2e5, 3: 3.67e5}
+
+
+def vc_workload(henry, torch, dev, precision):
+    from paper_2302_07804_gb300 import inputs
+    s = henry.Solver(scheme=henry.HENRY_SCHEME_VERTEX, precision=precision)
+    rows = []
+    for level, m in VC_COUNTS:
+        xi = henry.sample_xi(inputs.SEED, level, 3 * 10 ** 7, m, device=dev)
+        s.level_batch_solve(level, xi[:min(m, 8)].contiguous())  # warm-up: workspace, graphs
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, st, stats = s.level_batch_solve(level, xi, allow_failures=True)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        ny, nx = s.grid(level)
+        steps = s.cfg.steps0 << level
+        vs = m * (nx + 1) * (ny + 1) * steps
+        rows.append({"level": level, "samples": m, "seconds": sec, "vertex_steps_per_s": vs / sec,
+                     "cell_steps_per_s": stats["cell_steps"] / sec, "failed_samples": int(stats["failed_samples"]),
+                     "paper_ug4_vertex_steps_per_s_per_scenario": PAPER_VERTEX_STEPS_PER_S[level]})
+    s.close()
+    return {"workload": "vertex-centred scheme, one batch per level", "precision": "fp64" if precision == 0 else "mixed",
+            "levels": rows, "note": "the paper's column is one scenario of its own variant on 32 CPU cores (context)"}
+
+
 def run_uneven(args):
     """--workload uneven | kl-mixed: print the uneven workload's line."""
     import torch
@@ -921,6 +955,8 @@ def main():
             wl["kl_mixed"]["qoi_mixed_vs_oracle"] = kl_against_oracle(kl_q)
         if within_budget(t_start, wl, "adjoint"):
             wl["adjoint"] = adjoint_workload(henry, torch, dev, 1024, forward_subset=128)
+        if within_budget(t_start, wl, "vertex_centred"):
+            wl["vertex_centred"] = vc_workload(henry, torch, dev, henry.HENRY_FP64)
         line["workloads"] = wl
         # ---- CPU oracle on the host cores (bounded sample, the reference arm's per-step sample)
         try:

@@ -180,7 +180,7 @@ typedef struct {
                                   (default 2^20; 0: no limit): large batches of small grids run those levels
                                   as separate, large launches */
   int32_t scheme; /* HENRY_SCHEME_CELL (default) or HENRY_SCHEME_VERTEX */
-  int32_t newton_jacobian_every; /* cell-centred scheme: Newton assembles the Jacobian and the coarse operators at
+  int32_t newton_jacobian_every; /* Newton assembles the Jacobian and the coarse operators at
                                     iterations 0, k, 2k, ... of a time step and reuses them in between (chord
                                     Newton; k = 1, the default: every iteration).  The FP64 residual test
                                     decides convergence either way, so the converged states agree to it */
@@ -214,7 +214,7 @@ void henry_paper_config(henry_config* cfg);
  * fused one-CTA-per-sample solver; then, one at a time from the best so far,
  * the fused multigrid tail (mg_tail_cells in {0, 128, 512}) and the
  * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}) and
- * chord Newton (newton_jacobian_every in {1, 2, 3}, cell-centred scheme).
+ * chord Newton (newton_jacobian_every in {1, 2, 3}).
  * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
  * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
  * off where eligible), then the two later stages - on n_trial samples

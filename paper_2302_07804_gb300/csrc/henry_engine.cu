@@ -1040,7 +1040,7 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
     assemble_fine(!res_first);
     launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
-      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+      k_newton_res_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
                                                        G.newton_active, G.lin_active, G.newton_it, G.status,
                                                        G.counter, G.totals);
     });
@@ -1076,9 +1076,9 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
       double* pdc = G.part + P_DC * (int64_t)B * G.nct;
       k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
-      k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
+      k_newton_theta<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
       k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
-      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
+      k_newton_dx_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
     });
     CKL();
   }
@@ -1425,17 +1425,26 @@ int vc_linear_solve(henry_handle* H, VcGroup<T>& G, int B, cudaStream_t st, doub
   return HENRY_OK;
 }
 
-// Fine residual and Jacobian (scaled by inv_s) of the samples with
-// newton_active set, with the per-CTA max |F| into P_MAX.
+// Fine residual and Jacobian (scaled by inv_s; jac = false: the residual
+// alone) of the samples with newton_active set, with the per-CTA max |F|
+// into P_MAX.
 template <typename T>
-int vc_assemble_fine(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_s, cudaStream_t st) {
+int vc_assemble_fine(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_s, cudaStream_t st,
+                     bool jac = true) {
   typedef typename VT<T>::b4 B4;
   auto& L = G.lv[0];
-  launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * L.NV * (48.0 + 10.0 * sizeof(B4)), [&] {
-    k_vc_assemble_st<T, true><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
-        vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
-        (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
-  });
+  if (jac)
+    launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * L.NV * (48.0 + 10.0 * sizeof(B4)), [&] {
+      k_vc_assemble_st<T, true><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
+          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
+          (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
+    });
+  else
+    launch(H, st, HENRY_K_RESIDUAL, (double)H->nact * L.NV * 48.0, [&] {
+      k_vc_assemble_st<T, true, false><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
+          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
+          nullptr, G.part + P_MAX * (int64_t)B * G.nct);
+    });
   CKL();
   return HENRY_OK;
 }
@@ -1464,12 +1473,17 @@ int vc_implicit_step(henry_handle* H, VcGroup<T>& G, int B, int step, cudaStream
   CKL();
   int rc = vc_inject<T>(H, G, B, true, G.newton_active, st);
   if (rc) return rc;
+  // residual-first test and chord Newton as in implicit_step
+  const int jac_every = std::max(1, c.newton_jacobian_every);
+  int last_jac = -1;
   for (int it = 0; it <= c.newton_maxit; ++it) {
+    const bool jac_now = last_jac < 0 || it - last_jac >= jac_every;
+    const bool res_first = !jac_now || (c.newton_residual_first >= 0 && it >= c.newton_residual_first);
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
-    rc = vc_assemble_fine<T>(H, G, B, lg.tau, inv_s, st);
+    rc = vc_assemble_fine<T>(H, G, B, lg.tau, inv_s, st, !res_first);
     if (rc) return rc;
     launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
-      k_newton_res_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+      k_newton_res_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
                                                        G.newton_active, G.lin_active, G.newton_it, G.status,
                                                        G.counter, G.totals);
     });
@@ -1479,17 +1493,21 @@ int vc_implicit_step(henry_handle* H, VcGroup<T>& G, int B, int step, cudaStream
     if (rc) return rc;
     if (n_act == 0) break;
     H->nact = n_act;
-    rc = vc_inject<T>(H, G, B, false, G.lin_active, st);
-    if (!rc) rc = vc_coarse_ops<T>(H, G, B, lg.tau, inv_s, st);
+    if (jac_now) {
+      if (res_first) rc = vc_assemble_fine<T>(H, G, B, lg.tau, inv_s, st);
+      if (!rc) rc = vc_inject<T>(H, G, B, false, G.lin_active, st);
+      if (!rc) rc = vc_coarse_ops<T>(H, G, B, lg.tau, inv_s, st);
+      last_jac = it;
+    }
     if (!rc) rc = vc_linear_solve<T>(H, G, B, st);
     if (rc) return rc;
     H->nact = n_act;
     launch(H, st, HENRY_K_NEWTON, (double)n_act * N * (32.0 + sizeof(V2)), [&] {
       double* pdc = G.part + P_DC * (int64_t)B * G.nct;
       k_newton_step_max<T><<<nblk(n0), TPB, 0, st>>>(B, N, inv_pref, G.dx, pmax, pdc, G.newton_active);
-      k_newton_theta<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
+      k_newton_theta<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_dc_limit, pdc, G.newton_active, G.theta);
       k_newton_update<T><<<nblk(n0), TPB, 0, st>>>(B, N, L.x, G.dx, G.theta, G.newton_active);
-      k_newton_dx_check<<<nblk(B, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
+      k_newton_dx_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_dxtol, pmax, G.newton_active, G.status);
     });
     CKL();
   }
@@ -2253,7 +2271,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       cands.push_back(t);
       trial((int)cands.size() - 1);
     }
-    if (c.scheme == HENRY_SCHEME_CELL) {  // chord Newton: the Jacobian every 1, 2 or 3 iterations
+    {  // chord Newton: the Jacobian every 1, 2 or 3 iterations
       const int b3 = best;
       for (int v : {1, 2, 3}) {
         if (v == cands[b3].newton_jacobian_every || rc) continue;

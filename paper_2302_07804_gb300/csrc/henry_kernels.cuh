@@ -189,10 +189,13 @@ __global__ void k_finalize(int B, int nct, const double* __restrict__ part, int 
     if (lane == 0) fin[(int64_t)s * NPART + slot] = v;
   }
 }
-__device__ __forceinline__ double sample_max(const double* __restrict__ p, int nct) {
+// Max of a sample's nct non-negative partial maxima, by one warp (lanes
+// stride over the partials; a max does not depend on the order), returned
+// to every lane.  Wide grids have thousands of partials per sample.
+__device__ __forceinline__ double warp_sample_max(const double* __restrict__ p, int nct, int lane) {
   double v = 0.0;
-  for (int i = 0; i < nct; ++i) v = fmax(v, p[i]);
-  return v;
+  for (int i = lane; i < nct; i += 32) v = fmax(v, p[i]);
+  return warp_max(v);
 }
 
 // 2x2 block helpers as explicit fused multiply-add chains: two FMAs per row
@@ -1267,11 +1270,13 @@ __global__ void k_newton_res_check(int B, int nct, double atol, int maxit, const
                                    int* __restrict__ newton_active, int* __restrict__ lin_active,
                                    int* __restrict__ newton_it, int* __restrict__ status,
                                    int* __restrict__ n_active, unsigned long long* __restrict__ it_total) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per sample
+  const int s = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (s >= B) return;
   int act = newton_active[s];
+  const double rm = act ? warp_sample_max(rmax_part + (int64_t)s * nct, nct, lane) : 0.0;
+  if (lane != 0) return;
   if (act) {
-    const double rm = sample_max(rmax_part + (int64_t)s * nct, nct);
     if (!(rm <= 1.0e300)) {
       status[s] = 3;
       act = 0;
@@ -1320,14 +1325,15 @@ __global__ void __launch_bounds__(TPB) k_newton_step_max(int B, int N, double in
 // mass fraction by more than dc_limit is shortened; dc_limit <= 0: theta = 1).
 __global__ void k_newton_theta(int B, int nct, double dc_limit, const double* __restrict__ dc_part,
                                const int* __restrict__ newton_active, double* __restrict__ theta) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per sample
+  const int s = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (s >= B || !newton_active[s]) return;
   double th = 1.0;
   if (dc_limit > 0.0) {
-    const double mc = sample_max(dc_part + (int64_t)s * nct, nct);
+    const double mc = warp_sample_max(dc_part + (int64_t)s * nct, nct, lane);
     if (mc > dc_limit) th = dc_limit / mc;
   }
-  theta[s] = th;
+  if (lane == 0) theta[s] = th;
 }
 
 // a9: x += theta dx.
@@ -1349,9 +1355,11 @@ __global__ void __launch_bounds__(TPB) k_newton_update(int B, int N, double2* __
 
 __global__ void k_newton_dx_check(int B, int nct, double dxtol, const double* __restrict__ dmax_part,
                                   int* __restrict__ newton_active, int* __restrict__ status) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per sample
+  const int s = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (s >= B || !newton_active[s]) return;
-  const double dm = sample_max(dmax_part + (int64_t)s * nct, nct);
+  const double dm = warp_sample_max(dmax_part + (int64_t)s * nct, nct, lane);
+  if (lane != 0) return;
   if (!(dm <= 1.0e300)) {
     status[s] = 3;
     newton_active[s] = 0;

@@ -58,7 +58,9 @@ struct VcCoef {
 // corner b, and their derivatives with respect to the element's unknowns
 // (slot k: p of corner k, slot 4 + k: c of corner k), given the corners'
 // p and c; ih = 1 / h.  (Divisions are few: on GPUs with few FP64 units a
-// division is a long sequence of FP64 instructions.)
+// division is a long sequence of FP64 instructions.)  JAC = false: F and G
+// alone (the same arithmetic for the values; dF, dG untouched).
+template <bool JAC = true>
 __host__ __device__ inline void vc_face(const VcParams& P, const VcCoef& C, const double* p, const double* c, int f,
                                         double ih, double& F, double* dF, double& G, double* dG) {
   const int a = (f == 1) ? 2 : ((f == 3) ? 1 : 0);
@@ -88,6 +90,17 @@ __host__ __device__ inline void vc_face(const VcParams& P, const VcCoef& C, cons
   grav *= P.g;
   const double qn = -C.kmu * (dp + grav);
   F = rip * qn * hh;
+  if (!JAC) {
+    const double Dc = rip * C.PD;
+    const bool pos = F >= 0.0;
+    const double sg = pos ? 1.0 : -1.0, A = pos ? F : -F;
+    double s = 0.0;
+    if (Dc < 2.0 * A) s = 1.0 - Dc * (0.5 / A);
+    const double cab = c[a] - c[b];
+    const double cf = 0.5 * (c[a] + c[b]) + 0.5 * sg * s * cab;
+    G = F * cf - Dc * dc * hh;
+    return;
+  }
   double dDc[8], ddc[8];
   for (int k = 0; k < 4; ++k) {
     dF[k] = rip * (-C.kmu * gw[k]) * hh;                                    // d/dp_k
@@ -131,7 +144,9 @@ struct VcNaturalIndex {  // [ny + 1][nx + 1] row-major
 // (p, c) of vertex (j + dj, i + di) (36 doubles; zero for neighbours outside
 // the grid).  x, xo: the sample's states, pairs (p, c) at idx(j, i)
 // (vc_vertex: natural order [ny + 1][nx + 1][2]).
-template <typename IDX>
+// JAC = false: the residual alone (J is ignored; the residual's arithmetic is
+// the same as with JAC = true).
+template <typename IDX, bool JAC = true>
 __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C, const double* x, const double* xo,
                                              int j, int i, double* R, double* J, IDX idx) {
   double Rm = 0.0, Rs = 0.0;
@@ -164,10 +179,11 @@ __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C,
       const int b = (f == 0) ? 1 : ((f == 2) ? 2 : 3);
       if (a != kv && b != kv) continue;
       double F, G, dF[8], dG[8];
-      vc_face(P, C, p, c, f, ih, F, dF, G, dG);
+      vc_face<JAC>(P, C, p, c, f, ih, F, dF, G, dG);
       const double sgn = (a == kv) ? 1.0 : -1.0;  // out of this vertex's volume
       Rm += sgn * F;
       Rs += sgn * G;
+      if (!JAC) continue;
       for (int k = 0; k < 4; ++k) {
         const int q = (ey + (k >> 1) - j + 1) * 3 + (ex + (k & 1) - i + 1);
         Jm[q][0] += sgn * dF[k];
@@ -199,7 +215,7 @@ __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C,
 
   R[0] = Rm;
   R[1] = Rs;
-  if (J) {
+  if (JAC && J) {
     for (int q = 0; q < 9; ++q) {
       J[q * 4 + 0] = Jm[q][0];
       J[q * 4 + 1] = Jm[q][1];

@@ -65,8 +65,9 @@ __host__ __device__ __forceinline__ int vc_colour_cols(int nxv, int ci) { return
 // 1 / (rho0 h^2 / tau)), at the storage-ordered states x, xo ([B][stride]).
 // FINE: also F (double2, zero on the padding) and the per-CTA max |F| into
 // rmax_part[s][stride / TPB] (stride a multiple of TPB); blocks of padding
-// entries are zero.  Only samples with active[s] set are touched.
-template <typename T, bool FINE>
+// entries are zero.  Only samples with active[s] set are touched.  JAC =
+// false: the residual alone (bit-identical to the JAC = true residual).
+template <typename T, bool FINE, bool JAC = true>
 __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* __restrict__ coef, int B, int stride,
                                                         int64_t plane, double inv_s, const double2* __restrict__ x,
                                                         const double2* __restrict__ xo, const int* __restrict__ active,
@@ -92,8 +93,9 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
     const Coef cf = coef[s];
     const VcCoef c{cf.phi, cf.kmu, cf.PD, cf.qin};
     const int64_t base = (int64_t)s * stride;
-    vc_vertex_at(P, c, reinterpret_cast<const double*>(x + base), reinterpret_cast<const double*>(xo + base), j, i,
-                 R, J ? Jv : nullptr, VcStorageIndex{nxv});
+    vc_vertex_at<VcStorageIndex, JAC>(P, c, reinterpret_cast<const double*>(x + base),
+                                       reinterpret_cast<const double*>(xo + base), j, i, R, J ? Jv : nullptr,
+                                       VcStorageIndex{nxv});
   }
   if (FINE) {
     const double fm = R[0] * inv_s, fs = R[1] * inv_s;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
     const double bm = block_max_nonneg(loc, sh);
     if (threadIdx.x == 0) rmax_part[(int64_t)s * (stride / TPB) + st / TPB] = bm;
   }
-  if (J) {
+  if (JAC && J) {
 #pragma unroll
     for (int q = 0; q < 9; ++q)
       J[q * plane + e] = mkblk<B4>((T)(Jv[4 * q] * inv_s), (T)(Jv[4 * q + 1] * inv_s), (T)(Jv[4 * q + 2] * inv_s),

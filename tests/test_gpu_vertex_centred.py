@@ -250,3 +250,23 @@ def test_vc_scheme_rejects_unsupported_settings(hl):
     with pytest.raises(hl.HenryError):
         s.adjoint(0, xi, w)
     s.close()
+
+
+def test_vc_residual_first_and_chord_newton(hl):
+    """The vertex-centred Newton loop with the residual evaluated alone first
+    (bit-identical iterates) and with chord Newton (the Jacobian every 2nd
+    iteration; the same discrete solution, against the oracle at 1e-10)."""
+    prm = vc.Params()
+    xi = hl.sample_xi(inputs.SEED, 0, 7300, 3)
+    out = []
+    for rf in (-1, 0):
+        s = _vc_solver(hl, newton_residual_first=rf)
+        q, _, st, stats = s.level_batch_solve(0, xi)
+        out.append((q, st, stats["newton_iters"], stats["linear_iters"]))
+        s.close()
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1]) and out[0][2:] == out[1][2:]
+    s = _vc_solver(hl, newton_jacobian_every=2, lin_rtol=1e-2)
+    q, _, st, _ = s.level_batch_solve(0, xi)
+    assert int(st.abs().sum()) == 0
+    _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
+    s.close()
