@@ -187,6 +187,13 @@ typedef struct {
   int32_t level_priority; /* henry_batch_solve_mixed: 1 (default) runs finer levels on higher-priority
                              streams (their solves are the pass's critical path); 0: equal priorities.
                              Fixed when a level's stream is first created.  Same values either way */
+  int32_t assembly_tile_w; /* face-once assembly tiles: 0 (default) whole rows up to 256 cells wide, else
+                              128 x 2; 32, 64, 128 or 256: tiles of that many cells x 256 / width rows on
+                              every grid whose width and height they divide (the default elsewhere).
+                              Identical values for every tile shape */
+  int32_t mg_threads; /* threads per CTA of the multigrid smoother, restriction and prolongation kernels of
+                         the cell-centred scheme: 64, 128, 256 or 512 (0, the default: 256).  Identical
+                         values for every size */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -212,12 +219,14 @@ void henry_paper_config(henry_config* cfg);
  * converges, never where (the FP64 Newton test decides): the Krylov tolerance,
  * the V-cycle's smoothing counts and, where the level's grid allows it, the
  * fused one-CTA-per-sample solver; then, one at a time from the best so far,
- * the fused multigrid tail (mg_tail_cells in {0, 128, 512}) and the
- * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}) and
- * chord Newton (newton_jacobian_every in {1, 2, 3}).
+ * the fused multigrid tail (mg_tail_cells in {0, 32, 128, 512}), the
+ * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}), chord
+ * Newton (newton_jacobian_every in {1, 2, 3}), the assembly tile
+ * (assembly_tile_w in {0, 32, 64, 128, 256} where it divides the grid) and the
+ * multigrid kernels' CTA size (mg_threads in {64, 128, 256, 512}).
  * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
  * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
- * off where eligible), then the two later stages - on n_trial samples
+ * off where eligible), then the later stages - on n_trial samples
  * xi_dev[n_trial][n_xi] of `level` (with their coarse partners if
  * with_coarse), after one untimed warm-up, with CUDA events on `stream`, and
  * keeps the fastest candidate that solves every sample for that level of
@@ -232,6 +241,7 @@ typedef struct {
   int32_t nu1, nu2, fused_small_grids;
   double cell_steps_per_s; /* measured on the trial batch (0 for the configuration's own settings) */
   int32_t mg_tail_cells, newton_residual_first, newton_jacobian_every; /* as in henry_config */
+  int32_t assembly_tile_w, mg_threads;                                 /* as in henry_config */
 } henry_tuning;
 int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
                    henry_tuning* best_out, void* stream);

@@ -111,10 +111,11 @@ struct Group {
   LinScal* sc;
   T* Ainv;
   void* Jp = nullptr;  // fine-level fallback preconditioner operator (field models only)
-  // Instantiated CUDA graphs of one BiCGStab iteration's body, by (batch
-  // size, preconditioner operator); they hold this workspace's pointers and
-  // are dropped with it.
-  std::map<std::tuple<int, const void*, int, int>, cudaGraphExec_t> gexec;  // (B, preconditioner, nu1, nu2)
+  // Instantiated CUDA graphs of one BiCGStab iteration's body, by batch size,
+  // preconditioner operator and every setting that changes the body's
+  // launches (nu1, nu2, mg_tail_cells, mg_threads); they hold this
+  // workspace's pointers and are dropped with it.
+  std::map<std::tuple<int, const void*, int, int, int, int>, cudaGraphExec_t> gexec;
   bool graphs = true;  // false: never capture (the allocation-free entry point)
   void drop_graphs() {
     for (auto& kv : gexec) cudaGraphExecDestroy(kv.second);
@@ -390,17 +391,42 @@ void prof_drain(henry_handle* H) {
   P.pend.clear();
 }
 
-// The assembly kernel for a grid nx cells wide: the face-once tile form,
-// whole rows per tile where they fit (nx <= TPB), else 128 x 2 blocks; the
-// per-cell form with tile_assembly = 0 (same arguments, same results up to
-// rounding).
+// The assembly kernel for an nx x ny grid: the face-once tile form, in
+// assembly_tile_w x (TPB / assembly_tile_w) tiles where that tile divides the
+// grid, else whole rows per tile where they fit (nx <= TPB), else 128 x 2
+// tiles; the per-cell form with tile_assembly = 0.  Same arguments; the tile
+// forms give identical values (each face's arithmetic is the same wherever it
+// is evaluated), the per-cell form the same up to rounding.
 // JAC = false: the fine residual alone (same values as with JAC = true).
 template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
-auto assemble_kernel(const henry_config& c, int nx) -> decltype(&k_assemble<T, FINE, FIELDS, DROP, JAC>) {
+auto assemble_kernel(const henry_config& c, int nx, int ny) -> decltype(&k_assemble<T, FINE, FIELDS, DROP, JAC>) {
   if (!c.tile_assembly) return &k_assemble<T, FINE, FIELDS, DROP, JAC>;
+  const int tw = c.assembly_tile_w;
+  if (tw > 0 && nx % tw == 0 && ny % (TPB / tw) == 0) {  // N % TPB == 0 follows
+    switch (tw) {
+      case 32: return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC, 32>;
+      case 64: return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC, 64>;
+      case 128: return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC, 128>;
+      case 256: return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC, 256>;
+      default: break;
+    }
+  }
   if (nx <= TPB) return &k_assemble_tile<T, FINE, FIELDS, DROP, JAC>;
-  if (nx % TILE_W == 0) return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC>;  // N % TPB == 0 follows
+  if (nx % TILE_W_DEFAULT == 0 && ny % (TPB / TILE_W_DEFAULT) == 0)
+    return &k_assemble_tile2d<T, FINE, FIELDS, DROP, JAC, TILE_W_DEFAULT>;
   return &k_assemble<T, FINE, FIELDS, DROP, JAC>;
+}
+
+// Runs f(std::integral_constant<int, NT>{}) for the multigrid kernels' CTA
+// size nt: 64, 128, 256 or 512 threads (anything else: TPB).
+template <typename F>
+void with_mg_threads(int nt, F&& f) {
+  switch (nt) {
+    case 64: f(std::integral_constant<int, 64>()); break;
+    case 128: f(std::integral_constant<int, 128>()); break;
+    case 512: f(std::integral_constant<int, 512>()); break;
+    default: f(std::integral_constant<int, TPB>()); break;
+  }
 }
 bool has_fields(const henry_config& c) { return c.coef_model != HENRY_MODEL_UNIFORM3; }
 int qoi_count(const henry_config& c) {
@@ -657,11 +683,11 @@ int build_coarse_ops(henry_handle* H, Group<T>& G, int B, double inv_tau, double
     } else {
       launch(H, st, HENRY_K_COARSE_OPS, na * L.N * (32.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          assemble_kernel<T, false, true, DROP>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+          assemble_kernel<T, false, true, DROP>(H->cfg, L.nx, L.ny)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h, L.h * L.h * inv_tau * inv_s, inv_s, L.x, L.xo, G.lin_active,
               nullptr, (B4*)L.J, L.plane, nullptr, L.cc, L.fc);
         else
-          assemble_kernel<T, false>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
+          assemble_kernel<T, false>(H->cfg, L.nx, L.ny)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, L.h, 1.0 / L.h,
                                                                         L.h * L.h * inv_tau * inv_s, inv_s, L.x,
                                                                         L.xo, G.lin_active, nullptr, (B4*)L.J,
                                                                         L.plane, nullptr, nullptr, nullptr);
@@ -723,35 +749,53 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
   CtaLayout TL;
   const int kt = tail_level<T>(H->cfg, G, B, &TL);
   const int kend = kt > 0 ? kt : G.K;  // levels 0 .. kend - 1 run as separate kernels
+  const int mnt = H->cfg.mg_threads;
   for (int k = 0; k < kend; ++k) {
     Level& L = G.lv[k];
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
     const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
-    const unsigned gh = nblk((int64_t)B * L.N / 2);
+    const int64_t hn = (int64_t)B * L.N / 2;  // threads per half-sweep
     const double hc = na * L.N / 2;  // swept cells per half-sweep
     const int sm = k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE;
     Level& Lc = G.lv[k + 1];
+    auto sweep = [&](int col, auto mode) {
+      constexpr int MODE = decltype(mode)::value;
+      with_mg_threads(mnt, [&](auto nt) {
+        constexpr int NT = decltype(nt)::value;
+        k_sweep<T, MODE, NT><<<nblk(hn, NT), NT, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act);
+      });
+    };
     if (nu1 > 0) {
       launch(H, st, sm, hc * (b4 + 2 * v2), na * sweep_flops(L.nx, L.ny, 0),
-             [&] { k_sweep<T, 0><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, nullptr, act); });
+             [&] { sweep(0, std::integral_constant<int, 0>()); });
       launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
-             [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
+             [&] { sweep(1, std::integral_constant<int, 1>()); });
       for (int i = 1; i < nu1; ++i) {
         for (int col = 0; col < 2; ++col)
           launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
-                 [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
+                 [&] { sweep(col, std::integral_constant<int, 1>()); });
       }
       launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * (10 * b4 + 7 * v2), na * restrict_flops(L.nx, L.ny), [&] {
-        k_residual_restrict<T, 0><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
-                                                                          (V2*)Lc.mgb, act);
+        with_mg_threads(mnt, [&](auto nt) {
+          constexpr int NT = decltype(nt)::value;
+          k_residual_restrict<T, 0, NT><<<nblk((int64_t)B * Lc.N, NT), NT, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b,
+                                                                                   x, (V2*)Lc.mgb, act);
+        });
       });
     } else {
-      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.N * v2,
-             [&] { k_zero<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>((int64_t)B * L.N, x); });
+      launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.N * v2, [&] {
+        with_mg_threads(mnt, [&](auto nt) {
+          constexpr int NT = decltype(nt)::value;
+          k_zero<T, NT><<<nblk((int64_t)B * L.N, NT), NT, 0, st>>>((int64_t)B * L.N, x);
+        });
+      });
       launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * Lc.N * 5 * v2, [&] {
-        k_residual_restrict<T, 1><<<nblk((int64_t)B * Lc.N), TPB, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b, x,
-                                                                          (V2*)Lc.mgb, act);
+        with_mg_threads(mnt, [&](auto nt) {
+          constexpr int NT = decltype(nt)::value;
+          k_residual_restrict<T, 1, NT><<<nblk((int64_t)B * Lc.N, NT), NT, 0, st>>>(B, Lc.nx, Lc.ny, J, L.plane, b,
+                                                                                   x, (V2*)Lc.mgb, act);
+        });
       });
     }
     CKL();
@@ -792,22 +836,33 @@ int vcycle(henry_handle* H, Group<T>& G, int B, const typename VT<T>::v2* b0, ty
     const V2* b = k == 0 ? b0 : (const V2*)L.mgb;
     V2* x = k == 0 ? x0 : (V2*)L.mgx;
     const B4* J = (const B4*)((k == 0 && J0) ? J0 : L.J);
-    const unsigned gh = nblk((int64_t)B * L.N / 2);
+    const int64_t hn = (int64_t)B * L.N / 2;
     const double hc = na * L.N / 2;
     const int sm = k == 0 ? HENRY_K_SMOOTH : HENRY_K_SMOOTH_COARSE;
+    auto sweep = [&](int col, auto mode) {
+      constexpr int MODE = decltype(mode)::value;
+      with_mg_threads(mnt, [&](auto nt) {
+        constexpr int NT = decltype(nt)::value;
+        k_sweep<T, MODE, NT><<<nblk(hn, NT), NT, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x,
+                                                          MODE == 2 ? (const V2*)Lc.mgx : nullptr, act);
+      });
+    };
     if (nu2 > 0) {
       launch(H, st, sm, hc * (5 * b4 + 3.5 * v2), na * (sweep_flops(L.nx, L.ny, 1) + L.N),
-             [&] { k_sweep<T, 2><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 0, J, L.plane, b, x, (const V2*)Lc.mgx, act); });
+             [&] { sweep(0, std::integral_constant<int, 2>()); });
       launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
-             [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, 1, J, L.plane, b, x, nullptr, act); });
+             [&] { sweep(1, std::integral_constant<int, 1>()); });
       for (int i = 1; i < nu2; ++i) {
         for (int col = 0; col < 2; ++col)
           launch(H, st, sm, hc * (5 * b4 + 3 * v2), na * sweep_flops(L.nx, L.ny, 1),
-                 [&] { k_sweep<T, 1><<<gh, TPB, 0, st>>>(B, L.nx, L.ny, col, J, L.plane, b, x, nullptr, act); });
+                 [&] { sweep(col, std::integral_constant<int, 1>()); });
       }
     } else {
       launch(H, st, HENRY_K_RESIDUAL_RESTRICT, na * L.N * 2.25 * v2, [&] {
-        k_prolong_add<T><<<nblk((int64_t)B * L.N), TPB, 0, st>>>(B, L.nx, L.ny, x, (const V2*)Lc.mgx, act);
+        with_mg_threads(mnt, [&](auto nt) {
+          constexpr int NT = decltype(nt)::value;
+          k_prolong_add<T, NT><<<nblk((int64_t)B * L.N, NT), NT, 0, st>>>(B, L.nx, L.ny, x, (const V2*)Lc.mgx, act);
+        });
       });
     }
     CKL();
@@ -896,7 +951,7 @@ int linear_solve(henry_handle* H, Group<T>& G, int B, cudaStream_t st, const voi
   // launched on `st`.  Off while the kernel timer runs.
   const bool use_graph = H->cfg.cuda_graphs && G.graphs && !H->prof.on;
   auto run_graph = [&]() -> int {
-    const auto key = std::make_tuple(B, Jpre0, H->cfg.nu1, H->cfg.nu2);
+    const auto key = std::make_tuple(B, Jpre0, H->cfg.nu1, H->cfg.nu2, H->cfg.mg_tail_cells, H->cfg.mg_threads);
     auto f = G.gexec.find(key);
     if (f == G.gexec.end()) {
       if (!H->cap_stream) CK(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
@@ -957,7 +1012,7 @@ int retry_linear_solve(henry_handle* H, Group<T>& G, int B, double inv_tau, doub
   if (n_retry == 0) return HENRY_OK;
   H->nact = n_retry;
   double* pscratch = G.part + P_MAX * (int64_t)B * G.nct;
-  assemble_kernel<T, true, true, true>(H->cfg, L.nx)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
+  assemble_kernel<T, true, true, true>(H->cfg, L.nx, L.ny)<<<nblk((int64_t)B * L.N), TPB, 0, st>>>(
       phys_of(c), G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
       G.lin_active, nullptr, (B4*)G.Jp, L.plane, pscratch, L.cc, L.fc);
   CKL();
@@ -1002,22 +1057,22 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
     if (jac)
       launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * N * (48.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          assemble_kernel<T, true, true>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+          assemble_kernel<T, true, true>(c, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, (B4*)L.J,
               L.plane, pmax, L.cc, L.fc);
         else
-          assemble_kernel<T, true>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
+          assemble_kernel<T, true>(c, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h,
                                                                       vt, inv_s, L.x, L.xo, G.newton_active, G.F,
                                                                       (B4*)L.J, L.plane, pmax, nullptr, nullptr);
       });
     else
       launch(H, st, HENRY_K_RESIDUAL, (double)H->nact * N * 48.0, [&] {
         if (L.cc)
-          assemble_kernel<T, true, true, false, false>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+          assemble_kernel<T, true, true, false, false>(c, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, nullptr,
               L.plane, pmax, L.cc, L.fc);
         else
-          assemble_kernel<T, true, false, false, false>(c, L.nx)<<<nblk(n0), TPB, 0, st>>>(
+          assemble_kernel<T, true, false, false, false>(c, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(
               ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s, L.x, L.xo, G.newton_active, G.F, nullptr,
               L.plane, pmax, nullptr, nullptr);
       });
@@ -1656,6 +1711,8 @@ struct TuningScope {
     h->cfg.mg_tail_cells = f->second.mg_tail_cells;
     h->cfg.newton_residual_first = f->second.newton_residual_first;
     h->cfg.newton_jacobian_every = std::max(1, f->second.newton_jacobian_every);
+    h->cfg.assembly_tile_w = f->second.assembly_tile_w;
+    h->cfg.mg_threads = f->second.mg_threads;
   }
   ~TuningScope() { H->cfg = saved; }
 };
@@ -1727,22 +1784,22 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
   if (!jac) {
     double* pm = G.part + P_MAX * (int64_t)n * G.nct;
     if (L.cc)
-      assemble_kernel<T, true, true, false, false>(c, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+      assemble_kernel<T, true, true, false, false>(c, L.nx, L.ny)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
           phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
           G.newton_active, G.F, nullptr, L.plane, pm, L.cc, L.fc);
     else
-      assemble_kernel<T, true, false, false, false>(c, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+      assemble_kernel<T, true, false, false, false>(c, L.nx, L.ny)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
           phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
           G.newton_active, G.F, nullptr, L.plane, pm, nullptr, nullptr);
     CKL();
     return HENRY_OK;
   }
   if (L.cc)
-    assemble_kernel<T, true, true>(H->cfg, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
+    assemble_kernel<T, true, true>(H->cfg, L.nx, L.ny)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(
         phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h, lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
         G.newton_active, G.F, (B4*)L.J, L.plane, G.part + P_MAX * (int64_t)n * G.nct, L.cc, L.fc);
   else
-    assemble_kernel<T, true>(H->cfg, L.nx)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
+    assemble_kernel<T, true>(H->cfg, L.nx, L.ny)<<<nblk((int64_t)n * L.N), TPB, 0, st>>>(phys_of(c), G.coef, n, L.nx, L.ny, lg.h, 1.0 / lg.h,
                                                                  lg.h * lg.h * inv_tau * inv_s, inv_s, L.x, L.xo,
                                                                  G.newton_active, G.F, (B4*)L.J, L.plane,
                                                                  G.part + P_MAX * (int64_t)n * G.nct, nullptr, nullptr);
@@ -1855,11 +1912,11 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
       H->nact = B;
       launch(H, st, HENRY_K_ASSEMBLE, (double)n0 * (48.0 + 6.0 * sizeof(B4)), [&] {
         if (L.cc)
-          assemble_kernel<double, true, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt,
+          assemble_kernel<double, true, true>(H->cfg, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt,
                                                                   inv_s, L.x, L.xo, G.lin_active, G.F, (B4*)L.J,
                                                                   L.plane, pmax, L.cc, L.fc);
         else
-          assemble_kernel<double, true>(H->cfg, L.nx)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s,
+          assemble_kernel<double, true>(H->cfg, L.nx, L.ny)<<<nblk(n0), TPB, 0, st>>>(ph, G.coef, B, L.nx, L.ny, lg.h, 1.0 / lg.h, vt, inv_s,
                                                             L.x, L.xo, G.lin_active, G.F, (B4*)L.J, L.plane, pmax, nullptr, nullptr);
       });
       CKL();
@@ -2017,6 +2074,9 @@ int check_step_args(henry_handle* h, int level, const double* xi, int n, const d
 
 // Configuration checks shared by henry_create and the allocation-free entry
 // point (which has no workspace_bytes budget: with_workspace false).
+bool valid_tile_w(int w) { return w == 0 || w == 32 || w == 64 || w == 128 || w == 256; }
+bool valid_mg_threads(int n) { return n == 0 || n == 64 || n == 128 || n == 256 || n == 512; }
+
 int check_config(const henry_config& c, bool with_workspace) {
   // every floating-point setting finite (a NaN would pass the comparisons below)
   const double reals[] = {c.Lx, c.Ly, c.T, c.rho0, c.rho1, c.mu, c.g, c.Dm, c.phi_mean, c.K_mean, c.qin_mean,
@@ -2062,6 +2122,10 @@ int check_config(const henry_config& c, bool with_workspace) {
       !(c.newton_predictor >= 0.0 && c.newton_predictor <= 1.0) || !(c.newton_dc_limit >= 0.0) ||
       c.newton_jacobian_every < 1)
     return set_err(HENRY_EINVAL, "bad solver settings");
+  if (!valid_tile_w(c.assembly_tile_w)) return set_err(HENRY_EINVAL, "assembly_tile_w %d not in {0, 32, 64, 128, 256}",
+                                                       c.assembly_tile_w);
+  if (!valid_mg_threads(c.mg_threads))
+    return set_err(HENRY_EINVAL, "mg_threads %d not in {0, 64, 128, 256, 512}", c.mg_threads);
   return HENRY_OK;
 }
 
@@ -2101,6 +2165,8 @@ void henry_default_config(henry_config* c) {
   c->mg_tail_cells = 128;
   c->mg_tail_batch_cells = 1 << 20;
   c->scheme = HENRY_SCHEME_CELL;
+  c->assembly_tile_w = 0;
+  c->mg_threads = 0;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -2131,7 +2197,7 @@ int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
     return HENRY_OK;
   }
   if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < 0 ||
-      t->newton_jacobian_every < 1)
+      t->newton_jacobian_every < 1 || !valid_tile_w(t->assembly_tile_w) || !valid_mg_threads(t->mg_threads))
     return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d, mg_tail_cells %d)", t->lin_rtol, t->nu1,
                    t->nu2, t->mg_tail_cells);
   h->tuned[level] = *t;
@@ -2153,6 +2219,8 @@ int henry_get_tuning(henry_handle* h, int level, henry_tuning* out) {
     out->mg_tail_cells = h->cfg.mg_tail_cells;
     out->newton_residual_first = h->cfg.newton_residual_first;
     out->newton_jacobian_every = h->cfg.newton_jacobian_every;
+    out->assembly_tile_w = h->cfg.assembly_tile_w;
+    out->mg_threads = h->cfg.mg_threads;
   }
   return HENRY_OK;
 }
@@ -2195,6 +2263,8 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         t.mg_tail_cells = c.mg_tail_cells;
         t.newton_residual_first = c.newton_residual_first;
         t.newton_jacobian_every = c.newton_jacobian_every;
+        t.assembly_tile_w = c.assembly_tile_w;
+        t.mg_threads = c.mg_threads;
         cands.push_back(t);
       }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2254,7 +2324,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
     fused_won = c.precision == HENRY_MIXED ? fused_eligible<float>(cb, level, &CL) : fused_eligible<double>(cb, level, &CL);
   }
   if (!rc && best >= 0 && !fused_won) {
-    const int tails[3] = {0, 128, 512};
+    const int tails[4] = {0, 32, 128, 512};
     for (int v : tails) {
       if (v == cands[best].mg_tail_cells || rc) continue;
       henry_tuning t = cands[best];
@@ -2280,6 +2350,32 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         cands.push_back(t);
         trial((int)cands.size() - 1);
       }
+    }
+  }
+  if (!rc && best >= 0 && !fused_won && c.tile_assembly) {
+    // Stage 5: the assembly tile (whole rows / 128 x 2 by default, or
+    // w x 256 / w tiles), where the level's fine grid takes that tile.
+    const int b4 = best;
+    for (int v : {0, 32, 64, 128, 256}) {
+      if (v == cands[b4].assembly_tile_w || rc) continue;
+      if (v > 0 && (lg.nx % v != 0 || lg.ny % (TPB / v) != 0)) continue;
+      henry_tuning t = cands[b4];
+      t.assembly_tile_w = v;
+      cands.push_back(t);
+      trial((int)cands.size() - 1);
+    }
+  }
+  if (!rc && best >= 0 && !fused_won) {
+    // Stage 6: the CTA size of the smoother, restriction and prolongation
+    // kernels (small batches of mid-size grids fill more SMs with smaller CTAs).
+    const int b5 = best;
+    for (int v : {64, 128, 256, 512}) {
+      const int cur = cands[b5].mg_threads == 0 ? TPB : cands[b5].mg_threads;
+      if (v == cur || rc) continue;
+      henry_tuning t = cands[b5];
+      t.mg_threads = v;
+      cands.push_back(t);
+      trial((int)cands.size() - 1);
     }
   }
   h->tuned.erase(level);

@@ -628,15 +628,16 @@ __global__ void __launch_bounds__(TPB) k_assemble_tile(Phys ph, const Coef* __re
   }
 }
 
-// Tile assembly for grids wider than TPB cells: a CTA covers a TW x (TPB /
-// TW) block of cells of one sample (TW = 128), mapped by position, not by
-// storage order.  Phase 1: every cell evaluates its east and north faces
-// into shared memory.  Phase 2: a cell takes its west and south faces from
-// the tile, or, on the tile's west or south edge, evaluates them itself.
-// About 2.5 face evaluations per cell.  The per-tile max |F| goes to slot
-// (tile index) of the sample's N / TPB partials.
-constexpr int TILE_W = 128;
-template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
+// Tile assembly in 2-D tiles: a CTA covers a TILE_W x (TPB / TILE_W) block
+// of cells of one sample, mapped by position, not by storage order (nx a
+// multiple of TILE_W, ny of TPB / TILE_W).  Phase 1: every cell evaluates its
+// east and north faces into shared memory.  Phase 2: a cell takes its west
+// and south faces from the tile, or, on the tile's west or south edge,
+// evaluates them itself: 2 + 1 / TH + 1 / TILE_W face evaluations per cell
+// (TH = TPB / TILE_W rows; 2.5 for 128 x 2, 2.16 for 32 x 8).  The per-tile
+// max |F| goes to slot (tile index) of the sample's N / TPB partials.
+constexpr int TILE_W_DEFAULT = 128;  // for grids wider than TPB cells
+template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true, int TILE_W = TILE_W_DEFAULT>
 __global__ void __launch_bounds__(TPB) k_assemble_tile2d(Phys ph, const Coef* __restrict__ coef, int B, int nx,
                                                          int ny, double h, double inv_h, double vt_s, double inv_s,
                                                          const double2* __restrict__ x, const double2* __restrict__ xo,
@@ -905,14 +906,15 @@ __device__ __forceinline__ typename VT<T>::v2 sweep_cell(int nx, int ny, int ix,
   return mk2<V2>(y0, y1);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(TPB) k_sweep(int B, int nx, int ny, int col, const typename VT<T>::b4* __restrict__ J,
+// NT: threads per CTA (any multiple of 32 up to 1024; every thread owns one cell).
+template <typename T, int MODE, int NT = TPB>
+__global__ void __launch_bounds__(NT) k_sweep(int B, int nx, int ny, int col, const typename VT<T>::b4* __restrict__ J,
                                                int64_t plane, const typename VT<T>::v2* __restrict__ b,
                                                typename VT<T>::v2* __restrict__ x,
                                                const typename VT<T>::v2* __restrict__ xc,
                                                const int* __restrict__ active) {
   const int N = nx * ny, halfN = N >> 1, half = nx >> 1;
-  const int64_t t = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (t >= (int64_t)B * halfN) return;
   const int s = (int)(t / halfN);
   if (!active[s]) return;
@@ -978,15 +980,15 @@ __device__ __forceinline__ typename VT<T>::v2 restrict_cell(int ncx, int ncy, in
   return mk2<V2>(s0, s1);
 }
 
-template <typename T, int MODE>  // MODE 0: RED_ONLY, 1: ZERO_X
-__global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int ncy,
+template <typename T, int MODE, int NT = TPB>  // MODE 0: RED_ONLY, 1: ZERO_X
+__global__ void __launch_bounds__(NT) k_residual_restrict(int B, int ncx, int ncy,
                                                            const typename VT<T>::b4* __restrict__ J, int64_t plane,
                                                            const typename VT<T>::v2* __restrict__ b,
                                                            const typename VT<T>::v2* __restrict__ x,
                                                            typename VT<T>::v2* __restrict__ bc,
                                                            const int* __restrict__ active) {
   const int Nc = ncx * ncy;
-  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (e >= (int64_t)B * Nc) return;
   const int s = (int)(e / Nc);
   if (!active[s]) return;
@@ -998,13 +1000,13 @@ __global__ void __launch_bounds__(TPB) k_residual_restrict(int B, int ncx, int n
 }
 
 // x += P x_c (used only when there is no post-smoothing to fuse it into).
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_prolong_add(int B, int nx, int ny, typename VT<T>::v2* __restrict__ x,
-                                                     const typename VT<T>::v2* __restrict__ xc,
-                                                     const int* __restrict__ active) {
+template <typename T, int NT = TPB>
+__global__ void __launch_bounds__(NT) k_prolong_add(int B, int nx, int ny, typename VT<T>::v2* __restrict__ x,
+                                                    const typename VT<T>::v2* __restrict__ xc,
+                                                    const int* __restrict__ active) {
   typedef typename VT<T>::v2 V2;
   const int N = nx * ny;
-  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (e >= (int64_t)B * N) return;
   const int s = (int)(e / N);
   if (!active[s]) return;
@@ -1017,9 +1019,9 @@ __global__ void __launch_bounds__(TPB) k_prolong_add(int B, int nx, int ny, type
   x[e] = v;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_zero(int64_t n, typename VT<T>::v2* __restrict__ x) {
-  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+template <typename T, int NT = TPB>
+__global__ void __launch_bounds__(NT) k_zero(int64_t n, typename VT<T>::v2* __restrict__ x) {
+  const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
   if (e < n) x[e] = mk2<typename VT<T>::v2>((T)0, (T)0);
 }
 

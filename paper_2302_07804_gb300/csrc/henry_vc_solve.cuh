@@ -265,22 +265,29 @@ __global__ void __launch_bounds__(TPB) k_vc_prolong_add(int B, VcLevelArgs Lf, V
   int j, i;
   vxy(st, nfxv, j, i);
   const V2* c = xc + (int64_t)s * Lc.stride;
+  // the coarse vertices around (j, i): (J0 | J1) x (I0 | I1), with J1 = J0
+  // when j is even and I1 = I0 when i is even; weights 1, 1/2 or 1/4
   const int J0 = j >> 1, I0 = i >> 1, J1 = J0 + (j & 1), I1 = I0 + (i & 1);
-  const V2 a = c[vst(J0, I0, ncxv)], bb = c[vst(J0, I1, ncxv)], cc = c[vst(J1, I0, ncxv)], d = c[vst(J1, I1, ncxv)];
+  V2 sum = c[vst(J0, I0, ncxv)];
+  if (i & 1) {
+    const V2 e = c[vst(J0, I1, ncxv)];
+    sum.x += e.x;
+    sum.y += e.y;
+  }
+  if (j & 1) {
+    const V2 n = c[vst(J1, I0, ncxv)];
+    sum.x += n.x;
+    sum.y += n.y;
+    if (i & 1) {
+      const V2 ne = c[vst(J1, I1, ncxv)];
+      sum.x += ne.x;
+      sum.y += ne.y;
+    }
+  }
   const T w = (T)(((j & 1) ? 0.5 : 1.0) * ((i & 1) ? 0.5 : 1.0));
   V2 v = xf[(int64_t)s * Lf.stride + st];
-  // the four corners coincide where j or i is even; the weights then repeat the same value
-  const int nterm = ((j & 1) ? 2 : 1) * ((i & 1) ? 2 : 1);
-  T p0 = a.x, p1 = a.y;
-  if (nterm == 2) {
-    p0 = (j & 1) ? a.x + cc.x : a.x + bb.x;
-    p1 = (j & 1) ? a.y + cc.y : a.y + bb.y;
-  } else if (nterm == 4) {
-    p0 = ((a.x + bb.x) + cc.x) + d.x;
-    p1 = ((a.y + bb.y) + cc.y) + d.y;
-  }
-  v.x = fma_(w, p0, v.x);
-  v.y = fma_(w, p1, v.y);
+  v.x = fma_(w, sum.x, v.x);
+  v.y = fma_(w, sum.y, v.y);
   xf[(int64_t)s * Lf.stride + st] = v;
 }
 

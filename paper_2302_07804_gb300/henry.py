@@ -49,7 +49,8 @@ class HenryConfig(ctypes.Structure):
                 ("tile_assembly", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
                 ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("newton_jacobian_every", ctypes.c_int32),
-                ("level_priority", ctypes.c_int32)]
+                ("level_priority", ctypes.c_int32), ("assembly_tile_w", ctypes.c_int32),
+                ("mg_threads", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -75,7 +76,8 @@ class HenryTuning(ctypes.Structure):
     _fields_ = [("lin_rtol", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double),
                 ("mg_tail_cells", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
-                ("newton_jacobian_every", ctypes.c_int32)]
+                ("newton_jacobian_every", ctypes.c_int32), ("assembly_tile_w", ctypes.c_int32),
+                ("mg_threads", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

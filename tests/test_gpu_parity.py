@@ -470,6 +470,46 @@ def test_fused_multigrid_tail_is_bit_identical(hl, precision):
     assert q[0][3] == q[1][3]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_cta_size_and_tile_shape_are_bit_identical(hl, precision):
+    """The smoother, restriction and prolongation kernels' CTA size
+    (mg_threads) and the assembly tile (assembly_tile_w) change only which
+    CTA and thread does a cell's arithmetic: one V-cycle at levels 1 and 3
+    and level-2 solves with coarse partners are bit-identical, with the
+    settings in the configuration and as a level's tuning on one handle (so
+    that the BiCGStab graphs captured under one setting are not replayed
+    under another)."""
+    for level in (1, 3):
+        grid, xi, p, c, po, co = _random_case(890 + level, level, 2)
+        b = inputs.random_vectors(891 + level, 2, grid.ny, grid.nx)
+        zs = []
+        for nt in (0, 64, 128, 512):
+            s = hl.Solver(mg_threads=nt, mg_tail_cells=0, precision=precision)
+            zs.append(s.precondition(level, _to_dev(xi), _to_dev(_states_np(p, c)), _to_dev(_states_np(po, co)),
+                                     _to_dev(b)))
+            s.close()
+        for z in zs[1:]:
+            assert torch.equal(z, zs[0]), level
+    xi = hl.sample_xi(inputs.SEED, 2, 5200, 4)
+    q = []
+    for kw in (dict(), dict(mg_threads=128), dict(mg_threads=512, assembly_tile_w=32),
+               dict(mg_threads=64, assembly_tile_w=64, mg_tail_cells=0)):
+        s = hl.Solver(precision=precision, fused_small_grids=0, **kw)
+        qf, qc, st, stats = s.level_batch_solve(2, xi, with_coarse=True)
+        q.append((qf, qc, st, stats["newton_iters"], stats["linear_iters"]))
+        s.close()
+    s = hl.Solver(precision=precision, fused_small_grids=0)
+    for kw in (dict(mg_threads=128), dict(mg_threads=512, assembly_tile_w=32), dict(mg_tail_cells=0)):
+        for lv in (1, 2):
+            s.set_tuning(lv, dict(s.tuning(lv), **kw))
+        qf, qc, st, stats = s.level_batch_solve(2, xi, with_coarse=True)
+        q.append((qf, qc, st, stats["newton_iters"], stats["linear_iters"]))
+    s.close()
+    for o in q[1:]:
+        assert torch.equal(o[0], q[0][0]) and torch.equal(o[1], q[0][1]) and torch.equal(o[2], q[0][2])
+        assert o[3:] == q[0][3:]
+
+
 @pytest.mark.parametrize("every,precision", [(2, 0), (3, 0), (2, 1)])
 def test_chord_newton_reaches_the_oracle_solution(hl, every, precision):
     """Chord Newton (the Jacobian and coarse operators re-assembled every

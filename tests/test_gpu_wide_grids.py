@@ -191,3 +191,23 @@ def test_kl_assemble_level4_against_oracle(hl):
                 np.testing.assert_allclose(J[..., k, eq, var], Jo[..., k, eq, var], rtol=0,
                                            atol=1e-11 * max(scale, 1e-300))
     s.close()
+
+
+@pytest.mark.parametrize("level,tile_w", [(3, 32), (3, 256), (4, 32), (4, 64), (4, 256)])
+def test_assembly_tile_shapes_give_identical_values(hl, level, tile_w):
+    """Each tile shape (assembly_tile_w x 256 / assembly_tile_w cells)
+    evaluates every face with the same arithmetic as the default tiles (whole
+    256-cell rows at level 3, 128 x 2 at level 4), only in another CTA or
+    thread: F and every block are bit-identical, for the three-parameter and
+    the KL model (per-cell fields and face means)."""
+    grid, xi, p, c, po, co = _case(950 + level, level, 2)
+    gen = inputs.rng(952 + level)
+    th = _dev(np.concatenate([gen.standard_normal((2, 64)), gen.uniform(-1, 1, (2, 1))], axis=1))
+    for model, x in ((hl.HENRY_MODEL_UNIFORM3, _dev(xi)), (hl.HENRY_MODEL_KL, th)):
+        ref = hl.Solver(coef_model=model)
+        alt = hl.Solver(coef_model=model, assembly_tile_w=tile_w)
+        F0, J0 = ref.assemble(level, x, _dev(_st(p, c)), _dev(_st(po, co)))
+        F1, J1 = alt.assemble(level, x, _dev(_st(p, c)), _dev(_st(po, co)))
+        assert torch.equal(F1, F0) and torch.equal(J1, J0), (model, tile_w)
+        ref.close()
+        alt.close()
