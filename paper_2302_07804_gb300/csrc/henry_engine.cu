@@ -395,8 +395,9 @@ void prof_drain(henry_handle* H) {
 // assembly_tile_w x (TPB / assembly_tile_w) tiles where that tile divides the
 // grid, else whole rows per tile where they fit (nx <= TPB), else 128 x 2
 // tiles; the per-cell form with tile_assembly = 0.  Same arguments; the tile
-// forms give identical values (each face's arithmetic is the same wherever it
-// is evaluated), the per-cell form the same up to rounding.
+// forms evaluate each face with the same source arithmetic wherever it is
+// evaluated, the per-cell form evaluates it from both sides (same values up
+// to rounding).
 // JAC = false: the fine residual alone (same values as with JAC = true).
 template <typename T, bool FINE, bool FIELDS = false, bool DROP = false, bool JAC = true>
 auto assemble_kernel(const henry_config& c, int nx, int ny) -> decltype(&k_assemble<T, FINE, FIELDS, DROP, JAC>) {
@@ -1606,9 +1607,30 @@ int vc_set_coefficients(henry_handle* H, VcGroup<T>& G, const double* xi, int B,
   return HENRY_OK;
 }
 
+// The level's autotuned settings (henry_autotune) in force for one scope.
+struct TuningScope {
+  henry_handle* H;
+  henry_config saved;
+  TuningScope(henry_handle* h, int level) : H(h), saved(h->cfg) {
+    auto f = h->tuned.find(level);
+    if (f == h->tuned.end()) return;
+    h->cfg.lin_rtol = f->second.lin_rtol;
+    h->cfg.nu1 = f->second.nu1;
+    h->cfg.nu2 = f->second.nu2;
+    h->cfg.fused_small_grids = f->second.fused_small_grids;
+    h->cfg.mg_tail_cells = f->second.mg_tail_cells;
+    h->cfg.newton_residual_first = f->second.newton_residual_first;
+    h->cfg.newton_jacobian_every = std::max(1, f->second.newton_jacobian_every);
+    h->cfg.assembly_tile_w = f->second.assembly_tile_w;
+    h->cfg.mg_threads = f->second.mg_threads;
+  }
+  ~TuningScope() { H->cfg = saved; }
+};
+
 template <typename T>
 int vc_batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status,
                          bool first, henry_stats* stats, cudaStream_t st) {
+  TuningScope tuning(H, level);
   const LevelGeom lg = geom(H->cfg, level);
   const double per = (double)vc_bytes_per_sample<T>(H->cfg, level);
   const int Bmax = (int)std::max(1.0, std::min(std::floor(H->cfg.workspace_bytes / per), 1.0e6));
@@ -1696,26 +1718,6 @@ int vc_step_entry(henry_handle* H, int which, int level, const double* xi, int n
   CKL();
   return HENRY_OK;
 }
-
-// The level's autotuned settings (henry_autotune) in force for one scope.
-struct TuningScope {
-  henry_handle* H;
-  henry_config saved;
-  TuningScope(henry_handle* h, int level) : H(h), saved(h->cfg) {
-    auto f = h->tuned.find(level);
-    if (f == h->tuned.end()) return;
-    h->cfg.lin_rtol = f->second.lin_rtol;
-    h->cfg.nu1 = f->second.nu1;
-    h->cfg.nu2 = f->second.nu2;
-    h->cfg.fused_small_grids = f->second.fused_small_grids;
-    h->cfg.mg_tail_cells = f->second.mg_tail_cells;
-    h->cfg.newton_residual_first = f->second.newton_residual_first;
-    h->cfg.newton_jacobian_every = std::max(1, f->second.newton_jacobian_every);
-    h->cfg.assembly_tile_w = f->second.assembly_tile_w;
-    h->cfg.mg_threads = f->second.mg_threads;
-  }
-  ~TuningScope() { H->cfg = saved; }
-};
 
 template <typename T>
 int batch_solve_level(henry_handle* H, int level, const double* xi, int n, double* qoi, int32_t* status, bool first,
@@ -2323,9 +2325,11 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
     cb.fused_small_grids = cands[best].fused_small_grids;
     fused_won = c.precision == HENRY_MIXED ? fused_eligible<float>(cb, level, &CL) : fused_eligible<double>(cb, level, &CL);
   }
+  const bool cc = c.scheme == HENRY_SCHEME_CELL;  // the tail, tile and CTA-size stages are the cell scheme's
   if (!rc && best >= 0 && !fused_won) {
     const int tails[4] = {0, 32, 128, 512};
     for (int v : tails) {
+      if (!cc) break;
       if (v == cands[best].mg_tail_cells || rc) continue;
       henry_tuning t = cands[best];
       t.mg_tail_cells = v;
@@ -2352,7 +2356,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       }
     }
   }
-  if (!rc && best >= 0 && !fused_won && c.tile_assembly) {
+  if (!rc && best >= 0 && !fused_won && cc && c.tile_assembly) {
     // Stage 5: the assembly tile (whole rows / 128 x 2 by default, or
     // w x 256 / w tiles), where the level's fine grid takes that tile.
     const int b4 = best;
@@ -2365,7 +2369,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
       trial((int)cands.size() - 1);
     }
   }
-  if (!rc && best >= 0 && !fused_won) {
+  if (!rc && best >= 0 && !fused_won && cc) {
     // Stage 6: the CTA size of the smoother, restriction and prolongation
     // kernels (small batches of mid-size grids fill more SMs with smaller CTAs).
     const int b5 = best;

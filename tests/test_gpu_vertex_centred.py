@@ -270,3 +270,28 @@ def test_vc_residual_first_and_chord_newton(hl):
     assert int(st.abs().sum()) == 0
     _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
     s.close()
+
+
+def test_vc_level_tuning_applies_and_autotune_runs(hl):
+    """A level's tuning (henry_set_tuning, henry_autotune) governs the
+    vertex-centred solve as it does the cell-centred one: with lin_rtol 1e-2
+    and the Jacobian every 2nd iteration set as level 0's tuning, the solve
+    takes that path (fewer BiCGStab iterations than the configuration's
+    settings) and still reaches the oracle's QoIs at 1e-10; the autotuner
+    returns a setting that solves every trial sample."""
+    prm = vc.Params()
+    xi = hl.sample_xi(inputs.SEED, 0, 7400, 3)
+    s = _vc_solver(hl)
+    _, _, _, plain = s.level_batch_solve(0, xi)
+    s.set_tuning(0, dict(s.tuning(0), lin_rtol=1e-2, newton_jacobian_every=2))
+    q, _, st, tuned = s.level_batch_solve(0, xi)
+    assert int(st.abs().sum()) == 0
+    assert tuned["linear_iters"] < plain["linear_iters"], (tuned, plain)
+    _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
+    s.set_tuning(0, None)
+    t = s.autotune(0, hl.sample_xi(inputs.SEED, 0, 7500, 64))
+    assert t["cell_steps_per_s"] > 0 and t["mg_tail_cells"] == s.cfg.mg_tail_cells
+    q, _, st, _ = s.level_batch_solve(0, xi)
+    assert int(st.abs().sum()) == 0
+    _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
+    s.close()
