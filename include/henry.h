@@ -190,9 +190,10 @@ typedef struct {
   int32_t assembly_tile_w; /* face-once assembly tiles: 0 (default) whole rows up to 256 cells wide, else
                               128 x 2; 32, 64, 128 or 256: tiles of that many cells x 256 / width rows on
                               every grid whose width and height they divide (the default elsewhere).
-                              Every shape evaluates each face with the same arithmetic (FP64 results
-                              bit-identical; FP32 coarse operators may differ in the last bit where the
-                              compiler contracts a multiply-add differently) */
+                              Every shape evaluates each face with the same source arithmetic: F is
+                              bit-identical, Jacobian entries may differ in the last bit (the compiler
+                              contracts multiply-adds per call site, and tile-edge faces are evaluated
+                              at another call site) */
   int32_t mg_threads; /* threads per CTA of the multigrid smoother, restriction and prolongation kernels of
                          the cell-centred scheme: 64, 128, 256 or 512 (0, the default: 256).  Identical
                          values for every size */

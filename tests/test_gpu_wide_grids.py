@@ -196,10 +196,14 @@ def test_kl_assemble_level4_against_oracle(hl):
 @pytest.mark.parametrize("level,tile_w", [(3, 32), (3, 256), (4, 32), (4, 64), (4, 256)])
 def test_assembly_tile_shapes_give_identical_values(hl, level, tile_w):
     """Each tile shape (assembly_tile_w x 256 / assembly_tile_w cells)
-    evaluates every face with the same arithmetic as the default tiles (whole
-    256-cell rows at level 3, 128 x 2 at level 4), only in another CTA or
-    thread: F and every block are bit-identical, for the three-parameter and
-    the KL model (per-cell fields and face means)."""
+    evaluates every face with the same source arithmetic as the default tiles
+    (whole 256-cell rows at level 3, 128 x 2 at level 4), only in another CTA
+    or thread, or on a tile edge instead of in shared memory: F is
+    bit-identical, and every Jacobian block entry agrees to 1e-14 of that
+    entry's largest magnitude (the compiler contracts multiply-adds into FMAs
+    per call site, so the face derivatives evaluated on a tile edge may differ
+    in the last bit), for the three-parameter and the KL model (per-cell
+    fields and face means)."""
     grid, xi, p, c, po, co = _case(950 + level, level, 2)
     gen = inputs.rng(952 + level)
     th = _dev(np.concatenate([gen.standard_normal((2, 64)), gen.uniform(-1, 1, (2, 1))], axis=1))
@@ -208,6 +212,13 @@ def test_assembly_tile_shapes_give_identical_values(hl, level, tile_w):
         alt = hl.Solver(coef_model=model, assembly_tile_w=tile_w)
         F0, J0 = ref.assemble(level, x, _dev(_st(p, c)), _dev(_st(po, co)))
         F1, J1 = alt.assemble(level, x, _dev(_st(p, c)), _dev(_st(po, co)))
-        assert torch.equal(F1, F0) and torch.equal(J1, J0), (model, tile_w)
+        assert torch.equal(F1, F0), (model, tile_w)
+        J0, J1 = J0.cpu().numpy(), J1.cpu().numpy()
+        for k in range(J0.shape[-3]):
+            for eq in range(2):
+                for var in range(2):
+                    scale = np.abs(J0[..., k, eq, var]).max()
+                    np.testing.assert_allclose(J1[..., k, eq, var], J0[..., k, eq, var], rtol=0,
+                                               atol=1e-14 * max(scale, 1e-300), err_msg=str((model, tile_w, k)))
         ref.close()
         alt.close()
