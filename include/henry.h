@@ -174,8 +174,11 @@ typedef struct {
                                     Jacobian together.  Same values either way */
   int32_t mg_tail_cells; /* the V-cycle's coarse levels from the first one with at most this many cells per
                             sample down to the coarsest run as one kernel, one CTA per sample with those
-                            levels' operators and vectors in shared memory (default 128: 16 x 8 cells and
-                            below); 0: every level as separate kernels.  Same values either way */
+                            levels' vectors in shared memory, and their operators too where they fit beside
+                            them (the finest tail levels' operators are otherwise read from global memory at
+                            each use); -1 (default): 2048 cells (64 x 32) with FP32 linear algebra, 128
+                            (16 x 8) with FP64, the faster choice measured on small batches of each; 0: every
+                            level as separate kernels.  Same values either way */
   int32_t mg_tail_batch_cells; /* ... only while the batch times that level's cells per sample is at most this
                                   (default 2^20; 0: no limit): large batches of small grids run those levels
                                   as separate, large launches */
@@ -222,7 +225,7 @@ void henry_paper_config(henry_config* cfg);
  * converges, never where (the FP64 Newton test decides): the Krylov tolerance,
  * the V-cycle's smoothing counts and, where the level's grid allows it, the
  * fused one-CTA-per-sample solver; then, one at a time from the best so far,
- * the fused multigrid tail (mg_tail_cells in {0, 32, 128, 512}), the
+ * the fused multigrid tail (mg_tail_cells in {0, 32, 128, 512, 2048}), the
  * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}), chord
  * Newton (newton_jacobian_every in {1, 2, 3}), the assembly tile
  * (assembly_tile_w in {0, 32, 64, 128, 256} where it divides the grid) and the

@@ -81,13 +81,35 @@ struct CtaParams {
   double rho0g, Ly;
 };
 
+// Global-memory operands of the tail, by tail level: the level's block planes
+// (6 planes of plane[k] blocks, a sample's N_k blocks at offset s N_k), the
+// right-hand side b and result x of the first level ([B][N_0] vectors), and
+// the coarsest inverses ([B][16]).
+struct TailArgs {
+  const void* J[CTA_MAX_LEVELS];
+  int64_t plane[CTA_MAX_LEVELS];
+  const void* b;
+  void* x;
+  const void* ainv;
+};
+
+// A CTA's view of its shared memory.  J(k) is level k's 6 block planes with
+// plane stride plane(k): in shared memory (stride N_k), or, for a tail level
+// whose layout has no room for them (L->J[k] < 0), the sample's blocks in
+// global memory (stride A->plane[k]), read through L2 at every use.
 template <typename T>
 struct CtaSmem {
   typedef typename VT<T>::v2 V2;
   typedef typename VT<T>::b4 B4;
   unsigned char* base;
   const CtaLayout* L;
-  __device__ B4* J(int k) const { return reinterpret_cast<B4*>(base + L->J[k]); }
+  const TailArgs* A = nullptr;  // the tail's global operands (streamed levels only)
+  int s = 0;                    // the CTA's sample
+  __device__ B4* J(int k) const {
+    if (L->J[k] >= 0) return reinterpret_cast<B4*>(base + L->J[k]);
+    return const_cast<B4*>(reinterpret_cast<const B4*>(A->J[k])) + (int64_t)s * (L->nx[k] * L->ny[k]);
+  }
+  __device__ int64_t plane(int k) const { return L->J[k] >= 0 ? (int64_t)L->nx[k] * L->ny[k] : A->plane[k]; }
   __device__ double2* X(int k) const { return reinterpret_cast<double2*>(base + L->X[k]); }
   __device__ double2* XO(int k) const { return reinterpret_cast<double2*>(base + L->XO[k]); }
   __device__ V2* MX(int k) const { return reinterpret_cast<V2*>(base + L->MX[k]); }
@@ -107,11 +129,12 @@ __device__ __forceinline__ void cta_sweep(const CtaSmem<T>& S, int k, int col, c
                                           typename VT<T>::v2* x, const typename VT<T>::v2* xc) {
   const int nx = S.L->nx[k], ny = S.L->ny[k], N = nx * ny, half = nx >> 1;
   const typename VT<T>::b4* J = S.J(k);
+  const int64_t ps = S.plane(k);
   for (int u = threadIdx.x; u < (N >> 1); u += blockDim.x) {
     const int iy = u / half, j = u - iy * half;
     const int ix = 2 * j + ((col ^ iy) & 1);
     const int i = iy * nx + col * half + j;
-    x[i] = sweep_cell<T, MODE>(nx, ny, ix, iy, i, J, N, b, x, xc);
+    x[i] = sweep_cell<T, MODE>(nx, ny, ix, iy, i, J, ps, b, x, xc);
   }
   __syncthreads();
 }
@@ -138,14 +161,14 @@ __device__ void cta_vcycle(const CtaSmem<T>& S, int nu1, int nu2, const typename
       for (int c = threadIdx.x; c < ncx * ncy; c += blockDim.x) {
         int IX, IY;
         xy_of(c, ncx, IX, IY);
-        bc[c] = restrict_cell<T, 0>(ncx, ncy, IX, IY, S.J(k), N, b, x);
+        bc[c] = restrict_cell<T, 0>(ncx, ncy, IX, IY, S.J(k), S.plane(k), b, x);
       }
     } else {
       for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = mk2<V2>((T)0, (T)0);
       for (int c = threadIdx.x; c < ncx * ncy; c += blockDim.x) {
         int IX, IY;
         xy_of(c, ncx, IX, IY);
-        bc[c] = restrict_cell<T, 1>(ncx, ncy, IX, IY, S.J(k), N, b, x);
+        bc[c] = restrict_cell<T, 1>(ncx, ncy, IX, IY, S.J(k), S.plane(k), b, x);
       }
     }
     __syncthreads();
@@ -495,8 +518,9 @@ namespace hk {
 
 // Shared-memory layout of a tail starting on an nx x ny grid: per level the
 // 6 block planes and the multigrid vectors x, b (level 0 of the layout is the
-// tail's first level kt), the coarsest inverse and a reduction buffer.
-__host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayout* L) {
+// tail's first level kt), the coarsest inverse and a reduction buffer.  The
+// first n_stream levels keep their block planes in global memory (J = -1).
+__host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayout* L, int n_stream = 0) {
   const int b4 = 4 * tsize, v2 = 2 * tsize;
   int o = 0, k = 0, nx = nx0, ny = ny0;
   for (;;) {
@@ -504,7 +528,11 @@ __host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayo
     const int N = nx * ny;
     L->nx[k] = nx;
     L->ny[k] = ny;
-    L->J[k] = o; o = cta_align(o + 6 * b4 * N);
+    if (k < n_stream) {
+      L->J[k] = -1;
+    } else {
+      L->J[k] = o; o = cta_align(o + 6 * b4 * N);
+    }
     L->MX[k] = o; o = cta_align(o + v2 * N);
     L->MB[k] = o; o = cta_align(o + v2 * N);
     L->X[k] = L->XO[k] = -1;
@@ -514,6 +542,7 @@ __host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayo
     ++k;
   }
   L->K = k;
+  if (n_stream > k) return false;  // the coarsest level's blocks stay in shared memory
   L->r = L->rh = L->p = L->v = L->t = L->ph = L->dx = -1;
   L->ainv = o; o = cta_align(o + 16 * tsize);
   L->red = o; o = cta_align(o + 40 * 8);
@@ -521,17 +550,6 @@ __host__ __device__ inline bool tail_layout(int nx0, int ny0, int tsize, CtaLayo
   return true;
 }
 
-// Global-memory operands of the tail, by tail level: the level's block planes
-// (6 planes of plane[k] blocks, a sample's N_k blocks at offset s N_k), the
-// right-hand side b and result x of the first level ([B][N_0] vectors), and
-// the coarsest inverses ([B][16]).
-struct TailArgs {
-  const void* J[CTA_MAX_LEVELS];
-  int64_t plane[CTA_MAX_LEVELS];
-  const void* b;
-  void* x;
-  const void* ainv;
-};
 
 // Copy n 16-byte words from global to shared memory (all threads of the CTA).
 __device__ __forceinline__ void cta_copy16(void* dst, const void* src, int n) {
@@ -540,7 +558,7 @@ __device__ __forceinline__ void cta_copy16(void* dst, const void* src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-constexpr int TAIL_MAX_THREADS = 256;
+constexpr int TAIL_MAX_THREADS = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_MAX_THREADS) k_vcycle_tail(const __grid_constant__ CtaLayout L,
@@ -554,9 +572,13 @@ __global__ void __launch_bounds__(TAIL_MAX_THREADS) k_vcycle_tail(const __grid_c
   CtaSmem<T> S;
   S.base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 31) & ~uintptr_t(31));
   S.L = &L;
+  S.A = &A;
+  S.s = s;
   const int K = L.K;
-  // the sample's operators of every tail level: 6 contiguous runs of N_k blocks
+  // the sample's operators of every tail level held in shared memory: 6
+  // contiguous runs of N_k blocks (streamed levels are read where used)
   for (int k = 0; k <= K; ++k) {
+    if (L.J[k] < 0) continue;
     const int N = L.nx[k] * L.ny[k];
     const int words = N * (int)sizeof(B4) / 16;
     const B4* Jg = reinterpret_cast<const B4*>(A.J[k]) + (int64_t)s * N;

@@ -720,19 +720,24 @@ int restrict_states(henry_handle* H, Group<T>& G, int B, bool old, const int* ac
 }
 
 // First multigrid level of the fused tail: the first coarse level (k >= 1)
-// with at most mg_tail_cells cells per sample, if the tail below it has at
+// with at most mg_tail_cells cells per sample (-1: 2048 with FP32 linear
+// algebra, 128 with FP64, as measured), if the tail below it has at
 // least two levels, its shared-memory layout fits and the batch is small
 // enough (B x cells of that level <= mg_tail_batch_cells; larger batches keep
 // those levels as separate kernels, which then are large launches and fill
 // the FP64 pipe better than the tail's partly idle warps); -1: no tail.
 template <typename T>
 int tail_level(const henry_config& c, const Group<T>& G, int B, CtaLayout* L) {
-  if (c.mg_tail_cells <= 0) return -1;
+  const int cells = c.mg_tail_cells < 0 ? (sizeof(T) == sizeof(float) ? 2048 : 128) : c.mg_tail_cells;
+  if (cells <= 0) return -1;
   for (int k = 1; k < G.K; ++k) {
-    if (G.lv[k].N > c.mg_tail_cells) continue;
+    if (G.lv[k].N > cells) continue;
     if (c.mg_tail_batch_cells > 0 && (double)B * G.lv[k].N > (double)c.mg_tail_batch_cells) return -1;
-    if (!tail_layout(G.lv[k].nx, G.lv[k].ny, (int)sizeof(T), L) || L->bytes > smem_optin()) return -1;
-    return k;
+    // the finest tail levels read their operators from global memory (L2)
+    // when the layout does not fit otherwise
+    for (int ns = 0; ns < G.K - k; ++ns)
+      if (tail_layout(G.lv[k].nx, G.lv[k].ny, (int)sizeof(T), L, ns) && L->bytes <= smem_optin()) return k;
+    return -1;
   }
   return -1;
 }
@@ -2164,7 +2169,7 @@ void henry_default_config(henry_config* c) {
   c->newton_residual_first = 2;
   c->newton_jacobian_every = 1;
   c->level_priority = 1;
-  c->mg_tail_cells = 128;
+  c->mg_tail_cells = -1;
   c->mg_tail_batch_cells = 1 << 20;
   c->scheme = HENRY_SCHEME_CELL;
   c->assembly_tile_w = 0;
@@ -2198,7 +2203,7 @@ int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
     h->tuned.erase(level);
     return HENRY_OK;
   }
-  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < 0 ||
+  if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < -1 ||
       t->newton_jacobian_every < 1 || !valid_tile_w(t->assembly_tile_w) || !valid_mg_threads(t->mg_threads))
     return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d, mg_tail_cells %d)", t->lin_rtol, t->nu1,
                    t->nu2, t->mg_tail_cells);
@@ -2327,7 +2332,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
   }
   const bool cc = c.scheme == HENRY_SCHEME_CELL;  // the tail, tile and CTA-size stages are the cell scheme's
   if (!rc && best >= 0 && !fused_won) {
-    const int tails[4] = {0, 32, 128, 512};
+    const int tails[5] = {0, 32, 128, 512, 2048};
     for (int v : tails) {
       if (!cc) break;
       if (v == cands[best].mg_tail_cells || rc) continue;

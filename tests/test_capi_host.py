@@ -218,9 +218,9 @@ def test_autotune_arguments_return_einval(L):
     assert L.henry_autotune(s._h, 9, 0, P(16), 4, ctypes.byref(t), None) == henry.HENRY_EINVAL
     # without tuning, a level's settings are the configuration's
     assert s.tuning(2) == {"lin_rtol": 1e-4, "nu1": 2, "nu2": 2, "fused_small_grids": 1, "cell_steps_per_s": 0.0,
-                           "mg_tail_cells": 128, "newton_residual_first": 2, "newton_jacobian_every": 1,
+                           "mg_tail_cells": -1, "newton_residual_first": 2, "newton_jacobian_every": 1,
                            "assembly_tile_w": 0, "mg_threads": 0}
-    for bad in (dict(mg_tail_cells=-1), dict(assembly_tile_w=48), dict(mg_threads=32), dict(newton_jacobian_every=0)):
+    for bad in (dict(mg_tail_cells=-2), dict(assembly_tile_w=48), dict(mg_threads=32), dict(newton_jacobian_every=0)):
         with pytest.raises(henry.HenryError):
             s.set_tuning(2, dict(s.tuning(2), **bad))
     good = dict(s.tuning(2), assembly_tile_w=32, mg_threads=128)
