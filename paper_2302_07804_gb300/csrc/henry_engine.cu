@@ -1241,9 +1241,45 @@ size_t vc_bytes_per_sample(const henry_config& c, int level) {
   return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h);
 }
 
+// The face-once vertex assembly needs 147 KB of dynamic shared memory with
+// the Jacobian (the per-vertex kernel is used where the device grants less).
+bool vc_tile_fits() { return smem_optin() >= vc_tile_smem<true>() + 1024; }
+template <typename T>
+int ensure_vc_tile_attr() {
+  static std::atomic<int> done[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_err(HENRY_EINVAL, "device %d outside [0, 64)", dev);
+  if (done[dev].load(std::memory_order_relaxed) || !vc_tile_fits()) return HENRY_OK;
+  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          vc_tile_smem<true>()));
+  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          vc_tile_smem<true>()));
+  done[dev].store(1, std::memory_order_relaxed);
+  return HENRY_OK;
+}
+
+// Residual (and with JAC the Jacobian) of every vertex of a level: the
+// face-once tile kernel with tile_assembly (default), else one thread per
+// vertex evaluating its eight faces.  Same arguments and outputs.
+template <typename T, bool FINE, bool JAC = true>
+void vc_assemble_launch(const henry_config& c, cudaStream_t st, const VcParams& P, const Coef* coef, int B,
+                        int stride, int64_t plane, double inv_s, const double2* x, const double2* xo,
+                        const int* active, double2* F, typename VT<T>::b4* J, double* rmax_part) {
+  const unsigned g = nblk((int64_t)B * stride);
+  if (c.tile_assembly && vc_tile_fits())
+    k_vc_assemble_tile<T, FINE, JAC><<<g, TPB, vc_tile_smem<JAC>(), st>>>(P, coef, B, stride, plane, inv_s, x, xo,
+                                                                          active, F, J, rmax_part);
+  else
+    k_vc_assemble_st<T, FINE, JAC><<<g, TPB, 0, st>>>(P, coef, B, stride, plane, inv_s, x, xo, active, F, J,
+                                                      rmax_part);
+}
+
 template <typename T>
 int vc_get_group(henry_handle* H, int level, int B, VcGroup<T>** out) {
   int rc0 = ensure_pinned(H);
+  if (rc0) return rc0;
+  rc0 = ensure_vc_tile_attr<T>();
   if (rc0) return rc0;
   VcGroup<T>& g = vgroups<T>(H)[level];
   if (g.mem && g.Bcap >= B) {
@@ -1306,9 +1342,8 @@ int vc_coarse_ops(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_
   for (int k = 1; k <= G.K; ++k) {
     auto& L = G.lv[k];
     launch(H, st, HENRY_K_COARSE_OPS, (double)H->nact * L.NV * (32.0 + 10.0 * sizeof(B4)), [&] {
-      k_vc_assemble_st<T, false><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
-          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.lin_active, nullptr,
-          (B4*)L.J, nullptr);
+      vc_assemble_launch<T, false>(H->cfg, st, vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x,
+                                   L.xo, G.lin_active, nullptr, (B4*)L.J, nullptr);
     });
     CKL();
   }
@@ -1496,15 +1531,14 @@ int vc_assemble_fine(henry_handle* H, VcGroup<T>& G, int B, double tau, double i
   auto& L = G.lv[0];
   if (jac)
     launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * L.NV * (48.0 + 10.0 * sizeof(B4)), [&] {
-      k_vc_assemble_st<T, true><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
-          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
-          (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
+      vc_assemble_launch<T, true>(H->cfg, st, vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x,
+                                  L.xo, G.newton_active, G.F, (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
     });
   else
     launch(H, st, HENRY_K_RESIDUAL, (double)H->nact * L.NV * 48.0, [&] {
-      k_vc_assemble_st<T, true, false><<<nblk((int64_t)B * L.stride), TPB, 0, st>>>(
-          vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x, L.xo, G.newton_active, G.F,
-          nullptr, G.part + P_MAX * (int64_t)B * G.nct);
+      vc_assemble_launch<T, true, false>(H->cfg, st, vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s,
+                                         L.x, L.xo, G.newton_active, G.F, nullptr,
+                                         G.part + P_MAX * (int64_t)B * G.nct);
     });
   CKL();
   return HENRY_OK;

@@ -139,6 +139,73 @@ struct VcNaturalIndex {  // [ny + 1][nx + 1] row-major
   __host__ __device__ int operator()(int j, int i) const { return j * nx1 + i; }
 };
 
+// The pieces of a vertex's residual row, in the order vc_vertex_at adds
+// them (the face-once tile kernel adds the same pieces in the same order).
+// Rows are Jm[q][var] (mass) and Js[q][var] (salt), q = (dj + 1) 3 + (di + 1)
+// the neighbour (j + dj, i + di), var 0: p, 1: c.
+
+// Lumped storage phi |CV| (rho c^k - rho_old c_old^k) / tau of vertex (j, i)
+// (k = 0: mass, 1: salt) with cv, cvo its c and old c.
+template <bool JAC = true>
+__host__ __device__ inline void vc_storage(const VcParams& P, const VcCoef& C, double cv, double cvo, int j, int i,
+                                           double& Rm, double& Rs, double Jm[9][2], double Js[9][2]) {
+  const double rho = P.rho0 + P.drho * cv, rho_o = P.rho0 + P.drho * cvo;
+  const int nel = (i > 0 && j > 0) + (i < P.nx && j > 0) + (i > 0 && j < P.ny) + (i < P.nx && j < P.ny);
+  const double wt = C.phi * nel * (0.25 * P.h * P.h) / P.tau;  // lumped phi |CV| / tau
+  Rm += wt * (rho - rho_o);
+  Rs += wt * (rho * cv - rho_o * cvo);
+  if (JAC) {
+    Jm[4][1] += wt * P.drho;
+    Js[4][1] += wt * (rho + P.drho * cv);
+  }
+}
+
+// A face's fluxes out of the vertex's volume (sgn +1 when the vertex is the
+// face's source corner, -1 when it is the target) and their derivatives with
+// respect to the element's corners; q0 is the row slot of the element's
+// corner 0.
+template <bool JAC = true>
+__host__ __device__ inline void vc_add_face(double sgn, int q0, double F, const double* dF, double G,
+                                            const double* dG, double& Rm, double& Rs, double Jm[9][2],
+                                            double Js[9][2]) {
+  Rm += sgn * F;
+  Rs += sgn * G;
+  if (!JAC) return;
+  for (int k = 0; k < 4; ++k) {
+    const int q = q0 + (k >> 1) * 3 + (k & 1);
+    Jm[q][0] += sgn * dF[k];
+    Jm[q][1] += sgn * dF[4 + k];
+    Js[q][0] += sgn * dG[k];
+    Js[q][1] += sgn * dG[4 + k];
+  }
+}
+
+// Inflow of fresh water through x = 0 and the Dirichlet rows (x = Lx: both
+// equations; x = 0: salt); pv, cv the vertex's p and c.
+template <bool JAC = true>
+__host__ __device__ inline void vc_boundary(const VcParams& P, const VcCoef& C, double pv, double cv, int j, int i,
+                                            double& Rm, double& Rs, double Jm[9][2], double Js[9][2]) {
+  if (i == 0) Rm -= P.rho0 * C.qin * ((j == 0 || j == P.ny) ? 0.5 * P.h : P.h);
+  const double sc = P.rho0 * P.h * P.h / P.tau;
+  if (i == P.nx) {
+    const double pb = P.rho1 * P.g * (P.Ly - j * P.h);
+    const double pscale = P.rho0 * P.g * P.Ly;
+    Rm = sc * (pv - pb) / pscale;
+    Rs = sc * (cv - 1.0);
+    if (JAC) {
+      for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
+      Jm[4][0] = sc / pscale;
+      Js[4][1] = sc;
+    }
+  } else if (i == 0) {
+    Rs = sc * cv;
+    if (JAC) {
+      for (int q = 0; q < 9; ++q) Js[q][0] = Js[q][1] = 0.0;
+      Js[4][1] = sc;
+    }
+  }
+}
+
 // Residual (R^m, R^s) of vertex (j, i) of one sample and, if J is not NULL,
 // its Jacobian row blocks J[(dj + 1) * 3 + (di + 1)][eq][var] with respect to
 // (p, c) of vertex (j + dj, i + di) (36 doubles; zero for neighbours outside
@@ -152,17 +219,9 @@ __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C,
   double Rm = 0.0, Rs = 0.0;
   double Jm[9][2], Js[9][2];
   for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
-
-  // lumped storage
   const double cv = x[2 * idx(j, i) + 1], cvo = xo[2 * idx(j, i) + 1];
-  const double rho = P.rho0 + P.drho * cv, rho_o = P.rho0 + P.drho * cvo;
-  const int nel = (i > 0 && j > 0) + (i < P.nx && j > 0) + (i > 0 && j < P.ny) + (i < P.nx && j < P.ny);
-  const double wt = C.phi * nel * (0.25 * P.h * P.h) / P.tau;  // lumped phi |CV| / tau
+  vc_storage<JAC>(P, C, cv, cvo, j, i, Rm, Rs, Jm, Js);
   const double ih = 1.0 / P.h;
-  Rm += wt * (rho - rho_o);
-  Jm[4][1] += wt * P.drho;
-  Rs += wt * (rho * cv - rho_o * cvo);
-  Js[4][1] += wt * (rho + P.drho * cv);
 
   // the faces of the (up to four) elements this vertex is a corner of
   for (int kv = 0; kv < 4; ++kv) {
@@ -181,37 +240,10 @@ __host__ __device__ inline void vc_vertex_at(const VcParams& P, const VcCoef& C,
       double F, G, dF[8], dG[8];
       vc_face<JAC>(P, C, p, c, f, ih, F, dF, G, dG);
       const double sgn = (a == kv) ? 1.0 : -1.0;  // out of this vertex's volume
-      Rm += sgn * F;
-      Rs += sgn * G;
-      if (!JAC) continue;
-      for (int k = 0; k < 4; ++k) {
-        const int q = (ey + (k >> 1) - j + 1) * 3 + (ex + (k & 1) - i + 1);
-        Jm[q][0] += sgn * dF[k];
-        Jm[q][1] += sgn * dF[4 + k];
-        Js[q][0] += sgn * dG[k];
-        Js[q][1] += sgn * dG[4 + k];
-      }
+      vc_add_face<JAC>(sgn, (ey - j + 1) * 3 + (ex - i + 1), F, dF, G, dG, Rm, Rs, Jm, Js);
     }
   }
-
-  // inflow of fresh water through x = 0
-  if (i == 0) Rm -= P.rho0 * C.qin * ((j == 0 || j == P.ny) ? 0.5 * P.h : P.h);
-
-  // Dirichlet equations
-  const double sc = P.rho0 * P.h * P.h / P.tau;
-  if (i == P.nx) {
-    const double pb = P.rho1 * P.g * (P.Ly - j * P.h);
-    const double pscale = P.rho0 * P.g * P.Ly;
-    Rm = sc * (x[2 * idx(j, i)] - pb) / pscale;
-    Rs = sc * (cv - 1.0);
-    for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
-    Jm[4][0] = sc / pscale;
-    Js[4][1] = sc;
-  } else if (i == 0) {
-    Rs = sc * cv;
-    for (int q = 0; q < 9; ++q) Js[q][0] = Js[q][1] = 0.0;
-    Js[4][1] = sc;
-  }
+  vc_boundary<JAC>(P, C, x[2 * idx(j, i)], cv, j, i, Rm, Rs, Jm, Js);
 
   R[0] = Rm;
   R[1] = Rs;

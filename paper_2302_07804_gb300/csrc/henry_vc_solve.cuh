@@ -120,6 +120,166 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Face-once tile assembly (same arguments and outputs as k_vc_assemble_st).
+// A CTA takes TPB consecutive entries of the [B][stride] storage order.
+// Every face of the grid has one source corner, the vertex that owns it:
+//   E1 = element (j, i) face 0, E2 = element (j - 1, i) face 1 (both towards
+//   the east neighbour), N1 = element (j, i) face 2, N2 = element (j, i - 1)
+//   face 3 (both towards the north neighbour).
+// Phase 1: every vertex evaluates the faces it owns into shared memory.
+// Phase 2: every vertex adds its eight faces in vc_vertex_at's order - its
+// own four, its west neighbour's E1 and E2, its south neighbour's N1 and N2 -
+// read from shared memory, or evaluated again where the neighbour lies
+// outside the CTA's range.  About 4.3 face evaluations per vertex instead of
+// 8.  Vertices on x = Lx (Dirichlet in both equations) add no faces: their
+// rows are replaced anyway.  Shared memory: 4 x TPB face records.
+template <bool JAC>
+struct VcFaceRec {
+  double F, G, dF[JAC ? 8 : 1], dG[JAC ? 8 : 1];
+};
+
+template <bool JAC>
+__device__ __forceinline__ void vc_eval_face(const VcParams& P, const VcCoef& C, const double2* xs, int nxv, int ey,
+                                             int ex, int f, double ih, VcFaceRec<JAC>& r) {
+  double p[4], c[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 v = xs[vst(ey + (k >> 1), ex + (k & 1), nxv)];
+    p[k] = v.x;
+    c[k] = v.y;
+  }
+  vc_face<JAC>(P, C, p, c, f, ih, r.F, r.dF, r.G, r.dG);
+}
+
+template <typename T, bool FINE, bool JAC = true>
+__global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef* __restrict__ coef, int B,
+                                                          int stride, int64_t plane, double inv_s,
+                                                          const double2* __restrict__ x,
+                                                          const double2* __restrict__ xo,
+                                                          const int* __restrict__ active, double2* __restrict__ F,
+                                                          typename VT<T>::b4* __restrict__ J,
+                                                          double* __restrict__ rmax_part) {
+  typedef typename VT<T>::b4 B4;
+  typedef VcFaceRec<JAC> Rec;
+  extern __shared__ __align__(16) unsigned char vc_smem[];
+  Rec* rec = reinterpret_cast<Rec*>(vc_smem);  // [4][TPB]: E1, E2, N1, N2
+  __shared__ double sh[40];
+  const int nxv = P.nx + 1, NV = nxv * (P.ny + 1);
+  const int64_t t0 = (int64_t)blockIdx.x * TPB;
+  const int64_t e = t0 + threadIdx.x;
+  const int s = (int)(e / stride);
+  if (FINE) {
+    if (!active[s]) return;  // uniform over the CTA (stride % TPB == 0)
+  }
+  const bool on = FINE || (e < (int64_t)B * stride && active[s]);
+  const int st = (int)(e - (int64_t)s * stride);
+  const bool vtx = on && st < NV;
+  int j = 0, i = 0;
+  if (vtx) vxy(st, nxv, j, i);
+  const double2* xs = x + (int64_t)s * stride;
+  VcCoef C{0.0, 0.0, 0.0, 0.0};
+  if (vtx) {
+    const Coef cf = coef[s];
+    C = VcCoef{cf.phi, cf.kmu, cf.PD, cf.qin};
+  }
+  const double ih = 1.0 / P.h;
+  const int tid = threadIdx.x;
+  const bool faces = vtx && i < P.nx;  // x = Lx vertices own and add no face
+  if (faces) {
+    if (j < P.ny) {
+      vc_eval_face<JAC>(P, C, xs, nxv, j, i, 0, ih, rec[tid]);            // E1
+      vc_eval_face<JAC>(P, C, xs, nxv, j, i, 2, ih, rec[2 * TPB + tid]);  // N1
+      if (i > 0) vc_eval_face<JAC>(P, C, xs, nxv, j, i - 1, 3, ih, rec[3 * TPB + tid]);  // N2
+    }
+    if (j > 0) vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i, 1, ih, rec[TPB + tid]);  // E2
+  }
+  __syncthreads();
+  double Rm = 0.0, Rs = 0.0;
+  double Jm[9][2], Js[9][2];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Jm[q][0] = Jm[q][1] = Js[q][0] = Js[q][1] = 0.0;
+  if (vtx) {
+    const double2 xv = xs[st];
+    vc_storage<JAC>(P, C, xv.y, xo[(int64_t)s * stride + st].y, j, i, Rm, Rs, Jm, Js);
+    if (faces) {
+      // a neighbour's record: from shared memory if it is in this CTA's range
+      const int64_t ew = (i > 0) ? (int64_t)s * stride + vst(j, i - 1, nxv) - t0 : -1;
+      const int64_t es = (j > 0) ? (int64_t)s * stride + vst(j - 1, i, nxv) - t0 : -1;
+      const bool w_in = ew >= 0 && ew < TPB, s_in = es >= 0 && es < TPB;
+      Rec tmp;
+      if (j < P.ny) {  // element (j, i), corner 0
+        const Rec& e1 = rec[tid];
+        vc_add_face<JAC>(1.0, 4, e1.F, e1.dF, e1.G, e1.dG, Rm, Rs, Jm, Js);
+        const Rec& n1 = rec[2 * TPB + tid];
+        vc_add_face<JAC>(1.0, 4, n1.F, n1.dF, n1.G, n1.dG, Rm, Rs, Jm, Js);
+      }
+      if (j < P.ny && i > 0) {  // element (j, i - 1), corner 1
+        const Rec* w1 = &tmp;
+        if (w_in)
+          w1 = &rec[ew];
+        else
+          vc_eval_face<JAC>(P, C, xs, nxv, j, i - 1, 0, ih, tmp);
+        vc_add_face<JAC>(-1.0, 3, w1->F, w1->dF, w1->G, w1->dG, Rm, Rs, Jm, Js);
+        const Rec& n2 = rec[3 * TPB + tid];
+        vc_add_face<JAC>(1.0, 3, n2.F, n2.dF, n2.G, n2.dG, Rm, Rs, Jm, Js);
+      }
+      if (j > 0) {  // element (j - 1, i), corner 2
+        const Rec& e2 = rec[TPB + tid];
+        vc_add_face<JAC>(1.0, 1, e2.F, e2.dF, e2.G, e2.dG, Rm, Rs, Jm, Js);
+        const Rec* s1 = &tmp;
+        if (s_in)
+          s1 = &rec[2 * TPB + es];
+        else
+          vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i, 2, ih, tmp);
+        vc_add_face<JAC>(-1.0, 1, s1->F, s1->dF, s1->G, s1->dG, Rm, Rs, Jm, Js);
+      }
+      if (j > 0 && i > 0) {  // element (j - 1, i - 1), corner 3
+        const Rec* w2 = &tmp;
+        if (w_in)
+          w2 = &rec[TPB + ew];
+        else
+          vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i - 1, 1, ih, tmp);
+        vc_add_face<JAC>(-1.0, 0, w2->F, w2->dF, w2->G, w2->dG, Rm, Rs, Jm, Js);
+        const Rec* s2 = &tmp;
+        if (s_in)
+          s2 = &rec[3 * TPB + es];
+        else
+          vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i - 1, 3, ih, tmp);
+        vc_add_face<JAC>(-1.0, 0, s2->F, s2->dF, s2->G, s2->dG, Rm, Rs, Jm, Js);
+      }
+    }
+    vc_boundary<JAC>(P, C, xv.x, xv.y, j, i, Rm, Rs, Jm, Js);
+  }
+  if (FINE) {
+    const double fm = Rm * inv_s, fs = Rs * inv_s;
+    F[e] = make_double2(fm, fs);
+    double loc = fmax(fabs(fm), fabs(fs));
+    if (!(loc <= 1.0e300)) loc = INFINITY;
+    const double bm = block_max_nonneg(loc, sh);
+    if (threadIdx.x == 0) rmax_part[(int64_t)s * (stride / TPB) + st / TPB] = bm;
+  }
+  if (JAC && J && on) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      J[q * plane + e] = mkblk<B4>((T)(Jm[q][0] * inv_s), (T)(Jm[q][1] * inv_s), (T)(Js[q][0] * inv_s),
+                                   (T)(Js[q][1] * inv_s));
+    B4 inv = mkblk<B4>((T)0, (T)0, (T)0, (T)0);
+    if (vtx) {
+      const double a = Jm[4][0] * inv_s, b = Jm[4][1] * inv_s, c = Js[4][0] * inv_s, d = Js[4][1] * inv_s;
+      const double idet = 1.0 / (a * d - b * c);
+      inv = mkblk<B4>((T)(d * idet), (T)(-b * idet), (T)(-c * idet), (T)(a * idet));
+    }
+    J[9 * plane + e] = inv;
+  }
+}
+
+// Dynamic shared memory of k_vc_assemble_tile.
+template <bool JAC>
+constexpr int vc_tile_smem() {
+  return 4 * TPB * (int)sizeof(VcFaceRec<JAC>);
+}
+
 // Coarse states by injection: x_c(J, I) = x_f(2J, 2I), for the iterate and
 // (old != 0) the old state.
 __global__ void __launch_bounds__(TPB) k_vc_inject(int B, int ncx, int ncy, int stride_f, int stride_c,

@@ -295,3 +295,56 @@ def test_vc_level_tuning_applies_and_autotune_runs(hl):
     assert int(st.abs().sum()) == 0
     _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
     s.close()
+
+
+@pytest.mark.parametrize("level", [0, 2])
+def test_vc_face_once_assembly_matches_per_vertex_kernel_and_oracle(hl, level):
+    """The face-once tile assembly (the default: each element face evaluated
+    once by its source vertex and shared through shared memory, faces of
+    neighbours outside the CTA's range evaluated again) against the
+    one-thread-per-vertex kernel (tile_assembly = 0) and the oracle.  Level 2
+    (129 x 65 vertices) has CTA ranges that cut rows, so both the shared and
+    the re-evaluated neighbour faces are taken.  The two kernels add the same
+    faces in the same order; the compiler may contract multiply-adds
+    differently in each, so they are compared at 1e-14 of each quantity's
+    scale, the oracle at the assembly tests' tolerances.  The residual alone
+    (with_jacobian False) equals the residual assembled with the Jacobian."""
+    prm = vc.Params()
+    grid = vc.Grid.level(prm, level)
+    xi = inputs.uniform_xi(990 + level, 3)
+    states = [random_states(grid, 100 + k, 300.0) for k in range(3)]
+    olds = [random_states(grid, 110 + k, 300.0) for k in range(3)]
+    st = _dev(np.stack([np.stack(a, axis=-1) for a in states]))
+    so = _dev(np.stack([np.stack(a, axis=-1) for a in olds]))
+    a, b = _vc_solver(hl), _vc_solver(hl, tile_assembly=0)
+    Fa, Ja = a.assemble(level, _dev(xi), st, so)
+    Fb, Jb = b.assemble(level, _dev(xi), st, so)
+    Fr, _ = a.assemble(level, _dev(xi), st, so, with_jacobian=False)
+    assert torch.equal(Fr, Fa)
+    Fa, Ja, Fb, Jb = (t.cpu().numpy() for t in (Fa, Ja, Fb, Jb))
+    for eq in (0, 1):
+        np.testing.assert_allclose(Fa[..., eq], Fb[..., eq], rtol=0, atol=1e-14 * np.abs(Fb[..., eq]).max())
+    for q in range(9):
+        for eq in (0, 1):
+            for var in (0, 1):
+                sc = np.abs(Jb[..., q, eq, var]).max()
+                np.testing.assert_allclose(Ja[..., q, eq, var], Jb[..., q, eq, var], rtol=0,
+                                           atol=1e-14 * max(sc, 1e-300))
+    sc = vc.residual_scale(prm, grid)
+    for k in range(3):
+        coef = cc.coefficients(prm, grid, xi[k])
+        (p, c), (po, co) = states[k], olds[k]
+        Rm, Rs = vc.residual(prm, grid, coef, p, c, po, co)
+        Jo = blocks_from_sparse(vc.jacobian(prm, grid, coef, p, c, po, co), grid) / sc
+        fl = vc.face_fluxes(prm, grid, coef, p, c)
+        sm = max(max(np.abs(F).max() for _, _, F, _ in fl), sc)
+        ss = max(max(np.abs(G).max() for _, _, _, G in fl), sc)
+        np.testing.assert_allclose(Fa[k, ..., 0], Rm / sc, rtol=0, atol=1e-12 * sm / sc)
+        np.testing.assert_allclose(Fa[k, ..., 1], Rs / sc, rtol=0, atol=1e-12 * ss / sc)
+        for eq in (0, 1):
+            for var in (0, 1):
+                scj = np.abs(Jo[..., eq, var]).max()
+                np.testing.assert_allclose(Ja[k].reshape(Jo.shape)[..., eq, var], Jo[..., eq, var], rtol=0,
+                                           atol=1e-11 * scj)
+    a.close()
+    b.close()
