@@ -1241,9 +1241,11 @@ size_t vc_bytes_per_sample(const henry_config& c, int level) {
   return g.carve(nullptr, 1, lg.nx, lg.ny, lg.h);
 }
 
-// The face-once vertex assembly needs 147 KB of dynamic shared memory with
-// the Jacobian (the per-vertex kernel is used where the device grants less).
-bool vc_tile_fits() { return smem_optin() >= vc_tile_smem<true>() + 1024; }
+// The face-once vertex assembly: 128-thread CTAs with 73.7 KB of dynamic
+// shared memory with the Jacobian (the per-vertex kernel is used where the
+// device grants less).
+constexpr int VC_TILE_NT = 128;
+bool vc_tile_fits() { return smem_optin() >= vc_tile_smem<true, VC_TILE_NT>() + 1024; }
 template <typename T>
 int ensure_vc_tile_attr() {
   static std::atomic<int> done[64] = {};
@@ -1251,28 +1253,30 @@ int ensure_vc_tile_attr() {
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_err(HENRY_EINVAL, "device %d outside [0, 64)", dev);
   if (done[dev].load(std::memory_order_relaxed) || !vc_tile_fits()) return HENRY_OK;
-  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          vc_tile_smem<true>()));
-  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          vc_tile_smem<true>()));
+  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, true, true, VC_TILE_NT>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, vc_tile_smem<true, VC_TILE_NT>()));
+  CK(cudaFuncSetAttribute(k_vc_assemble_tile<T, false, true, VC_TILE_NT>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, vc_tile_smem<true, VC_TILE_NT>()));
   done[dev].store(1, std::memory_order_relaxed);
   return HENRY_OK;
 }
 
 // Residual (and with JAC the Jacobian) of every vertex of a level: the
 // face-once tile kernel with tile_assembly (default), else one thread per
-// vertex evaluating its eight faces.  Same arguments and outputs.
+// vertex evaluating its eight faces.  Same arguments and outputs, except the
+// granularity of FINE's per-CTA maxima (vc_max_parts).
+bool vc_use_tile(const henry_config& c) { return c.tile_assembly && vc_tile_fits(); }
 template <typename T, bool FINE, bool JAC = true>
 void vc_assemble_launch(const henry_config& c, cudaStream_t st, const VcParams& P, const Coef* coef, int B,
                         int stride, int64_t plane, double inv_s, const double2* x, const double2* xo,
                         const int* active, double2* F, typename VT<T>::b4* J, double* rmax_part) {
-  const unsigned g = nblk((int64_t)B * stride);
-  if (c.tile_assembly && vc_tile_fits())
-    k_vc_assemble_tile<T, FINE, JAC><<<g, TPB, vc_tile_smem<JAC>(), st>>>(P, coef, B, stride, plane, inv_s, x, xo,
-                                                                          active, F, J, rmax_part);
+  if (vc_use_tile(c))
+    k_vc_assemble_tile<T, FINE, JAC, VC_TILE_NT>
+        <<<nblk((int64_t)B * stride, VC_TILE_NT), VC_TILE_NT, vc_tile_smem<JAC, VC_TILE_NT>(), st>>>(
+            P, coef, B, stride, plane, inv_s, x, xo, active, F, J, rmax_part);
   else
-    k_vc_assemble_st<T, FINE, JAC><<<g, TPB, 0, st>>>(P, coef, B, stride, plane, inv_s, x, xo, active, F, J,
-                                                      rmax_part);
+    k_vc_assemble_st<T, FINE, JAC><<<nblk((int64_t)B * stride), TPB, 0, st>>>(P, coef, B, stride, plane, inv_s, x,
+                                                                              xo, active, F, J, rmax_part);
 }
 
 template <typename T>
@@ -1521,24 +1525,40 @@ int vc_linear_solve(henry_handle* H, VcGroup<T>& G, int B, cudaStream_t st, doub
   return HENRY_OK;
 }
 
+// Where the fine assembly leaves its per-CTA maxima of |F| and how many a
+// sample has: the P_MAX partials (nct per sample) for the per-vertex kernel;
+// for the tile kernel's 128-entry CTAs (2 nct per sample) the P_RR and P_RN
+// partials, which are free between an assembly and the residual test and
+// are rewritten by the next Krylov solve.
+template <typename T>
+double* vc_max_parts(const henry_handle* H, VcGroup<T>& G, int B, int* nct) {
+  if (vc_use_tile(H->cfg)) {
+    *nct = G.nct * (TPB / VC_TILE_NT);
+    return G.part + P_RR * (int64_t)B * G.nct;
+  }
+  *nct = G.nct;
+  return G.part + P_MAX * (int64_t)B * G.nct;
+}
+
 // Fine residual and Jacobian (scaled by inv_s; jac = false: the residual
 // alone) of the samples with newton_active set, with the per-CTA max |F|
-// into P_MAX.
+// into vc_max_parts.
 template <typename T>
 int vc_assemble_fine(henry_handle* H, VcGroup<T>& G, int B, double tau, double inv_s, cudaStream_t st,
                      bool jac = true) {
   typedef typename VT<T>::b4 B4;
   auto& L = G.lv[0];
+  int nct_max = 0;
+  double* pm = vc_max_parts<T>(H, G, B, &nct_max);
   if (jac)
     launch(H, st, HENRY_K_ASSEMBLE, (double)H->nact * L.NV * (48.0 + 10.0 * sizeof(B4)), [&] {
       vc_assemble_launch<T, true>(H->cfg, st, vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s, L.x,
-                                  L.xo, G.newton_active, G.F, (B4*)L.J, G.part + P_MAX * (int64_t)B * G.nct);
+                                  L.xo, G.newton_active, G.F, (B4*)L.J, pm);
     });
   else
     launch(H, st, HENRY_K_RESIDUAL, (double)H->nact * L.NV * 48.0, [&] {
       vc_assemble_launch<T, true, false>(H->cfg, st, vc_params<T>(H->cfg, L, tau), G.coef, B, L.stride, L.plane, inv_s,
-                                         L.x, L.xo, G.newton_active, G.F, nullptr,
-                                         G.part + P_MAX * (int64_t)B * G.nct);
+                                         L.x, L.xo, G.newton_active, G.F, nullptr, pm);
     });
   CKL();
   return HENRY_OK;
@@ -1577,8 +1597,10 @@ int vc_implicit_step(henry_handle* H, VcGroup<T>& G, int B, int step, cudaStream
     CK(cudaMemsetAsync(G.counter, 0, sizeof(int), st));
     rc = vc_assemble_fine<T>(H, G, B, lg.tau, inv_s, st, !res_first);
     if (rc) return rc;
-    launch(H, st, HENRY_K_NEWTON, (double)B * 8 * G.nct, [&] {
-      k_newton_res_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, G.nct, c.newton_atol, c.newton_maxit, pmax,
+    int nct_f = 0;
+    const double* fmax_parts = vc_max_parts<T>(H, G, B, &nct_f);
+    launch(H, st, HENRY_K_NEWTON, (double)B * 8 * nct_f, [&] {
+      k_newton_res_check<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(B, nct_f, c.newton_atol, c.newton_maxit, fmax_parts,
                                                        G.newton_active, G.lin_active, G.newton_it, G.status,
                                                        G.counter, G.totals);
     });

@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
 }
 
 // ---------------------------------------------------------------------------
-// Face-once tile assembly (same arguments and outputs as k_vc_assemble_st).
-// A CTA takes TPB consecutive entries of the [B][stride] storage order.
+// Face-once tile assembly (same arguments and outputs as k_vc_assemble_st,
+// except that FINE's per-CTA maxima of |F| are per NT entries:
+// rmax_part[s][stride / NT]).  A CTA of NT threads takes NT consecutive
+// entries of the [B][stride] storage order.
 // Every face of the grid has one source corner, the vertex that owns it:
 //   E1 = element (j, i) face 0, E2 = element (j - 1, i) face 1 (both towards
 //   the east neighbour), N1 = element (j, i) face 2, N2 = element (j, i - 1)
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_st(VcParams P, const Coef* 
 // read from shared memory, or evaluated again where the neighbour lies
 // outside the CTA's range.  About 4.3 face evaluations per vertex instead of
 // 8.  Vertices on x = Lx (Dirichlet in both equations) add no faces: their
-// rows are replaced anyway.  Shared memory: 4 x TPB face records.
+// rows are replaced anyway.  Shared memory: 4 x NT face records (73.7 KB
+// for NT = 128 with the Jacobian, so that three CTAs share an SM).
 template <bool JAC>
 struct VcFaceRec {
   double F, G, dF[JAC ? 8 : 1], dG[JAC ? 8 : 1];
@@ -152,8 +155,8 @@ __device__ __forceinline__ void vc_eval_face(const VcParams& P, const VcCoef& C,
   vc_face<JAC>(P, C, p, c, f, ih, r.F, r.dF, r.G, r.dG);
 }
 
-template <typename T, bool FINE, bool JAC = true>
-__global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef* __restrict__ coef, int B,
+template <typename T, bool FINE, bool JAC = true, int NT = 128>
+__global__ void __launch_bounds__(NT) k_vc_assemble_tile(VcParams P, const Coef* __restrict__ coef, int B,
                                                           int stride, int64_t plane, double inv_s,
                                                           const double2* __restrict__ x,
                                                           const double2* __restrict__ xo,
@@ -163,14 +166,14 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
   typedef typename VT<T>::b4 B4;
   typedef VcFaceRec<JAC> Rec;
   extern __shared__ __align__(16) unsigned char vc_smem[];
-  Rec* rec = reinterpret_cast<Rec*>(vc_smem);  // [4][TPB]: E1, E2, N1, N2
+  Rec* rec = reinterpret_cast<Rec*>(vc_smem);  // [4][NT]: E1, E2, N1, N2
   __shared__ double sh[40];
   const int nxv = P.nx + 1, NV = nxv * (P.ny + 1);
-  const int64_t t0 = (int64_t)blockIdx.x * TPB;
+  const int64_t t0 = (int64_t)blockIdx.x * NT;
   const int64_t e = t0 + threadIdx.x;
   const int s = (int)(e / stride);
   if (FINE) {
-    if (!active[s]) return;  // uniform over the CTA (stride % TPB == 0)
+    if (!active[s]) return;  // uniform over the CTA (stride % NT == 0)
   }
   const bool on = FINE || (e < (int64_t)B * stride && active[s]);
   const int st = (int)(e - (int64_t)s * stride);
@@ -189,10 +192,10 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
   if (faces) {
     if (j < P.ny) {
       vc_eval_face<JAC>(P, C, xs, nxv, j, i, 0, ih, rec[tid]);            // E1
-      vc_eval_face<JAC>(P, C, xs, nxv, j, i, 2, ih, rec[2 * TPB + tid]);  // N1
-      if (i > 0) vc_eval_face<JAC>(P, C, xs, nxv, j, i - 1, 3, ih, rec[3 * TPB + tid]);  // N2
+      vc_eval_face<JAC>(P, C, xs, nxv, j, i, 2, ih, rec[2 * NT + tid]);  // N1
+      if (i > 0) vc_eval_face<JAC>(P, C, xs, nxv, j, i - 1, 3, ih, rec[3 * NT + tid]);  // N2
     }
-    if (j > 0) vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i, 1, ih, rec[TPB + tid]);  // E2
+    if (j > 0) vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i, 1, ih, rec[NT + tid]);  // E2
   }
   __syncthreads();
   double Rm = 0.0, Rs = 0.0;
@@ -206,12 +209,12 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
       // a neighbour's record: from shared memory if it is in this CTA's range
       const int64_t ew = (i > 0) ? (int64_t)s * stride + vst(j, i - 1, nxv) - t0 : -1;
       const int64_t es = (j > 0) ? (int64_t)s * stride + vst(j - 1, i, nxv) - t0 : -1;
-      const bool w_in = ew >= 0 && ew < TPB, s_in = es >= 0 && es < TPB;
+      const bool w_in = ew >= 0 && ew < NT, s_in = es >= 0 && es < NT;
       Rec tmp;
       if (j < P.ny) {  // element (j, i), corner 0
         const Rec& e1 = rec[tid];
         vc_add_face<JAC>(1.0, 4, e1.F, e1.dF, e1.G, e1.dG, Rm, Rs, Jm, Js);
-        const Rec& n1 = rec[2 * TPB + tid];
+        const Rec& n1 = rec[2 * NT + tid];
         vc_add_face<JAC>(1.0, 4, n1.F, n1.dF, n1.G, n1.dG, Rm, Rs, Jm, Js);
       }
       if (j < P.ny && i > 0) {  // element (j, i - 1), corner 1
@@ -221,15 +224,15 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
         else
           vc_eval_face<JAC>(P, C, xs, nxv, j, i - 1, 0, ih, tmp);
         vc_add_face<JAC>(-1.0, 3, w1->F, w1->dF, w1->G, w1->dG, Rm, Rs, Jm, Js);
-        const Rec& n2 = rec[3 * TPB + tid];
+        const Rec& n2 = rec[3 * NT + tid];
         vc_add_face<JAC>(1.0, 3, n2.F, n2.dF, n2.G, n2.dG, Rm, Rs, Jm, Js);
       }
       if (j > 0) {  // element (j - 1, i), corner 2
-        const Rec& e2 = rec[TPB + tid];
+        const Rec& e2 = rec[NT + tid];
         vc_add_face<JAC>(1.0, 1, e2.F, e2.dF, e2.G, e2.dG, Rm, Rs, Jm, Js);
         const Rec* s1 = &tmp;
         if (s_in)
-          s1 = &rec[2 * TPB + es];
+          s1 = &rec[2 * NT + es];
         else
           vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i, 2, ih, tmp);
         vc_add_face<JAC>(-1.0, 1, s1->F, s1->dF, s1->G, s1->dG, Rm, Rs, Jm, Js);
@@ -237,13 +240,13 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
       if (j > 0 && i > 0) {  // element (j - 1, i - 1), corner 3
         const Rec* w2 = &tmp;
         if (w_in)
-          w2 = &rec[TPB + ew];
+          w2 = &rec[NT + ew];
         else
           vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i - 1, 1, ih, tmp);
         vc_add_face<JAC>(-1.0, 0, w2->F, w2->dF, w2->G, w2->dG, Rm, Rs, Jm, Js);
         const Rec* s2 = &tmp;
         if (s_in)
-          s2 = &rec[3 * TPB + es];
+          s2 = &rec[3 * NT + es];
         else
           vc_eval_face<JAC>(P, C, xs, nxv, j - 1, i - 1, 3, ih, tmp);
         vc_add_face<JAC>(-1.0, 0, s2->F, s2->dF, s2->G, s2->dG, Rm, Rs, Jm, Js);
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
     double loc = fmax(fabs(fm), fabs(fs));
     if (!(loc <= 1.0e300)) loc = INFINITY;
     const double bm = block_max_nonneg(loc, sh);
-    if (threadIdx.x == 0) rmax_part[(int64_t)s * (stride / TPB) + st / TPB] = bm;
+    if (threadIdx.x == 0) rmax_part[(int64_t)s * (stride / NT) + st / NT] = bm;
   }
   if (JAC && J && on) {
 #pragma unroll
@@ -275,9 +278,9 @@ __global__ void __launch_bounds__(TPB) k_vc_assemble_tile(VcParams P, const Coef
 }
 
 // Dynamic shared memory of k_vc_assemble_tile.
-template <bool JAC>
+template <bool JAC, int NT = 128>
 constexpr int vc_tile_smem() {
-  return 4 * TPB * (int)sizeof(VcFaceRec<JAC>);
+  return 4 * NT * (int)sizeof(VcFaceRec<JAC>);
 }
 
 // Coarse states by injection: x_c(J, I) = x_f(2J, 2I), for the iterate and
