@@ -176,9 +176,10 @@ typedef struct {
                             sample down to the coarsest run as one kernel, one CTA per sample with those
                             levels' vectors in shared memory, and their operators too where they fit beside
                             them (the finest tail levels' operators are otherwise read from global memory at
-                            each use); -1 (default): 2048 cells (64 x 32) with FP32 linear algebra, 128
-                            (16 x 8) with FP64, the faster choice measured on small batches of each; 0: every
-                            level as separate kernels.  Same values either way */
+                            each use); -1 (default): 2048 cells (64 x 32) with FP32 linear algebra on fine grids
+                            of 128 x 64 cells or more, else 128 (16 x 8), the faster choice measured on the
+                            MLMC levels' batches; 0: every level as separate kernels.  Same values either
+                            way */
   int32_t mg_tail_batch_cells; /* ... only while the batch times that level's cells per sample is at most this
                                   (default 2^20; 0: no limit): large batches of small grids run those levels
                                   as separate, large launches */

@@ -505,6 +505,12 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
   return L->bytes <= optin;
 }
 
+int smem_optin();
+// Dynamic shared memory the tail kernel may use: the opt-in limit less a
+// reserve for static shared memory.
+constexpr int TAIL_STATIC_RESERVE = 256;
+int tail_dyn_max() { return std::max(0, smem_optin() - TAIL_STATIC_RESERVE); }
+
 // The device's opt-in shared memory per CTA (cached per device; 0 on error).
 int smem_optin() {
   int dev = 0;
@@ -526,8 +532,8 @@ int ensure_tail_attr() {
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return set_err(HENRY_EINVAL, "device %d outside [0, 64)", dev);
   if (done[dev].load(std::memory_order_relaxed)) return HENRY_OK;
-  const int optin = smem_optin();
-  if (optin > 0) CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  const int dmax = tail_dyn_max();
+  if (dmax > 0) CK(cudaFuncSetAttribute(k_vcycle_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, dmax));
   done[dev].store(1, std::memory_order_relaxed);
   return HENRY_OK;
 }
@@ -721,14 +727,16 @@ int restrict_states(henry_handle* H, Group<T>& G, int B, bool old, const int* ac
 
 // First multigrid level of the fused tail: the first coarse level (k >= 1)
 // with at most mg_tail_cells cells per sample (-1: 2048 with FP32 linear
-// algebra, 128 with FP64, as measured), if the tail below it has at
+// algebra on fine grids of 128 x 64 cells or more, else 128, as measured),
+// if the tail below it has at
 // least two levels, its shared-memory layout fits and the batch is small
 // enough (B x cells of that level <= mg_tail_batch_cells; larger batches keep
 // those levels as separate kernels, which then are large launches and fill
 // the FP64 pipe better than the tail's partly idle warps); -1: no tail.
 template <typename T>
 int tail_level(const henry_config& c, const Group<T>& G, int B, CtaLayout* L) {
-  const int cells = c.mg_tail_cells < 0 ? (sizeof(T) == sizeof(float) ? 2048 : 128) : c.mg_tail_cells;
+  const int cells =
+      c.mg_tail_cells >= 0 ? c.mg_tail_cells : (sizeof(T) == sizeof(float) && G.lv[0].N >= 8192 ? 2048 : 128);
   if (cells <= 0) return -1;
   for (int k = 1; k < G.K; ++k) {
     if (G.lv[k].N > cells) continue;
@@ -736,7 +744,7 @@ int tail_level(const henry_config& c, const Group<T>& G, int B, CtaLayout* L) {
     // the finest tail levels read their operators from global memory (L2)
     // when the layout does not fit otherwise
     for (int ns = 0; ns < G.K - k; ++ns)
-      if (tail_layout(G.lv[k].nx, G.lv[k].ny, (int)sizeof(T), L, ns) && L->bytes <= smem_optin()) return k;
+      if (tail_layout(G.lv[k].nx, G.lv[k].ny, (int)sizeof(T), L, ns) && L->bytes <= tail_dyn_max()) return k;
     return -1;
   }
   return -1;

@@ -447,15 +447,16 @@ def test_fused_multigrid_tail_is_bit_identical(hl, precision):
     """The V-cycle's coarse levels run as one kernel per cycle (one CTA per
     sample, operators in shared memory) compute exactly what the level-by-
     level kernels compute: one V-cycle at levels 0, 2 and 4 and full solves
-    with coarse partners are bit-identical with the tail on (the default,
-    from 32 x 16 cells, and from 64 x 32 cells, whose block planes do not fit
-    in shared memory beside the vectors and are read from global memory) and
-    off."""
+    with coarse partners are bit-identical with the tail on (from 4 x 2, 8 x
+    4, 16 x 8 and 32 x 16 cells, and from 64 x 32 cells, whose block planes
+    do not fit in shared memory beside the vectors and are read from global
+    memory) and off."""
     for level in (0, 2, 4):
-        grid, xi, p, c, po, co = _random_case(880 + level, level, 2)
-        b = inputs.random_vectors(881 + level, 2, grid.ny, grid.nx)
+        n = 5 if level < 4 else 2
+        grid, xi, p, c, po, co = _random_case(880 + level, level, n)
+        b = inputs.random_vectors(881 + level, n, grid.ny, grid.nx)
         zs = []
-        for tail in (0, 128, 512, 2048):
+        for tail in (0, 8, 32, 128, 512, 2048):
             s = hl.Solver(mg_tail_cells=tail, precision=precision)
             zs.append(s.precondition(level, _to_dev(xi), _to_dev(_states_np(p, c)), _to_dev(_states_np(po, co)),
                                      _to_dev(b)))
@@ -464,8 +465,8 @@ def test_fused_multigrid_tail_is_bit_identical(hl, precision):
             assert torch.equal(z, zs[0]), level
     xi = hl.sample_xi(inputs.SEED, 2, 5100, 4)
     q = []
-    for tail in (0, 128, 2048):
-        s = hl.Solver(mg_tail_cells=tail, precision=precision, fused_small_grids=0)
+    for tail in (0, 32, 128, 2048):
+        s = hl.Solver(mg_tail_cells=tail, precision=precision, fused_small_grids=0, mg_tail_batch_cells=0)
         qf, qc, st, stats = s.level_batch_solve(2, xi, with_coarse=True)
         q.append((qf, qc, st, stats["linear_iters"]))
         s.close()
