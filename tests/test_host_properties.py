@@ -91,8 +91,11 @@ def test_kl_basis_agrees_with_the_oracle_to_its_conditioning(henry, ell, terms):
     for any correlation length and number of terms.  Eigenvalues far below
     the largest are fixed only to rounding of the largest, and so are their
     modes, so the comparison is absolute in lam_max: the eigenvalues to
-    1e-13 lam_max, and the field contributions sqrt(lam_k) psi_k to
-    1e-9 sqrt(lam_max)."""
+    1e-13 lam_max, the field contributions sqrt(lam_k) psi_k of the terms
+    with lam_k >= 1e-12 lam_max to 1e-9 sqrt(lam_max), and those of the
+    terms below, whose eigenvalues lie within rounding of zero (long
+    correlation lengths with many terms, e.g. 1.125 with 56), to
+    1e-6 sqrt(lam_max) = sqrt(1e-12 lam_max) times the modes' unit scale."""
     from oracle import henry as oh
     from oracle import kl as okl
     sl, modes = henry.kl_basis(0, kl_terms=terms, kl_corr_len=ell)
@@ -104,7 +107,11 @@ def test_kl_basis_agrees_with_the_oracle_to_its_conditioning(henry, ell, terms):
     assert np.abs(sl ** 2 - b.lam).max() <= 1e-13 * lmax
     f_lib = sl[:, None, None] * modes
     f_orc = np.sqrt(b.lam)[:, None, None] * b.modes(xc, yc)
-    assert np.abs(f_lib - f_orc).max() <= 1e-9 * np.sqrt(lmax)
+    d = np.abs(f_lib - f_orc).reshape(terms, -1).max(axis=1)
+    resolved = b.lam >= 1e-12 * lmax
+    assert d[resolved].max() <= 1e-9 * np.sqrt(lmax)
+    if (~resolved).any():
+        assert d[~resolved].max() <= 1e-6 * np.sqrt(lmax)
 
 
 ints = st.one_of(st.integers(min_value=-3, max_value=70), st.sampled_from([0, 1 << 20, 1 << 29, (1 << 31) - 1, -(1 << 31)]))
