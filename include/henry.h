@@ -145,8 +145,8 @@ typedef struct {
   double lin_rtol;     /* BiCGStab: ||r||_2 <= lin_rtol ||b||_2 per sample (default 1e-4: inexact Newton) */
   int32_t newton_maxit, lin_maxit, nu1, nu2; /* caps; pre/post smoothing sweeps of the V-cycle */
   double workspace_bytes;                    /* device workspace budget per batch (chunking) */
-  double newton_predictor; /* Newton's first iterate of step n+1: x^n + w (x^n - x^{n-1}), w in [0, 1]
-                              (0: x^n; default 1, linear extrapolation in time) */
+  double newton_predictor; /* weight w in [0, 1] of the time predictor of Newton's first iterate of step
+                              n+1 (0: x^n; default 1: the full extrapolation of newton_predictor_order) */
   double newton_dc_limit;  /* Newton steps with max |dc| > limit are scaled down to it (default 1; 0: off) */
   int32_t fused_small_grids; /* grids of <= 512 cells solved by one CTA per sample with the whole hierarchy in
                                 shared memory: 1 (default) in HENRY_MIXED only, 2 also in HENRY_FP64,
@@ -201,6 +201,12 @@ typedef struct {
   int32_t mg_threads; /* threads per CTA of the multigrid smoother, restriction and prolongation kernels of
                          the cell-centred scheme: 64, 128, 256 or 512 (0, the default: 256).  Identical
                          values for every size */
+  int32_t newton_predictor_order; /* Newton's first iterate of step n+1 (with weight newton_predictor): 1
+                                     linear extrapolation from x^n and x^{n-1}; 2 (default) quadratic, x^n +
+                                     w (2 (x^n - x^{n-1}) - (x^{n-1} - x^{n-2})), from step 2 on (linear at
+                                     step 1).  Every solve path and henry_adjoint (whose checkpoints then hold
+                                     three states) follow it.  The FP64 residual test decides convergence
+                                     either way */
 } henry_config;
 
 /* Iteration statistics of one henry_level_batch_solve call (host struct). */
@@ -229,8 +235,9 @@ void henry_paper_config(henry_config* cfg);
  * the fused multigrid tail (mg_tail_cells in {0, 32, 128, 512, 2048}), the
  * residual-first Newton test (newton_residual_first in {-1, 2, 3, 4}), chord
  * Newton (newton_jacobian_every in {1, 2, 3}), the assembly tile
- * (assembly_tile_w in {0, 32, 64, 128, 256} where it divides the grid) and the
- * multigrid kernels' CTA size (mg_threads in {64, 128, 256, 512}).
+ * (assembly_tile_w in {0, 32, 64, 128, 256} where it divides the grid), the
+ * multigrid kernels' CTA size (mg_threads in {64, 128, 256, 512}) and the
+ * order of Newton's time predictor (newton_predictor_order in {1, 2}).
  * henry_autotune times every candidate - first lin_rtol in {1e-4, 1e-3,
  * 1e-2} x (nu1, nu2) in {(2,2), (1,2), (2,1)} x (fused small-grid solver on /
  * off where eligible), then the later stages - on n_trial samples
@@ -249,6 +256,7 @@ typedef struct {
   double cell_steps_per_s; /* measured on the trial batch (0 for the configuration's own settings) */
   int32_t mg_tail_cells, newton_residual_first, newton_jacobian_every; /* as in henry_config */
   int32_t assembly_tile_w, mg_threads;                                 /* as in henry_config */
+  int32_t newton_predictor_order; /* as in henry_config (0: the configuration's) */
 } henry_tuning;
 int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi_dev, int n_trial,
                    henry_tuning* best_out, void* stream);

@@ -78,6 +78,7 @@ struct CtaParams {
   Phys ph;
   int nx0, ny0, steps, nu1, nu2, newton_maxit, lin_maxit;
   double h0, tau, inv_s, inv_pref, atol, dxtol, rtol2, predictor, dc_limit;
+  int predictor_order;  // 1: linear, 2: quadratic from step 2 on (xoo_g holds x^{n-2})
   double rho0g, Ly;
 };
 
@@ -253,14 +254,16 @@ __device__ void cta_coarse_inverse(const CtaSmem<T>& S) {
 }
 
 // The fused scenario solve: one CTA per sample.  xo_g: the sample's old state
-// in global memory ([B][N0] double2, storage layout); qoi[B][2]; status[B]
+// in global memory ([B][N0] double2, storage layout), xoo_g the state before
+// it (quadratic predictor; may be NULL with predictor_order 1); qoi[B][2]; status[B]
 // (0 on entry for samples to solve).  totals[0] += Newton iterations,
 // totals[1] += BiCGStab iterations.
 template <typename T>
 __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant__ CtaParams P,
                                                            const __grid_constant__ CtaLayout L, int B,
                                                            const Coef* __restrict__ coef,
-                                                           double2* __restrict__ xo_g, double* __restrict__ qoi,
+                                                           double2* __restrict__ xo_g, double2* __restrict__ xoo_g,
+                                                           double* __restrict__ qoi,
                                                            int* __restrict__ status,
                                                            unsigned long long* __restrict__ totals) {
   typedef typename VT<T>::v2 V2;
@@ -283,6 +286,8 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant
   const int nx0 = P.nx0, ny0 = P.ny0, N0 = nx0 * ny0, K = L.K;
   const Coef cf = coef[s];
   double2* xo = xo_g + (int64_t)s * N0;
+  const bool quad = P.predictor_order == 2 && xoo_g;
+  double2* xoo = quad ? xoo_g + (int64_t)s * N0 : nullptr;
   double2* x = S.X(0);
   V2 *r = S.vec(L.r), *rh = S.vec(L.rh), *p = S.vec(L.p), *v = S.vec(L.v), *t = S.vec(L.t);
   V2 *ph = S.vec(L.ph), *dx = S.vec(L.dx);
@@ -296,6 +301,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant
     const double2 v0 = make_double2(P.rho0g * (P.Ly - (iy + 0.5) * P.h0), 0.0);
     x[i] = v0;
     xo[i] = v0;
+    if (quad) xoo[i] = v0;
   }
   __syncthreads();
 
@@ -303,9 +309,18 @@ __global__ void __launch_bounds__(CTA_THREADS) k_cta_solve(const __grid_constant
     // a10: x_old <- x (and Newton's first iterate by the predictor)
     for (int i = threadIdx.x; i < N0; i += blockDim.x) {
       const double2 a = x[i], b = xo[i];
+      double2 c = b;
+      if (quad) {
+        c = xoo[i];
+        xoo[i] = b;
+      }
       xo[i] = a;
-      if (step > 0 && P.predictor > 0.0)
+      if (quad && step > 1 && P.predictor > 0.0) {  // as k_step_begin_predict2
+        const double dx = 2.0 * (a.x - b.x) - (b.x - c.x), dy = 2.0 * (a.y - b.y) - (b.y - c.y);
+        x[i] = make_double2(fma(P.predictor, dx, a.x), fma(P.predictor, dy, a.y));
+      } else if (step > 0 && P.predictor > 0.0) {
         x[i] = make_double2(fma(P.predictor, a.x - b.x, a.x), fma(P.predictor, a.y - b.y, a.y));
+      }
     }
     __syncthreads();
     // restricted old states of the coarse levels

@@ -101,6 +101,7 @@ struct Group {
   size_t bytes = 0;
   std::vector<Level> lv;
   double2* F = nullptr;
+  double2* xoo = nullptr;  // fine state x^{n-2} (the quadratic predictor)
   V2 *r, *rh, *p, *v, *s, *t, *ph, *sh, *dx;
   Coef* coef;
   double* part;
@@ -159,6 +160,7 @@ struct Group {
     }
     const int64_t n0 = (int64_t)B * nx0 * ny0;
     V2** vecs[9] = {&r, &rh, &p, &v, &s, &t, &ph, &sh, &dx};
+    xoo = c.take<double2>(sizeof(double2) * n0);  // also the fused solver's
     if (light_ws) {
       F = nullptr;
       for (auto vp : vecs) *vp = nullptr;
@@ -214,6 +216,7 @@ struct VcGroup {
   size_t bytes = 0;
   std::vector<Lv> lv;
   double2* F = nullptr;
+  double2* xoo = nullptr;  // fine state x^{n-2} (the quadratic predictor)
   V2 *r, *rh, *p, *v, *s, *t, *ph, *sh, *dx;
   Coef* coef;
   double *part, *theta, *fin;
@@ -248,6 +251,7 @@ struct VcGroup {
     }
     const int64_t n0 = L[0].plane;
     F = c.take<double2>(sizeof(double2) * n0);
+    xoo = c.take<double2>(sizeof(double2) * n0);
     V2** vecs[9] = {&r, &rh, &p, &v, &s, &t, &ph, &sh, &dx};
     for (auto vp : vecs) *vp = c.take<V2>(sizeof(V2) * n0);
     coef = c.take<Coef>(sizeof(Coef) * B);
@@ -1055,10 +1059,17 @@ int implicit_step(henry_handle* H, Group<T>& G, int B, int step, cudaStream_t st
   double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
   H->nact = B;
   launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
-    if (step > 0 && c.newton_predictor > 0.0)
-      k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
-    else
-      k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    // quadratic predictor from step 2 on (three states), linear at step 1
+    const bool quad = c.newton_predictor_order == 2 && G.xoo;
+    if (step > 1 && quad && c.newton_predictor > 0.0) {
+      k_step_begin_predict2<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo, G.xoo);
+    } else {
+      if (quad) k_copy_d2<<<nblk(n0), TPB, 0, st>>>(n0, L.xo, G.xoo);
+      if (step > 0 && c.newton_predictor > 0.0)
+        k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
+      else
+        k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    }
     k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
   });
   CKL();
@@ -1216,6 +1227,7 @@ int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, d
   P.dxtol = c.newton_dxtol;
   P.rtol2 = c.lin_rtol * c.lin_rtol;
   P.predictor = c.newton_predictor;
+  P.predictor_order = c.newton_predictor_order;
   P.dc_limit = c.newton_dc_limit;
   P.rho0g = c.rho0 * c.g;
   P.Ly = c.Ly;
@@ -1223,7 +1235,7 @@ int solve_group_fused(henry_handle* H, Group<T>& G, int B, const CtaLayout& L, d
   CK(cudaMemsetAsync(G.totals, 0, 4 * sizeof(unsigned long long), st));
   H->nact = B;
   launch(H, st, HENRY_K_FUSED, (double)B * (double)lg.nx * lg.ny * lg.steps * 64.0 + (double)B * 48.0, [&] {
-    k_cta_solve<T><<<B, CTA_THREADS, L.bytes, st>>>(P, L, B, G.coef, G.lv[0].xo, qoi, G.status, G.totals);
+    k_cta_solve<T><<<B, CTA_THREADS, L.bytes, st>>>(P, L, B, G.coef, G.lv[0].xo, G.xoo, qoi, G.status, G.totals);
   });
   CKL();
   return HENRY_OK;
@@ -1587,10 +1599,17 @@ int vc_implicit_step(henry_handle* H, VcGroup<T>& G, int B, int step, cudaStream
   double* pmax = G.part + P_MAX * (int64_t)B * G.nct;
   H->nact = B;
   launch(H, st, HENRY_K_NEWTON, (double)n0 * 32, [&] {
-    if (step > 0 && c.newton_predictor > 0.0)
-      k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
-    else
-      k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    // the predictor as in implicit_step (quadratic from step 2 on)
+    const bool quad = c.newton_predictor_order == 2 && G.xoo;
+    if (step > 1 && quad && c.newton_predictor > 0.0) {
+      k_step_begin_predict2<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo, G.xoo);
+    } else {
+      if (quad) k_copy_d2<<<nblk(n0), TPB, 0, st>>>(n0, L.xo, G.xoo);
+      if (step > 0 && c.newton_predictor > 0.0)
+        k_step_begin_predict<<<nblk(n0), TPB, 0, st>>>(n0, c.newton_predictor, L.x, L.xo);
+      else
+        k_step_begin<<<nblk(n0), TPB, 0, st>>>(n0, L.x, L.xo);
+    }
     k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.newton_active, G.newton_it);
   });
   CKL();
@@ -1692,6 +1711,7 @@ struct TuningScope {
     h->cfg.newton_jacobian_every = std::max(1, f->second.newton_jacobian_every);
     h->cfg.assembly_tile_w = f->second.assembly_tile_w;
     h->cfg.mg_threads = f->second.mg_threads;
+    if (f->second.newton_predictor_order > 0) h->cfg.newton_predictor_order = f->second.newton_predictor_order;
   }
   ~TuningScope() { H->cfg = saved; }
 };
@@ -1885,10 +1905,11 @@ int assemble_all(henry_handle* H, Group<T>& G, int n, bool coarse, cudaStream_t 
 
 bool valid_level(henry_handle* h, int level) { return h && level >= 0 && level <= h->cfg.max_level; }
 // ---------------------------------------------------------------------------
-// Discrete adjoint (henry_adjoint).  The forward solve keeps the state pair
-// (x_n, x_{n-1}) every `ckpt` steps and the states of the last segment; the
-// backward sweep visits the segments from the last, recomputes each
-// segment's states from its checkpoint pair (the same kernels and inputs, so
+// Discrete adjoint (henry_adjoint).  The forward solve keeps the states the
+// predictor of the next step reads - (x_n, x_{n-1}), and x_{n-2} with the
+// quadratic predictor - every `ckpt` steps, and the states of the last
+// segment; the backward sweep visits the segments from the last, recomputes
+// each segment's states from its checkpoint (the same kernels and inputs, so
 // the same states), and for every step from the last to the first assembles
 // the Jacobian at (x_m, x_{m-1}), builds the coarse operators, transposes the
 // whole multigrid hierarchy in place, solves J_m^T lam_m = rhs with the same
@@ -1897,7 +1918,8 @@ size_t adjoint_bytes_per_sample(const henry_config& c, int level, int ckpt) {
   const LevelGeom lg = geom(c, level);
   const size_t N = (size_t)lg.nx * lg.ny;
   const size_t nck = (size_t)((lg.steps + ckpt - 1) / ckpt);
-  return (2 * nck + (size_t)ckpt + 1) * N * sizeof(double2) + (size_t)A_NPLANE * N * sizeof(double);
+  const size_t cw = c.newton_predictor_order == 2 ? 3 : 2;  // states per checkpoint
+  return (cw * nck + (size_t)ckpt + 1) * N * sizeof(double2) + (size_t)A_NPLANE * N * sizeof(double);
 }
 
 int ensure_adj_mem(henry_handle* H, size_t bytes) {
@@ -1932,8 +1954,9 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
   const double vt = lg.h * lg.h * inv_tau * inv_s;
   const int steps = lg.steps;
   const int nck = (steps + C - 1) / C;
+  const int cw = c.newton_predictor_order == 2 ? 3 : 2;  // states per checkpoint
   Carver cv{H->adj_mem, 0};
-  double2* ck = cv.take<double2>(vbytes * 2 * nck);  // [nck][x_n, x_{n-1}][B N]
+  double2* ck = cv.take<double2>(vbytes * cw * nck);  // [nck][x_n, x_{n-1} (, x_{n-2})][B N]
   double2* seg = cv.take<double2>(vbytes * C);       // [C][B N]: states of one segment
   double2* rhs = cv.take<double2>(vbytes);
   double* S = cv.take<double>(sizeof(double) * A_NPLANE * (size_t)n0);
@@ -1946,8 +1969,10 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
   CK(cudaMemcpyAsync(L.xo, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
   for (int step = 0; step < steps; ++step) {
     if (step % C == 0) {
-      CK(cudaMemcpyAsync(ck + (int64_t)(2 * (step / C)) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(ck + (int64_t)(2 * (step / C) + 1) * n0, L.xo, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ck + (int64_t)(cw * (step / C)) * n0, L.x, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(ck + (int64_t)(cw * (step / C) + 1) * n0, L.xo, vbytes, cudaMemcpyDeviceToDevice, st));
+      if (cw == 3)
+        CK(cudaMemcpyAsync(ck + (int64_t)(cw * (step / C) + 2) * n0, G.xoo, vbytes, cudaMemcpyDeviceToDevice, st));
     }
     int rc = implicit_step<double>(H, G, B, step, st);
     if (rc) return rc;
@@ -1964,9 +1989,10 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
   CKL();
   for (int k = nck - 1; k >= 0; --k) {
     const int s0 = k * C, s1 = std::min(s0 + C, steps);
-    if (k != nck - 1) {  // recompute the segment's states from its checkpoint pair
-      CK(cudaMemcpyAsync(L.x, ck + (int64_t)(2 * k) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(L.xo, ck + (int64_t)(2 * k + 1) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
+    if (k != nck - 1) {  // recompute the segment's states from its checkpoint
+      CK(cudaMemcpyAsync(L.x, ck + (int64_t)(cw * k) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(L.xo, ck + (int64_t)(cw * k + 1) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
+      if (cw == 3) CK(cudaMemcpyAsync(G.xoo, ck + (int64_t)(cw * k + 2) * n0, vbytes, cudaMemcpyDeviceToDevice, st));
       for (int step = s0; step < s1; ++step) {
         int rc = implicit_step<double>(H, G, B, step, st);
         if (rc) return rc;
@@ -1975,7 +2001,7 @@ int adjoint_group(henry_handle* H, Group<double>& G, int B, const double* xi, co
     }
     for (int step = s1 - 1; step >= s0; --step) {  // state m = step + 1
       const double2* xm = seg + (int64_t)(step - s0) * n0;
-      const double2* xm1 = step == s0 ? ck + (int64_t)(2 * k) * n0 : seg + (int64_t)(step - s0 - 1) * n0;
+      const double2* xm1 = step == s0 ? ck + (int64_t)(cw * k) * n0 : seg + (int64_t)(step - s0 - 1) * n0;
       CK(cudaMemcpyAsync(L.x, xm, vbytes, cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(L.xo, xm1, vbytes, cudaMemcpyDeviceToDevice, st));
       k_step_flags<<<nblk(B, 128), 128, 0, st>>>(B, G.status, G.lin_active, G.newton_it);
@@ -2197,6 +2223,8 @@ int check_config(const henry_config& c, bool with_workspace) {
                                                        c.assembly_tile_w);
   if (!valid_mg_threads(c.mg_threads))
     return set_err(HENRY_EINVAL, "mg_threads %d not in {0, 64, 128, 256, 512}", c.mg_threads);
+  if (c.newton_predictor_order != 1 && c.newton_predictor_order != 2)
+    return set_err(HENRY_EINVAL, "newton_predictor_order %d not in {1, 2}", c.newton_predictor_order);
   return HENRY_OK;
 }
 
@@ -2238,6 +2266,7 @@ void henry_default_config(henry_config* c) {
   c->scheme = HENRY_SCHEME_CELL;
   c->assembly_tile_w = 0;
   c->mg_threads = 0;
+  c->newton_predictor_order = 2;
   c->adj_maxit = 200;
   c->fused_small_grids = 1;
   c->coef_model = HENRY_MODEL_UNIFORM3;
@@ -2268,7 +2297,8 @@ int henry_set_tuning(henry_handle* h, int level, const henry_tuning* t) {
     return HENRY_OK;
   }
   if (!(t->lin_rtol > 0.0) || t->nu1 < 0 || t->nu2 < 0 || t->nu1 + t->nu2 == 0 || t->mg_tail_cells < -1 ||
-      t->newton_jacobian_every < 1 || !valid_tile_w(t->assembly_tile_w) || !valid_mg_threads(t->mg_threads))
+      t->newton_jacobian_every < 1 || !valid_tile_w(t->assembly_tile_w) || !valid_mg_threads(t->mg_threads) ||
+      t->newton_predictor_order < 0 || t->newton_predictor_order > 2)
     return set_err(HENRY_EINVAL, "bad tuning (lin_rtol %g, nu1 %d, nu2 %d, mg_tail_cells %d)", t->lin_rtol, t->nu1,
                    t->nu2, t->mg_tail_cells);
   h->tuned[level] = *t;
@@ -2292,6 +2322,7 @@ int henry_get_tuning(henry_handle* h, int level, henry_tuning* out) {
     out->newton_jacobian_every = h->cfg.newton_jacobian_every;
     out->assembly_tile_w = h->cfg.assembly_tile_w;
     out->mg_threads = h->cfg.mg_threads;
+    out->newton_predictor_order = h->cfg.newton_predictor_order;
   }
   return HENRY_OK;
 }
@@ -2336,6 +2367,7 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         t.newton_jacobian_every = c.newton_jacobian_every;
         t.assembly_tile_w = c.assembly_tile_w;
         t.mg_threads = c.mg_threads;
+        t.newton_predictor_order = c.newton_predictor_order;
         cands.push_back(t);
       }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2423,6 +2455,13 @@ int henry_autotune(henry_handle* h, int level, int with_coarse, const double* xi
         cands.push_back(t);
         trial((int)cands.size() - 1);
       }
+    }
+    if (!rc) {  // the predictor of Newton's first iterate: linear or quadratic in time
+      const int b6 = best;
+      henry_tuning t = cands[b6];
+      t.newton_predictor_order = cands[b6].newton_predictor_order == 2 ? 1 : 2;
+      cands.push_back(t);
+      trial((int)cands.size() - 1);
     }
   }
   if (!rc && best >= 0 && !fused_won && cc && c.tile_assembly) {

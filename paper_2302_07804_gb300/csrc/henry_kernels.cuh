@@ -1387,6 +1387,25 @@ __global__ void __launch_bounds__(TPB) k_step_begin_predict(int64_t n, double w,
   xo[e] = a;
   x[e] = make_double2(fma(w, a.x - b.x, a.x), fma(w, a.y - b.y, a.y));
 }
+// The quadratic predictor: x^{n+1} ~ x^n + w (2 (x^n - x^{n-1}) - (x^{n-1} -
+// x^{n-2})), i.e. 3 x^n - 3 x^{n-1} + x^{n-2} for w = 1 (extrapolation of the
+// parabola through the last three states); xoo <- x^{n-1}, xo <- x^n.
+__global__ void __launch_bounds__(TPB) k_step_begin_predict2(int64_t n, double w, double2* __restrict__ x,
+                                                             double2* __restrict__ xo, double2* __restrict__ xoo) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e >= n) return;
+  const double2 a = x[e], b = xo[e], c = xoo[e];
+  xoo[e] = b;
+  xo[e] = a;
+  const double dx = 2.0 * (a.x - b.x) - (b.x - c.x), dy = 2.0 * (a.y - b.y) - (b.y - c.y);
+  x[e] = make_double2(fma(w, dx, a.x), fma(w, dy, a.y));
+}
+// xoo <- x^{n-1} ahead of a step that still uses the linear predictor, so
+// that the next step has three states.
+__global__ void __launch_bounds__(TPB) k_copy_d2(int64_t n, const double2* __restrict__ src, double2* __restrict__ dst) {
+  const int64_t e = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  if (e < n) dst[e] = src[e];
+}
 __global__ void k_step_flags(int B, const int* __restrict__ status, int* __restrict__ newton_active,
                              int* __restrict__ newton_it) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;

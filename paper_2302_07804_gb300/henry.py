@@ -50,7 +50,7 @@ class HenryConfig(ctypes.Structure):
                 ("mg_tail_cells", ctypes.c_int32), ("mg_tail_batch_cells", ctypes.c_int32),
                 ("scheme", ctypes.c_int32), ("newton_jacobian_every", ctypes.c_int32),
                 ("level_priority", ctypes.c_int32), ("assembly_tile_w", ctypes.c_int32),
-                ("mg_threads", ctypes.c_int32)]
+                ("mg_threads", ctypes.c_int32), ("newton_predictor_order", ctypes.c_int32)]
 
 
 class HenryStats(ctypes.Structure):
@@ -77,7 +77,7 @@ class HenryTuning(ctypes.Structure):
                 ("fused_small_grids", ctypes.c_int32), ("cell_steps_per_s", ctypes.c_double),
                 ("mg_tail_cells", ctypes.c_int32), ("newton_residual_first", ctypes.c_int32),
                 ("newton_jacobian_every", ctypes.c_int32), ("assembly_tile_w", ctypes.c_int32),
-                ("mg_threads", ctypes.c_int32)]
+                ("mg_threads", ctypes.c_int32), ("newton_predictor_order", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

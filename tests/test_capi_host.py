@@ -64,7 +64,8 @@ def test_create_validates_config(L):
     for bad in (dict(nx0=30), dict(ny0=12, nx0=24), dict(precision=7), dict(nu1=-1), dict(max_level=12),
                 dict(Lx=3.0), dict(ny0=1 << 12, nx0=1 << 13, max_level=8), dict(ny0=1 << 29, nx0=1 << 30, max_level=0),
                 dict(steps0=1 << 26, max_level=5), dict(qoi_set=4), dict(workspace_bytes=0.0),
-                dict(assembly_tile_w=16), dict(assembly_tile_w=512), dict(mg_threads=96), dict(mg_threads=1024)):
+                dict(assembly_tile_w=16), dict(assembly_tile_w=512), dict(mg_threads=96), dict(mg_threads=1024),
+                dict(newton_predictor_order=3), dict(newton_predictor_order=0)):
         with pytest.raises(henry.HenryError) as e:
             henry.Solver(**bad)
         assert e.value.code == henry.HENRY_EINVAL
@@ -219,8 +220,9 @@ def test_autotune_arguments_return_einval(L):
     # without tuning, a level's settings are the configuration's
     assert s.tuning(2) == {"lin_rtol": 1e-4, "nu1": 2, "nu2": 2, "fused_small_grids": 1, "cell_steps_per_s": 0.0,
                            "mg_tail_cells": -1, "newton_residual_first": 2, "newton_jacobian_every": 1,
-                           "assembly_tile_w": 0, "mg_threads": 0}
-    for bad in (dict(mg_tail_cells=-2), dict(assembly_tile_w=48), dict(mg_threads=32), dict(newton_jacobian_every=0)):
+                           "assembly_tile_w": 0, "mg_threads": 0, "newton_predictor_order": 2}
+    for bad in (dict(mg_tail_cells=-2), dict(assembly_tile_w=48), dict(mg_threads=32), dict(newton_jacobian_every=0),
+                dict(newton_predictor_order=3)):
         with pytest.raises(henry.HenryError):
             s.set_tuning(2, dict(s.tuning(2), **bad))
     good = dict(s.tuning(2), assembly_tile_w=32, mg_threads=128)

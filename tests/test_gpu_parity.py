@@ -527,6 +527,40 @@ def test_multigrid_cta_size_and_tile_shape_are_bit_identical(hl, precision):
     s.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_linear_predictor_reaches_the_oracle_solution(hl, precision):
+    """The default predictor of Newton's first iterate is quadratic in time
+    (newton_predictor_order 2, which every other test runs); the linear one
+    (order 1) converges to the same discrete solution: level-1 solves with
+    coarse partners and level-0 solves (the fused small-grid solver in mixed
+    precision) against the oracle at relative 1e-10, set in the
+    configuration, and level-2 solves with it set as a level's tuning."""
+    xi = hl.sample_xi(inputs.SEED, 1, 4700, 3)
+    s = hl.Solver(newton_predictor_order=1, precision=precision)
+    qf, qc, st, _ = s.level_batch_solve(1, xi, with_coarse=True)
+    q0, _, st0, _ = s.level_batch_solve(0, xi)
+    assert int(st.abs().sum()) == 0 and int(st0.abs().sum()) == 0
+    x = xi.cpu().numpy()
+    ref1, _ = ohenry.solve_scenarios(PRM, 1, x)
+    ref0, _ = ohenry.solve_scenarios(PRM, 0, x)
+    _qoi_check(qf.cpu().numpy(), ref1)
+    _qoi_check(qc.cpu().numpy(), ref0)
+    _qoi_check(q0.cpu().numpy(), ref0)
+    s.close()
+    t = hl.Solver(precision=precision)
+    for lv in (1, 2):
+        t.set_tuning(lv, dict(t.tuning(lv), newton_predictor_order=1))
+    xi2 = hl.sample_xi(inputs.SEED, 2, 4720, 2)
+    q2, q1, st2, _ = t.level_batch_solve(2, xi2, with_coarse=True)
+    assert int(st2.abs().sum()) == 0
+    x2 = xi2.cpu().numpy()
+    ref2, _ = ohenry.solve_scenarios(PRM, 2, x2)
+    ref1b, _ = ohenry.solve_scenarios(PRM, 1, x2)
+    _qoi_check(q2.cpu().numpy(), ref2)
+    _qoi_check(q1.cpu().numpy(), ref1b)
+    t.close()
+
+
 @pytest.mark.parametrize("every,precision", [(2, 0), (3, 0), (2, 1)])
 def test_chord_newton_reaches_the_oracle_solution(hl, every, precision):
     """Chord Newton (the Jacobian and coarse operators re-assembled every

@@ -265,11 +265,13 @@ def test_vc_residual_first_and_chord_newton(hl):
         out.append((q, st, stats["newton_iters"], stats["linear_iters"]))
         s.close()
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1]) and out[0][2:] == out[1][2:]
-    s = _vc_solver(hl, newton_jacobian_every=2, lin_rtol=1e-2)
-    q, _, st, _ = s.level_batch_solve(0, xi)
-    assert int(st.abs().sum()) == 0
-    _qoi_close(q.cpu().numpy(), np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()]))
-    s.close()
+    ref = np.array([vc.solve_scenario(prm, 0, v)[0] for v in xi.cpu().numpy()])
+    for kw in (dict(newton_jacobian_every=2, lin_rtol=1e-2), dict(newton_predictor_order=1)):
+        s = _vc_solver(hl, **kw)  # chord Newton; the linear time predictor (the default is quadratic)
+        q, _, st, _ = s.level_batch_solve(0, xi)
+        assert int(st.abs().sum()) == 0
+        _qoi_close(q.cpu().numpy(), ref)
+        s.close()
 
 
 def test_vc_level_tuning_applies_and_autotune_runs(hl):
