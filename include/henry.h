@@ -142,7 +142,7 @@ typedef struct {
   int32_t coarse_op;                   /* HENRY_COARSE_REDISCRETISE or HENRY_COARSE_GALERKIN */
   double newton_atol;  /* stop when max |R| / (rho0 h^2 / tau) <= newton_atol ... */
   double newton_dxtol; /* ... or right after an update with max(|dp| / (rho0 g Ly), |dc|) <= newton_dxtol */
-  double lin_rtol;     /* BiCGStab: ||r||_2 <= lin_rtol ||b||_2 per sample (default 1e-4: inexact Newton) */
+  double lin_rtol;     /* BiCGStab: ||r||_2 <= lin_rtol ||b||_2 per sample (default 1e-3: inexact Newton) */
   int32_t newton_maxit, lin_maxit, nu1, nu2; /* caps; pre/post smoothing sweeps of the V-cycle */
   double workspace_bytes;                    /* device workspace budget per batch (chunking) */
   double newton_predictor; /* weight w in [0, 1] of the time predictor of Newton's first iterate of step

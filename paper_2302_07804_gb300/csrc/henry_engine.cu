@@ -2245,7 +2245,7 @@ void henry_default_config(henry_config* c) {
   c->coarse_op = HENRY_COARSE_REDISCRETISE;
   c->newton_atol = 1e-11;
   c->newton_dxtol = 1e-12;
-  c->lin_rtol = 1e-4;  // inexact Newton: the FP64 residual test decides convergence
+  c->lin_rtol = 1e-3;  // inexact Newton: the FP64 residual test decides convergence
   c->newton_maxit = 30;
   c->lin_maxit = 40;
   c->nu1 = 2; c->nu2 = 2;
