@@ -511,7 +511,8 @@ bool fused_eligible(const henry_config& c, int level, CtaLayout* L) {
 
 int smem_optin();
 // Dynamic shared memory the tail kernel may use: the opt-in limit less a
-// reserve for static shared memory.
+// small margin (the kernel declares no static shared memory; the margin
+// keeps room should it ever declare some).
 constexpr int TAIL_STATIC_RESERVE = 256;
 int tail_dyn_max() { return std::max(0, smem_optin() - TAIL_STATIC_RESERVE); }
 
